@@ -1,0 +1,476 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 connectivity path.
+
+Headline (one JSON line on stdout): static connectivity throughput in
+Gedges/s (directed CSR entries m per second) on an R-MAT graph of scale 26,
+edge factor 16, (a, b, c, d) = (0.57, 0.19, 0.19, 0.05), symmetrised, uint64
+offsets and uint32 edges, with the default k-out (k=2) + UF-Rem-CAS
+combination; its fraction of the HBM roofline (CSR bytes read once over the
+measured copy bandwidth); the dominant kernel's roofline; the end-to-end rate
+through the host-buffer entry point; the oracle's rate on a bounded sample of
+the same graph on the host cores; and the incremental rates (updates/s and
+p50/p99 batch latency) on an R-MAT scale-24 base graph.
+
+A step is one cc_static call over the resident graph.  Inputs (7.7 GB CSR,
+268 MB labels) exceed the 126 MB L2, so no flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (torchrun): every rank labels its own replica of the graph (the
+path has no exchange step at one graph per GPU): weak scaling, no collective
+on the data path; rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "static CC Gedges/s & % HBM peak at RMAT-26; incremental updates/s & p99"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--scale", type=int, default=26)
+    p.add_argument("--edge-factor", type=int, default=16)
+    p.add_argument("--sample", default="kout")
+    p.add_argument("--finish", default="uf_rem_cas")
+    p.add_argument("--find", default="naive")
+    p.add_argument("--splice", default="split_one")
+    p.add_argument("--freq-samples", type=int, default=0)
+    p.add_argument("--incr-scale", type=int, default=24)
+    p.add_argument("--incr-batches", type=int, default=100)
+    p.add_argument("--incr-qfrac", type=float, default=0.5)
+    p.add_argument("--no-incr", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--combos", action="store_true", help="also time every sampling x finish combination")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.file is None:
+            return None
+        rows = []
+        try:
+            with open(self.file.name) as f:
+                for ln in f:
+                    parts = [x.strip() for x in ln.split(",")]
+                    if len(parts) >= 8:
+                        rows.append(parts)
+            os.unlink(self.file.name)
+        except Exception:
+            return None
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- workloads
+def make_graph(scale, ef, device):
+    import synth
+    return synth.rmat(scale, ef, seed=1, device=device)
+
+
+def algorithmic_bytes(kernel, n, m, m_finish, n_nz, k, off_bytes):
+    """Compulsory bytes of one launch of `kernel` (word granularity):
+    offsets 8 B (or 4 B) per vertex, edges 4 B each, parent words 4 B each.
+    n_nz: vertices with at least one edge; m_finish: edges out of non-L_max
+    vertices."""
+    ob = off_bytes
+    table = {
+        "k_iota": 4 * n,                                          # write P
+        "k_kout": ob * (n + 1) + n_nz * k * (4 + 4) + 4 * n + 4 * n_nz,   # offsets, k edges + k parents, own parent, one link
+        "k_shortcut": 8 * n,                                      # read + write P
+        "k_count_labels": 4 * n + 4 * n,                          # read labels, count RMW
+        "k_argmax_counts": 4 * n,
+        "k_cand_bin": 4 * n + ob * (n + 1),                       # labels + offsets
+        "k_light_list": 4 * m_finish * 2,                         # edges + parent of each neighbour
+        "k_chunks": 4 * m_finish * 2,
+        "k_range_bin": ob * (n + 1) + 4 * n + 4 * m + 4 * m // 2,  # offsets, own parent, edges, parents of lower neighbours
+    }
+    return table.get(kernel)
+
+
+def run_ours(args):
+    import torch
+    import paper_2008_03909_gb300 as cc
+    import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    t0 = time.time()
+    g = make_graph(args.scale, args.edge_factor, dev)
+    n, m = g.n, g.m
+    gen_s = time.time() - t0
+    deg = g.offsets[1:] - g.offsets[:-1]
+    n_nz = int((deg > 0).sum().item())
+    del deg
+    torch.cuda.empty_cache()
+    off, edg = g.offsets, g.edges
+    so = cc.sample_opt(args.sample, k=2, bfs_tries=3, ldd_beta=0.2, seed=1, freq_samples=args.freq_samples)
+    fo = cc.finish_opt(args.finish, args.find, args.splice)
+    labels = torch.empty(n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    # one checked run: stats + invariants that hold at any size
+    lab, st = cc.cc_static(off, edg, so, fo, labels, stats=True)
+    src = torch.repeat_interleave(torch.arange(n, device=dev, dtype=torch.int32), (off[1:] - off[:-1]))
+    ok = bool((lab[src.long()] == lab[edg.long()]).all().item()) if m else True
+    del src
+    ar = torch.arange(n, device=dev, dtype=torch.int32)
+    ok = ok and bool((lab <= ar).all().item()) and bool((lab[lab.long()] == lab).all().item())
+    ncomp = int((lab == ar).sum().item())
+    del ar
+    torch.cuda.empty_cache()
+
+    for _ in range(args.warmup):
+        cc.cc_static(off, edg, so, fo, labels)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches0 = cc.launch_count()
+    cc.profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            cc.cc_static(off, edg, so, fo, labels)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    prof = cc.profile_read()
+    cc.profile_enable(False)
+    launches = cc.launch_count() - launches0
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    value = world * m / (ms * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    off_bytes = 8 if off.dtype == torch.int64 else 4
+    b_csr = off_bytes * (n + 1) + 4 * m
+    hbm_frac = (b_csr / (peak * 1e9)) / (ms * 1e-3)
+
+    # dominant kernel roofline (per-launch averages from the timed region)
+    kernels = {k: {"launches": v[0], "ms_total": round(v[1], 4), "ms_avg": v[1] / max(v[0], 1),
+                   "share": v[1] / max(sum(x[1] for x in prof.values()), 1e-9)} for k, v in prof.items()}
+    dom = max(kernels, key=lambda k: kernels[k]["ms_total"]) if kernels else None
+    roof = None
+    if dom:
+        ab = algorithmic_bytes(dom, n, m, st["edges_finish"], n_nz, 2, off_bytes)
+        if ab is not None:
+            per_launch_ms = kernels[dom]["ms_avg"]
+            ach = ab / (per_launch_ms * 1e-3) / 1e9
+            roof = {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                    "frac": round(ach / peak, 4), "traffic": None, "peak_kind": peak_kind,
+                    "algorithmic_bytes": ab, "ms_avg": round(per_launch_ms, 5)}
+
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": "Gedges/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": f"rmat{args.scale}_ef{args.edge_factor}", "n": n, "m": m,
+                   "rmat": [0.57, 0.19, 0.19, 0.05], "seed": 1, "offsets": "u64" if off_bytes == 8 else "u32",
+                   "sample": args.sample, "finish": f"{args.finish}+{args.find}+{args.splice}",
+                   "freq_samples": args.freq_samples, "l2": "inputs exceed L2 (no flush)",
+                   "parallelism": f"replicas x{world}"},
+        "hbm_roof_frac": round(hbm_frac, 4), "hbm_roof_peak_gbs": peak,
+        "roofline": roof, "kernels": kernels, "gpu_launches": launches,
+        "check": {"invariants_ok": ok, "components": ncomp, "lmax": st["lmax"], "edges_finish": st["edges_finish"],
+                  "n_nonisolated": n_nz},
+        "gen_s": round(gen_s, 2),
+    }
+    clocks = clk.summary()
+    out["clocks"] = clocks
+
+    # end to end through the host-buffer entry point (pinned host CSR)
+    if not args.no_e2e:
+        h_off = off.cpu().pin_memory()
+        h_edg = edg.cpu().pin_memory()
+        h_lab = torch.empty(n, dtype=torch.int32).pin_memory()
+        cc.cc_static_host(h_off, h_edg, so, fo, h_lab)
+        k2 = max(1, min(args.steps, 5))
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t1 = time.perf_counter()
+        for _ in range(k2):
+            cc.cc_static_host(h_off, h_edg, so, fo, h_lab)
+        e2e_s = (time.perf_counter() - t1) / k2
+        if dist:
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        same = bool(torch.equal(h_lab, lab.cpu()))
+        out["e2e"] = {"value": round(world * m / e2e_s / 1e9, 3), "unit": "Gedges/s",
+                      "h2d_bytes_per_step": b_csr, "d2h_bytes_per_step": 4 * n, "ms_per_step": round(e2e_s * 1e3, 3),
+                      "labels_equal_device_path": same}
+        del h_off, h_edg, h_lab
+
+    # incremental: resident union-find, batches of inserts + queries
+    if not args.no_incr:
+        out["incremental"] = bench_incremental(args, cc, synth, dev)
+
+    if args.combos:
+        out["combos"] = bench_combos(args, cc, off, edg, labels, lab, m)
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(off, edg, args.cpu_seconds)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out if rank == 0 else None
+
+
+def bench_combos(args, cc, off, edg, labels, ref, m):
+    import torch
+    res = {}
+    for s in ("none", "kout", "bfs", "ldd"):
+        for f in ("uf_rem_cas", "uf_async", "sv", "lt_prf"):
+            so = cc.sample_opt(s)
+            fo = cc.finish_opt(f, "naive" if f != "uf_async" else "split")
+            cc.cc_static(off, edg, so, fo, labels)
+            same = bool(torch.equal(labels, ref))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 3
+            e0.record()
+            for _ in range(reps):
+                cc.cc_static(off, edg, so, fo, labels)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            res[f"{s}+{f}"] = {"ms": round(ms, 3), "gedges_s": round(m / (ms * 1e-3) / 1e9, 2), "exact": same}
+    return res
+
+
+def bench_incremental(args, cc, synth, dev):
+    import torch
+    base = synth.rmat(args.incr_scale, 16, seed=2, device=dev)
+    n = base.n
+    inc = cc.Incremental(n, base.offsets, base.edges)
+    del base
+    torch.cuda.empty_cache()
+    sizes = synth.log_uniform_sizes(args.incr_batches, 1e3, 1e7, seed=3, stream=50)
+    qf = args.incr_qfrac
+    # stage every batch in pinned host memory (inserts R-MAT distributed,
+    # queries uniform), then time host -> device -> answers -> host
+    batches = []
+    for b, sz in enumerate(sizes):
+        nq = int(round(sz * qf))
+        ni = sz - nq
+        ins = synth.rmat_pairs(args.incr_scale, ni, seed=100 + b, stream=60, device=dev).reshape(-1)
+        qs = synth.random_pairs(n, nq, seed=100 + b, stream=70, device=dev).reshape(-1)
+        batches.append((ins.cpu().pin_memory(), qs.cpu().pin_memory(), ni, nq))
+    max_i = max(b[2] for b in batches) * 2 + 2
+    max_q = max(b[3] for b in batches) * 2 + 2
+    d_ins = torch.empty(max_i, dtype=torch.int32, device=dev)
+    d_qs = torch.empty(max_q, dtype=torch.int32, device=dev)
+    d_ans = torch.empty(max_q // 2, dtype=torch.uint8, device=dev)
+    h_ans = torch.empty(max_q // 2, dtype=torch.uint8).pin_memory()
+    stream = torch.cuda.current_stream()
+    lat_dev, lat_e2e = [], []
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in batches]
+    total_ins = total_q = 0
+    torch.cuda.synchronize()
+    t_all = time.perf_counter()
+    for (hi, hq, ni, nq), (a, b) in zip(batches, ev):
+        t1 = time.perf_counter()
+        d_ins[: 2 * ni].copy_(hi, non_blocking=True)
+        d_qs[: 2 * nq].copy_(hq, non_blocking=True)
+        a.record(stream)
+        inc.insert(d_ins[: 2 * ni])
+        inc.query(d_qs[: 2 * nq], out=d_ans[:nq])
+        b.record(stream)
+        h_ans[:nq].copy_(d_ans[:nq], non_blocking=True)
+        stream.synchronize()
+        lat_e2e.append((time.perf_counter() - t1) * 1e3)
+        total_ins += ni
+        total_q += nq
+    wall = time.perf_counter() - t_all
+    for a, b in ev:
+        lat_dev.append(a.elapsed_time(b))
+    dev_s = sum(lat_dev) / 1e3
+
+    def pct(xs, p):
+        xs = sorted(xs)
+        return xs[min(len(xs) - 1, int(math.ceil(p / 100 * len(xs))) - 1)]
+
+    inc.close()
+    return {"base": f"rmat{args.incr_scale}_ef16", "n": n, "batches": len(batches), "query_fraction": qf,
+            "inserts": total_ins, "queries": total_q,
+            "updates_per_s_device": round(total_ins / dev_s, 1), "ops_per_s_device": round((total_ins + total_q) / dev_s, 1),
+            "updates_per_s_e2e": round(total_ins / wall, 1), "ops_per_s_e2e": round((total_ins + total_q) / wall, 1),
+            "p50_ms_device": round(pct(lat_dev, 50), 4), "p99_ms_device": round(pct(lat_dev, 99), 4),
+            "p50_ms_e2e": round(pct(lat_e2e, 50), 4), "p99_ms_e2e": round(pct(lat_e2e, 99), 4),
+            "batch_sizes": "log-uniform in [1e3, 1e7], seeded"}
+
+
+def cpu_baseline(off, edg, seconds):
+    """The oracle's sequential union-find (O1) over the first vertices' edges
+    of the same graph, grown until it runs ~`seconds`; Gedges/s."""
+    import numpy as np
+    import oracle
+    offs = off.cpu().numpy().astype(np.uint64)
+    n = offs.shape[0] - 1
+    # calibrate on a small prefix, then run a prefix sized for `seconds`
+    target_e = 20_000_000
+    u_end = int(np.searchsorted(offs, target_e))
+    e_end = int(offs[u_end])
+    edges = edg[:e_end].cpu().numpy().view(np.uint32)
+    P = np.arange(n, dtype=np.uint32)
+    t0 = time.perf_counter()
+    _, cnt = _prefix(oracle, offs, edges, u_end, P)
+    dt = time.perf_counter() - t0
+    rate = cnt / max(dt, 1e-9)
+    want_e = min(int(offs[-1]), int(rate * seconds))
+    if want_e > e_end:
+        u_end = int(np.searchsorted(offs, want_e))
+        e_end = int(offs[u_end])
+        edges = edg[:e_end].cpu().numpy().view(np.uint32)
+        P = np.arange(n, dtype=np.uint32)
+        t0 = time.perf_counter()
+        _, cnt = _prefix(oracle, offs, edges, u_end, P)
+        dt = time.perf_counter() - t0
+    return {"value": round(cnt / dt / 1e9, 5), "unit": "Gedges/s", "cores": 1, "kind": "oracle",
+            "sample": f"O1 sequential union-find over the edges of vertices [0, {u_end}) "
+                      f"({cnt} of {int(offs[-1])} directed edges) of the same graph, {dt:.1f} s",
+            "seconds": round(dt, 2), "host_cores": len(os.sched_getaffinity(0))}
+
+
+def _prefix(oracle, offs, edges, u_end, P):
+    """uf_prefix on a CSR whose edge array holds only the prefix's edges."""
+    import ctypes
+    import numpy as np
+    L = oracle.lib()
+    Ip = offs.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+    Ap = edges.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+    cnt = L.oracle_uf_prefix(offs.shape[0] - 1, Ip, Ap, u_end, P.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
+    return P, int(cnt)
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step is a bounded sample (O1
+    over a prefix of the same graph's vertices) on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    import numpy as np
+    import torch
+    import oracle
+    dev = torch.device("cuda", 0) if torch.cuda.is_available() else torch.device("cpu")
+    g = make_graph(args.scale, args.edge_factor, dev)
+    offs = g.offsets.cpu().numpy().astype(np.uint64)
+    n = g.n
+    per_step = max(1.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
+    target = 5_000_000
+    u_end = int(np.searchsorted(offs, target))
+    edges = g.edges[: int(offs[u_end])].cpu().numpy().view(np.uint32)
+    t0 = time.perf_counter()
+    _, cnt = _prefix(oracle, offs, edges, u_end, np.arange(n, dtype=np.uint32))
+    rate = cnt / max(time.perf_counter() - t0, 1e-9)
+    want = min(int(offs[-1]), int(rate * per_step))
+    u_end = int(np.searchsorted(offs, want))
+    e_end = int(offs[u_end])
+    edges = g.edges[:e_end].cpu().numpy().view(np.uint32)
+    for _ in range(args.warmup):
+        _prefix(oracle, offs, edges, u_end, np.arange(n, dtype=np.uint32))
+    times = []
+    for _ in range(args.steps):
+        P = np.arange(n, dtype=np.uint32)
+        t0 = time.perf_counter()
+        _, cnt = _prefix(oracle, offs, edges, u_end, P)
+        times.append(time.perf_counter() - t0)
+    dt = sum(times) / len(times)
+    value = cnt / dt / 1e9
+    sample = f"O1 over the edges of vertices [0, {u_end}) ({cnt} directed edges) of rmat{args.scale}_ef{args.edge_factor}"
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "Gedges/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"rmat{args.scale}_ef{args.edge_factor}", "n": n, "m": int(offs[-1]),
+                       "sample": args.sample, "finish": args.finish},
+            "cpu_baseline": {"value": round(value, 5), "unit": "Gedges/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 5), "unit": "Gedges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

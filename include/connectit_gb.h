@@ -1,0 +1,205 @@
+/*
+ * connectit_gb.h -- C ABI of a GB300 (sm_103a) implementation of ConnectIt's
+ * static and incremental graph connectivity (Dhulipala, Hong, Shun,
+ * "ConnectIt: A Framework for Static and Incremental Parallel Graph
+ * Connectivity Algorithms").
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ * Graph: symmetric CSR (Section 2, "Graph Notation and Formats").  `offsets`
+ *   holds n+1 entries (uint32 when offsets_u64 == 0, else uint64) with
+ *   offsets[0] = 0 and offsets[n] = m; `edges` holds m uint32 vertex ids; the
+ *   neighbours of v are edges[offsets[v] .. offsets[v+1]-1].  Every
+ *   undirected edge must be stored in both directions (the finish methods
+ *   skip the edges out of the largest sampled component and rely on the
+ *   reverse copy, Theorem B.2).  Self-loops and duplicates are allowed.
+ * Result: canonical labels, labels[v] = the smallest vertex id of v's
+ *   connected component (a connectivity labelling, Section 2, in the unique
+ *   min-id form).  Every sampling x finish combination writes the same array.
+ * Memory: every array argument is a DEVICE pointer owned by the caller,
+ *   except in cc_static_host, whose arrays are host pointers.  The library
+ *   allocates only its own scratch (stream-ordered, cudaMallocAsync on the
+ *   call's stream) and frees it before the call's work completes.
+ * Streams: `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *   Work is enqueued on it.  Calls return once their work is enqueued, except
+ *   where a method's loop depends on device data (BFS and LDD sampling, the
+ *   SV and LT finishes), where the call waits on the stream between rounds.
+ * Errors: argument checks are synchronous and return CC_ERR_INVALID before
+ *   anything is enqueued.  Input faults found on the device (an edge id >= n,
+ *   decreasing or out-of-range offsets) and iteration caps reached in a
+ *   device loop never trap: kernels skip the bad access, record a bit in a
+ *   per-device sticky error word and return.  cc_device_error() reads and
+ *   clears that word; calls that synchronise anyway (cc_static_ex with
+ *   stats, cc_static_host) return it as their status.
+ * Threads: entry points may be called from several host threads on
+ *   different streams; they share the sticky error word.
+ */
+#ifndef CONNECTIT_GB_H
+#define CONNECTIT_GB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum cc_status {
+    CC_OK = 0,
+    CC_ERR_INVALID = 1,        /* bad argument: nothing was enqueued */
+    CC_ERR_OOM = 2,            /* scratch allocation failed */
+    CC_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+    CC_ERR_NONCONVERGED = 4,   /* a device loop reached its iteration/time cap */
+    CC_ERR_BAD_INPUT = 5,      /* device found an edge id >= n or bad offsets */
+    CC_ERR_UNSUPPORTED = 6     /* option combination not provided */
+} cc_status;
+
+/* Device sticky-error bits (cc_device_error). */
+#define CC_DEVERR_BAD_EDGE     1u
+#define CC_DEVERR_BAD_OFFSETS  2u
+#define CC_DEVERR_NONCONVERGED 4u
+
+/* Sampling methods (Section 3.2; Algorithms 4-6). */
+enum { CC_SAMPLE_NONE = 0, CC_SAMPLE_KOUT = 1, CC_SAMPLE_BFS = 2, CC_SAMPLE_LDD = 3 };
+/* Finish methods (Section 3.3): UF-Rem-CAS (Algorithm 14), UF-Async
+ * (Algorithm 10), Shiloach-Vishkin (Algorithm 15), Liu-Tarjan PRF
+ * (ParentConnect + RootUpdate + FullShortcut, Appendix D). */
+enum { CC_FINISH_UF_REM_CAS = 0, CC_FINISH_UF_ASYNC = 1, CC_FINISH_SV = 2, CC_FINISH_LT_PRF = 3 };
+/* Find options (Algorithm 8): no compaction, atomic path splitting, atomic
+ * path halving.  For UF-Rem-CAS this is the Compress option of Algorithm 14. */
+enum { CC_FIND_NAIVE = 0, CC_FIND_SPLIT = 1, CC_FIND_HALVE = 2 };
+/* Splice options of Rem's algorithm (Algorithm 9). */
+enum { CC_SPLICE_SPLIT_ONE = 0, CC_SPLICE_HALVE_ONE = 1 };
+
+typedef struct cc_sample_opt {
+    int32_t kind;          /* CC_SAMPLE_* */
+    uint32_t k;            /* k-out: edges per vertex, the first plus k-1 uniform picks (>= 1; 2) */
+    uint32_t bfs_tries;    /* BFS: number of tries c (>= 1; 3) */
+    float ldd_beta;        /* LDD: beta in (0, 64] (0.2) */
+    uint64_t seed;         /* seed of every random draw (k-out picks, BFS sources, freq sample) */
+    uint32_t freq_samples; /* IdentifyFrequent: 0 counts all n labels; S in [1, 4096] counts S
+                              seeded sample positions (an estimate; changes work, not labels) */
+    uint32_t reserved;     /* must be 0 */
+} cc_sample_opt;
+
+typedef struct cc_finish_opt {
+    int32_t kind;          /* CC_FINISH_* */
+    int32_t find;          /* CC_FIND_* (union-find finishes) */
+    int32_t splice;        /* CC_SPLICE_* (UF-Rem-CAS) */
+    int32_t reserved;      /* must be 0 */
+} cc_finish_opt;
+
+/* Counters of one cc_static_ex call. */
+typedef struct cc_stats {
+    uint32_t lmax;          /* L_max, the frequent sampled label (0xFFFFFFFF with no sampling) */
+    int32_t sample_info;    /* BFS: index of the successful try or -1; LDD: rounds; else 0 */
+    uint32_t rounds;        /* SV / LT: rounds run; union-find: 0 */
+    uint32_t reserved;
+    uint64_t edges_finish;  /* directed edges read by the finish (out of non-L_max vertices) */
+} cc_stats;
+
+/* Sensible defaults: k-out k=2, c=3 BFS tries, LDD beta=0.2, seed 1, exact
+ * IdentifyFrequent; UF-Rem-CAS with SplitAtomicOne and no extra compression. */
+void cc_default_opts(cc_sample_opt *sample, cc_finish_opt *finish);
+
+/* Static connectivity, Algorithm 1: labels <- identity; SampleComponents;
+ * L_max <- IdentifyFrequent; FinishComponents skipping the vertices whose
+ * sampled label is L_max; then a final shortcut to canonical min-id labels.
+ * labels_out: device uint32[n], written (it also serves as the parent array
+ * during the call).  sample/finish: host pointers; NULL = defaults. */
+cc_status cc_static(const void *offsets, int offsets_u64, const uint32_t *edges, uint32_t n,
+                    uint64_t m, const cc_sample_opt *sample, const cc_finish_opt *finish,
+                    uint32_t *labels_out, void *stream);
+
+/* cc_static plus counters: when stats != NULL the call synchronises the
+ * stream, fills *stats (host memory) and returns the device error status. */
+cc_status cc_static_ex(const void *offsets, int offsets_u64, const uint32_t *edges, uint32_t n,
+                       uint64_t m, const cc_sample_opt *sample, const cc_finish_opt *finish,
+                       uint32_t *labels_out, cc_stats *stats, void *stream);
+
+/* cc_static on HOST buffers (offsets, edges, labels_out in host memory,
+ * ideally pinned): copies the graph to library-allocated device memory,
+ * runs cc_static, copies the labels back and synchronises.  Returns the
+ * device error status. */
+cc_status cc_static_host(const void *offsets, int offsets_u64, const uint32_t *edges, uint32_t n,
+                         uint64_t m, const cc_sample_opt *sample, const cc_finish_opt *finish,
+                         uint32_t *labels_out, void *stream);
+
+/* The three phases of Algorithm 1 on their own (the same kernels cc_static
+ * runs), so that each can be checked and timed alone.
+ * cc_sample: labels <- identity, then SampleComponents (k-out: union-find
+ *   over the picked edges and full compression; BFS / LDD: clusters), each
+ *   sampled cluster relabelled to its smallest member (a min-rooted star).
+ *   labels_out: device uint32[n].  *sample_info_out (host, may be NULL) gets
+ *   the BFS try index / LDD rounds; it forces a synchronisation.
+ * cc_identify_frequent: *lmax_out (DEVICE uint32) <- the most frequent
+ *   label of labels[0..n) (ties: smallest label); freq_samples/seed as in
+ *   cc_sample_opt.
+ * cc_finish: labels_inout holds sampled labels (min-rooted stars, as
+ *   cc_sample writes them); runs the finish skipping vertices whose label
+ *   equals lmax (0xFFFFFFFF: skip none) and writes canonical labels. */
+cc_status cc_sample(const void *offsets, int offsets_u64, const uint32_t *edges, uint32_t n,
+                    uint64_t m, const cc_sample_opt *sample, uint32_t *labels_out,
+                    int32_t *sample_info_out, void *stream);
+cc_status cc_identify_frequent(const uint32_t *labels, uint32_t n, uint32_t freq_samples,
+                               uint64_t seed, uint32_t *lmax_out, void *stream);
+cc_status cc_finish(const void *offsets, int offsets_u64, const uint32_t *edges, uint32_t n,
+                    uint64_t m, const cc_finish_opt *finish, uint32_t lmax, uint32_t *labels_inout,
+                    uint32_t *rounds_out, void *stream);
+
+/* Batch-incremental connectivity (Section 3.5, Algorithm 3; Appendix B.4).
+ * A handle owns a resident parent array P (n uint32 in device memory).
+ * cc_incr_create runs Initialize: static connectivity of the base graph
+ *   (offsets/edges device pointers; both may be NULL when m == 0) into P.
+ *   Finish kinds: the union-find ones (SV / LT batches: CC_ERR_UNSUPPORTED).
+ * cc_incr_insert_batch: Insert(u, v) for k pairs (device uint32[2k],
+ *   interleaved u0 v0 u1 v1 ...), each a Union.
+ * cc_incr_query_batch: IsConnected(u, v) for q pairs -> answers_out (device
+ *   uint8[q], 1 = connected).  A query sees every insert enqueued earlier on
+ *   the handle (inserts and queries are separate phases, the
+ *   phase-concurrent setting of Section 3.5, type 3).
+ * cc_incr_labels: canonical min-id labels of the current graph.
+ * Pairs with an id >= n are skipped and flagged (CC_DEVERR_BAD_EDGE); their
+ *   answers are 0.  Calls on one handle must be stream-ordered. */
+typedef struct cc_incr cc_incr;
+cc_status cc_incr_create(const void *offsets, int offsets_u64, const uint32_t *edges, uint32_t n,
+                         uint64_t m, const cc_sample_opt *sample, const cc_finish_opt *finish,
+                         void *stream, cc_incr **out);
+cc_status cc_incr_insert_batch(cc_incr *h, const uint32_t *pairs, uint64_t k, void *stream);
+cc_status cc_incr_query_batch(cc_incr *h, const uint32_t *pairs, uint64_t q, uint8_t *answers_out,
+                              void *stream);
+cc_status cc_incr_labels(cc_incr *h, uint32_t *labels_out, void *stream);
+uint32_t cc_incr_num_vertices(const cc_incr *h);
+cc_status cc_incr_destroy(cc_incr *h);
+
+/* Synchronise `stream`, then read and clear the per-device sticky error
+ * word (CC_DEVERR_* bits) into *bits_out (host; may be NULL).  Returns
+ * CC_OK when the word was 0, else the matching status. */
+cc_status cc_device_error(void *stream, uint32_t *bits_out);
+
+/* Test hook: cap on the iterations of one device loop (a find, a union, a
+ * round loop).  0 restores the default (2n + 1024 steps, 4096 rounds). */
+void cc_set_iteration_cap(uint64_t cap);
+
+/* Instrumentation (the library's own tracing; no paper counterpart beyond
+ * its per-phase timings).  Every kernel launch increments a process-wide
+ * counter (cc_launch_count).  While profiling is enabled, each launch is
+ * also bracketed by CUDA events on its stream; cc_profile_read waits for
+ * those events and returns per-kernel totals (name, launches, milliseconds)
+ * accumulated since profiling was enabled, up to `max` entries, returning
+ * the number of kernels.  Enabling resets the totals. */
+typedef struct cc_kernel_time {
+    char name[48];
+    uint64_t launches;
+    double ms;
+} cc_kernel_time;
+void cc_profile_enable(int on);
+int cc_profile_read(cc_kernel_time *out, int max);
+uint64_t cc_launch_count(void);
+
+const char *cc_status_str(cc_status s);
+const char *cc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CONNECTIT_GB_H */

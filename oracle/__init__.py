@@ -48,6 +48,8 @@ def lib():
             L.oracle_draw.argtypes = [c.c_uint64, c.c_uint64]
             L.oracle_cc_uf.restype = c.c_uint64
             L.oracle_cc_uf.argtypes = [c.c_uint32, u64p, u32p, u32p]
+            L.oracle_uf_prefix.restype = c.c_uint64
+            L.oracle_uf_prefix.argtypes = [c.c_uint32, u64p, u32p, c.c_uint32, u32p]
             L.oracle_cc_bfs.restype = c.c_int
             L.oracle_cc_bfs.argtypes = [c.c_uint32, u64p, u32p, u32p]
             L.oracle_identify_frequent.restype = c.c_uint32
@@ -118,6 +120,16 @@ def cc_uf(offsets, edges):
     lab = np.empty(n, np.uint32)
     links = lib().oracle_cc_uf(n, Ip, Ap, lab.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
     return lab, int(links)
+
+
+def uf_prefix(offsets, edges, u_end: int, P=None):
+    """O1's union loop over the edges of vertices [0, u_end) (a bounded slice
+    for timing).  Returns (forest P, edges processed)."""
+    n, (I, Ip), (A, Ap) = _graph(_as_np(offsets), _as_np(edges))
+    if P is None:
+        P = np.arange(n, dtype=np.uint32)
+    cnt = lib().oracle_uf_prefix(n, Ip, Ap, u_end, P.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
+    return P, int(cnt)
 
 
 def cc_bfs(offsets, edges):

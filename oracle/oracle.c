@@ -85,6 +85,20 @@ uint64_t oracle_cc_uf(uint32_t n, const uint64_t *I, const uint32_t *A, uint32_t
     return links;   /* = n - #components */
 }
 
+/* O1's union loop restricted to the edges of vertices [0, u_end), on a
+ * caller-initialised forest P (identity for a fresh start): a bounded
+ * slice of the same work, used to time the oracle on a sample of a large
+ * graph.  Returns the number of edges processed. */
+uint64_t oracle_uf_prefix(uint32_t n, const uint64_t *I, const uint32_t *A, uint32_t u_end, uint32_t *P) {
+    uint64_t e_done = 0;
+    if (u_end > n) u_end = n;
+    for (uint32_t u = 0; u < u_end; u++) {
+        for (uint64_t e = I[u]; e < I[u + 1]; e++) uf_union(P, u, A[e]);
+        e_done += I[u + 1] - I[u];
+    }
+    return e_done;
+}
+
 /* O2: BFS from each unlabelled vertex in increasing id order; the source is
  * the smallest id of its component because every smaller vertex is already
  * labelled.  Shares nothing with O1. */

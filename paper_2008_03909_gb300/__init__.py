@@ -1,0 +1,312 @@
+"""GB300-native ConnectIt connectivity: Python binding of ``libconnectit_gb``.
+
+Argument marshalling only: every step of the connectivity path runs in the
+library's CUDA kernels (``csrc/``).  PyTorch supplies device memory and
+streams.  The functions mirror the C ABI of ``include/connectit_gb.h``:
+
+* ``cc_static``            -- Algorithm 1 (sampling, IdentifyFrequent, finish)
+* ``cc_static_host``       -- the same on host buffers (copies included)
+* ``cc_sample`` / ``cc_identify_frequent`` / ``cc_finish`` -- its phases
+* ``Incremental``          -- ``cc_incr_create`` / ``_insert_batch`` /
+  ``_query_batch`` / ``_labels`` / ``_destroy``
+
+There is no CPU fallback: if the library cannot be loaded, or a tensor is
+not on a CUDA device, the call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libconnectit_gb.so")
+
+SAMPLE = {"none": 0, "kout": 1, "bfs": 2, "ldd": 3}
+FINISH = {"uf_rem_cas": 0, "uf_async": 1, "sv": 2, "lt_prf": 3}
+FIND = {"naive": 0, "split": 1, "halve": 2}
+SPLICE = {"split_one": 0, "halve_one": 1}
+NONE = 0xFFFFFFFF
+
+STATUS = {0: "CC_OK", 1: "CC_ERR_INVALID", 2: "CC_ERR_OOM", 3: "CC_ERR_CUDA", 4: "CC_ERR_NONCONVERGED",
+          5: "CC_ERR_BAD_INPUT", 6: "CC_ERR_UNSUPPORTED"}
+
+
+class CCError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(status, status)}")
+        self.status = status
+
+
+class SampleOpt(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("k", ctypes.c_uint32), ("bfs_tries", ctypes.c_uint32),
+                ("ldd_beta", ctypes.c_float), ("seed", ctypes.c_uint64), ("freq_samples", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class FinishOpt(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("find", ctypes.c_int32), ("splice", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_uint64), ("ms", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("lmax", ctypes.c_uint32), ("sample_info", ctypes.c_int32), ("rounds", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("edges_finish", ctypes.c_uint64)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+_SIGS = {
+    "cc_default_opts": (None, [ctypes.POINTER(SampleOpt), ctypes.POINTER(FinishOpt)]),
+    "cc_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64,
+                                 ctypes.POINTER(SampleOpt), ctypes.POINTER(FinishOpt), ctypes.c_void_p,
+                                 ctypes.c_void_p]),
+    "cc_static_ex": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint32,
+                                    ctypes.c_uint64, ctypes.POINTER(SampleOpt), ctypes.POINTER(FinishOpt),
+                                    ctypes.c_void_p, ctypes.POINTER(Stats), ctypes.c_void_p]),
+    "cc_static_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint32,
+                                      ctypes.c_uint64, ctypes.POINTER(SampleOpt), ctypes.POINTER(FinishOpt),
+                                      ctypes.c_void_p, ctypes.c_void_p]),
+    "cc_sample": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64,
+                                 ctypes.POINTER(SampleOpt), ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
+                                 ctypes.c_void_p]),
+    "cc_identify_frequent": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64,
+                                            ctypes.c_void_p, ctypes.c_void_p]),
+    "cc_finish": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64,
+                                 ctypes.POINTER(FinishOpt), ctypes.c_uint32, ctypes.c_void_p,
+                                 ctypes.POINTER(ctypes.c_uint32), ctypes.c_void_p]),
+    "cc_incr_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint32,
+                                      ctypes.c_uint64, ctypes.POINTER(SampleOpt), ctypes.POINTER(FinishOpt),
+                                      ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "cc_incr_insert_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]),
+    "cc_incr_query_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
+                                           ctypes.c_void_p]),
+    "cc_incr_labels": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "cc_incr_num_vertices": (ctypes.c_uint32, [ctypes.c_void_p]),
+    "cc_incr_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "cc_device_error": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32)]),
+    "cc_set_iteration_cap": (None, [ctypes.c_uint64]),
+    "cc_profile_enable": (None, [ctypes.c_int]),
+    "cc_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "cc_launch_count": (ctypes.c_uint64, []),
+    "cc_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "cc_version": (ctypes.c_char_p, []),
+}
+
+
+def lib():
+    """Load (building first if needed) the CUDA library.  Raises if it cannot."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                from . import build as _b
+                _b.build()
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        raise CCError(status, what)
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _dev(t: torch.Tensor, dtypes, what: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what} must be a CUDA tensor (no CPU fallback)")
+    if t.dtype not in dtypes:
+        raise TypeError(f"{what}: dtype {t.dtype} not in {dtypes}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    return t
+
+
+def sample_opt(kind="kout", k=2, bfs_tries=3, ldd_beta=0.2, seed=1, freq_samples=0) -> SampleOpt:
+    return SampleOpt(SAMPLE[kind] if isinstance(kind, str) else kind, k, bfs_tries, ldd_beta, seed, freq_samples, 0)
+
+
+def finish_opt(kind="uf_rem_cas", find="naive", splice="split_one") -> FinishOpt:
+    return FinishOpt(FINISH[kind] if isinstance(kind, str) else kind, FIND[find] if isinstance(find, str) else find,
+                     SPLICE[splice] if isinstance(splice, str) else splice, 0)
+
+
+def _graph_args(offsets: torch.Tensor, edges: torch.Tensor):
+    _dev(offsets, (torch.int32, torch.int64), "offsets")
+    _dev(edges, (torch.int32,), "edges")
+    n = offsets.numel() - 1
+    return (ctypes.c_void_p(offsets.data_ptr()), 1 if offsets.dtype == torch.int64 else 0,
+            ctypes.c_void_p(edges.data_ptr() if edges.numel() else 0), n, edges.numel())
+
+
+def cc_static(offsets, edges, sample: SampleOpt | None = None, finish: FinishOpt | None = None,
+              labels_out: torch.Tensor | None = None, stream=None, stats: bool = False):
+    """Canonical min-id labels (int32 view of uint32) on the offsets' device.
+    With stats=True also returns a dict of counters (and synchronises)."""
+    Ip, u64, Ap, n, m = _graph_args(offsets, edges)
+    if labels_out is None:
+        labels_out = torch.empty(n, dtype=torch.int32, device=offsets.device)
+    _dev(labels_out, (torch.int32,), "labels_out")
+    so = sample if sample is not None else sample_opt()
+    fo = finish if finish is not None else finish_opt()
+    L = lib()
+    if stats:
+        st = Stats()
+        _check(L.cc_static_ex(Ip, u64, Ap, n, m, ctypes.byref(so), ctypes.byref(fo),
+                              ctypes.c_void_p(labels_out.data_ptr()), ctypes.byref(st), _stream(stream)),
+               "cc_static_ex")
+        return labels_out, {"lmax": st.lmax, "sample_info": st.sample_info, "rounds": st.rounds,
+                            "edges_finish": st.edges_finish}
+    _check(L.cc_static(Ip, u64, Ap, n, m, ctypes.byref(so), ctypes.byref(fo), ctypes.c_void_p(labels_out.data_ptr()),
+                       _stream(stream)), "cc_static")
+    return labels_out
+
+
+def cc_static_host(offsets: torch.Tensor, edges: torch.Tensor, sample=None, finish=None,
+                   labels_out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """cc_static on host (ideally pinned) tensors; copies inside the call."""
+    for t, nm in ((offsets, "offsets"), (edges, "edges")):
+        if t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{nm} must be a contiguous host tensor")
+    n = offsets.numel() - 1
+    if labels_out is None:
+        labels_out = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    so = sample if sample is not None else sample_opt()
+    fo = finish if finish is not None else finish_opt()
+    _check(lib().cc_static_host(ctypes.c_void_p(offsets.data_ptr()), 1 if offsets.dtype == torch.int64 else 0,
+                                ctypes.c_void_p(edges.data_ptr() if edges.numel() else 0), n, edges.numel(),
+                                ctypes.byref(so), ctypes.byref(fo), ctypes.c_void_p(labels_out.data_ptr()),
+                                _stream(stream)), "cc_static_host")
+    return labels_out
+
+
+def cc_sample(offsets, edges, sample: SampleOpt | None = None, labels_out=None, stream=None):
+    """Sampled labels (min-rooted stars) and the sampling info (BFS try / LDD rounds)."""
+    Ip, u64, Ap, n, m = _graph_args(offsets, edges)
+    if labels_out is None:
+        labels_out = torch.empty(n, dtype=torch.int32, device=offsets.device)
+    info = ctypes.c_int32(0)
+    so = sample if sample is not None else sample_opt()
+    _check(lib().cc_sample(Ip, u64, Ap, n, m, ctypes.byref(so), ctypes.c_void_p(labels_out.data_ptr()),
+                           ctypes.byref(info), _stream(stream)), "cc_sample")
+    return labels_out, info.value
+
+
+def cc_identify_frequent(labels: torch.Tensor, freq_samples: int = 0, seed: int = 1, out=None, stream=None):
+    _dev(labels, (torch.int32,), "labels")
+    if out is None:
+        out = torch.empty(1, dtype=torch.int32, device=labels.device)
+    _check(lib().cc_identify_frequent(ctypes.c_void_p(labels.data_ptr()), labels.numel(), freq_samples, seed,
+                                      ctypes.c_void_p(out.data_ptr()), _stream(stream)), "cc_identify_frequent")
+    return out
+
+
+def cc_finish(offsets, edges, labels_inout: torch.Tensor, lmax: int, finish: FinishOpt | None = None, stream=None):
+    Ip, u64, Ap, n, m = _graph_args(offsets, edges)
+    _dev(labels_inout, (torch.int32,), "labels_inout")
+    fo = finish if finish is not None else finish_opt()
+    rounds = ctypes.c_uint32(0)
+    _check(lib().cc_finish(Ip, u64, Ap, n, m, ctypes.byref(fo), lmax & 0xFFFFFFFF,
+                           ctypes.c_void_p(labels_inout.data_ptr()), ctypes.byref(rounds), _stream(stream)),
+           "cc_finish")
+    return labels_inout, rounds.value
+
+
+def device_error(stream=None) -> int:
+    """Synchronise the stream and read-and-clear the sticky device error bits."""
+    bits = ctypes.c_uint32(0)
+    lib().cc_device_error(_stream(stream), ctypes.byref(bits))
+    return bits.value
+
+
+def set_iteration_cap(cap: int):
+    lib().cc_set_iteration_cap(cap)
+
+
+def launch_count() -> int:
+    """Kernel launches the library has made in this process."""
+    return int(lib().cc_launch_count())
+
+
+def profile_enable(on: bool = True):
+    lib().cc_profile_enable(1 if on else 0)
+
+
+def profile_read() -> dict:
+    """{kernel: (launches, total_ms)} since profiling was enabled."""
+    L = lib()
+    cnt = L.cc_profile_read(None, 0)
+    arr = (KernelTime * max(cnt, 1))()
+    cnt = L.cc_profile_read(ctypes.cast(arr, ctypes.c_void_p), cnt)
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].ms)) for i in range(cnt)}
+
+
+class Incremental:
+    """Resident union-find for batch-incremental connectivity."""
+
+    def __init__(self, n: int, offsets=None, edges=None, sample=None, finish=None, stream=None, device=None):
+        self._h = ctypes.c_void_p(0)
+        so = sample if sample is not None else sample_opt()
+        fo = finish if finish is not None else finish_opt()
+        if offsets is not None:
+            Ip, u64, Ap, n2, m = _graph_args(offsets, edges)
+            assert n2 == n
+            self.device = offsets.device
+        else:
+            Ip, u64, Ap, m = ctypes.c_void_p(0), 0, ctypes.c_void_p(0), 0
+            self.device = torch.device(device or "cuda")
+        _check(lib().cc_incr_create(Ip, u64, Ap, n, m, ctypes.byref(so), ctypes.byref(fo), _stream(stream),
+                                    ctypes.byref(self._h)), "cc_incr_create")
+        self.n = n
+
+    def insert(self, pairs: torch.Tensor, stream=None):
+        _dev(pairs, (torch.int32,), "pairs")
+        _check(lib().cc_incr_insert_batch(self._h, ctypes.c_void_p(pairs.data_ptr()), pairs.numel() // 2,
+                                          _stream(stream)), "cc_incr_insert_batch")
+
+    def query(self, pairs: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        _dev(pairs, (torch.int32,), "pairs")
+        q = pairs.numel() // 2
+        if out is None:
+            out = torch.empty(q, dtype=torch.uint8, device=pairs.device)
+        _check(lib().cc_incr_query_batch(self._h, ctypes.c_void_p(pairs.data_ptr()), q,
+                                         ctypes.c_void_p(out.data_ptr()), _stream(stream)), "cc_incr_query_batch")
+        return out
+
+    def labels(self, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty(self.n, dtype=torch.int32, device=self.device)
+        _check(lib().cc_incr_labels(self._h, ctypes.c_void_p(out.data_ptr()), _stream(stream)), "cc_incr_labels")
+        return out
+
+    def close(self):
+        if self._h:
+            lib().cc_incr_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

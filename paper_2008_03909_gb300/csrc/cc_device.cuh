@@ -1,0 +1,353 @@
+// cc_device.cuh -- device primitives shared by the connectivity kernels:
+// relaxed loads, bounded loops, counter-based draws, the union-find engines
+// of Section 3.3.1 (Algorithms 8-10 and 14) and the degree-binned edge
+// traversal every edge-processing kernel uses.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cooperative_groups.h>
+
+namespace ccg {
+
+constexpr uint32_t NONE = 0xFFFFFFFFu;
+constexpr uint32_t ERR_BAD_EDGE = 1u;
+constexpr uint32_t ERR_BAD_OFFSETS = 2u;
+constexpr uint32_t ERR_NONCONVERGED = 4u;
+constexpr uint64_t OP_TIME_LIMIT_NS = 4000000000ull;  // one find/union may run 4 s at most
+
+enum { FIND_NAIVE = 0, FIND_SPLIT = 1, FIND_HALVE = 2 };
+enum { SPLICE_SPLIT_ONE = 0, SPLICE_HALVE_ONE = 1 };
+
+// Degree binning: vertices of degree <= LIGHT_MAX are handled by one thread;
+// the edges of heavier vertices are cut into chunks of <= CHUNK edges, each
+// handled by one warp, so a hub with millions of edges spreads over the grid.
+constexpr uint32_t LIGHT_MAX = 32;
+constexpr uint32_t CHUNK = 2048;
+
+// Per-launch context passed by value.
+struct Dev {
+    uint32_t *err;   // per-device sticky error word (CC_DEVERR_* bits)
+    uint64_t cap;    // iteration cap of one device loop
+};
+
+// ---------------------------------------------------------------- loads
+// A relaxed, device-scope load of a parent slot: sees other SMs' writes
+// (the starred reads of Algorithms 8, 9 and 14 are such loads).
+__device__ __forceinline__ uint32_t ld_rel(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+// Streamed read-only input (CSR edges): evict-first in L1 and L2 so the
+// parent array keeps the cache.
+__device__ __forceinline__ uint32_t ld_stream(const uint32_t *p) { return __ldcs(p); }
+template <typename T>
+__device__ __forceinline__ T ld_off(const T *p) { return __ldg(p); }
+
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounds one device loop by an iteration cap and a wall-clock limit; when
+// either is reached it records ERR_NONCONVERGED and tells the loop to stop.
+struct Guard {
+    uint64_t it = 0, t0 = 0;
+    __device__ __forceinline__ bool step(const Dev &d) {
+        if (++it > d.cap) { atomicOr(d.err, ERR_NONCONVERGED); return false; }
+        if ((it & 1023) == 0) {
+            uint64_t t = gtimer();
+            if (t0 == 0) t0 = t;
+            else if (t - t0 > OP_TIME_LIMIT_NS) { atomicOr(d.err, ERR_NONCONVERGED); return false; }
+        }
+        return true;
+    }
+};
+
+// ---------------------------------------------------------------- draws
+// Counter-based draws: the ctr-th output of a SplitMix64 sequence started at
+// state s (Steele, Lea, Flood, OOPSLA 2014), mix64(s + (ctr+1) * gamma).
+__host__ __device__ __forceinline__ uint64_t draw64(uint64_t s, uint64_t ctr) {
+    uint64_t z = s + (ctr + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+constexpr uint64_t TAG_KOUT = 0x6B6F7574ull;
+constexpr uint64_t TAG_FREQ = 0x66726571ull;
+constexpr uint64_t TAG_BFS = 0x62667373ull;
+
+// ---------------------------------------------------------------- finds
+// Root of x given px = P[x] (Algorithm 8): FindNaive follows parents;
+// FindAtomicSplit points each visited node at its grandparent and moves to
+// the parent; FindAtomicHalve does the same and moves to the grandparent.
+template <int FIND>
+__device__ __forceinline__ uint32_t find_from(uint32_t *P, uint32_t x, uint32_t px, const Dev &d) {
+    Guard g;
+    if (FIND == FIND_NAIVE) {
+        while (px != x) {
+            x = px;
+            px = ld_rel(P + x);
+            if (!g.step(d)) break;
+        }
+        return x;
+    } else if (FIND == FIND_SPLIT) {
+        uint32_t v = px;
+        if (v == x) return x;
+        uint32_t w = ld_rel(P + v);
+        while (v != w) {
+            atomicCAS(P + x, v, w);
+            x = v;
+            v = w;
+            w = ld_rel(P + v);
+            if (!g.step(d)) break;
+        }
+        return v;
+    } else {
+        uint32_t v = px;
+        if (v == x) return x;
+        uint32_t w = ld_rel(P + v);
+        while (v != w) {
+            atomicCAS(P + x, v, w);
+            x = w;
+            v = ld_rel(P + x);
+            if (v == x) return x;
+            w = ld_rel(P + v);
+            if (!g.step(d)) break;
+        }
+        return v;
+    }
+}
+
+// ---------------------------------------------------------------- unions
+// Both engines keep P[x] <= x: a root is only ever linked under a smaller
+// id, so every root is the minimum of its tree and the final roots are the
+// canonical labels.  pu = P[u] and pv = P[v] are passed in already loaded
+// (callers batch those loads); pu == pv means nothing to do.
+
+// UF-Async (Algorithm 10; the CAS is on the larger root's own slot): find
+// both roots, CAS the larger root under the smaller, retry from the current
+// roots if another thread linked first.
+template <int FIND>
+struct UnionAsync {
+    static constexpr int find_kind = FIND;
+    __device__ static __forceinline__ bool unite(uint32_t *P, uint32_t u, uint32_t v, uint32_t pu,
+                                                 uint32_t pv, const Dev &d) {
+        uint32_t ru = find_from<FIND>(P, u, pu, d);
+        uint32_t rv = find_from<FIND>(P, v, pv, d);
+        Guard g;
+        while (ru != rv) {
+            if (ru < rv) { uint32_t t = ru; ru = rv; rv = t; }
+            uint32_t old = atomicCAS(P + ru, ru, rv);
+            if (old == ru) return true;
+            ru = find_from<FIND>(P, ru, old, d);
+            rv = find_from<FIND>(P, rv, ld_rel(P + rv), d);
+            if (!g.step(d)) return false;
+        }
+        return false;
+    }
+};
+
+// UF-Rem-CAS (Algorithm 14): walk r_u, r_v upward comparing parents; when
+// the side with the larger parent is a root, CAS it under the other side's
+// parent; otherwise take one splice step there (SplitAtomicOne: compact one
+// link and move to the parent; HalveAtomicOne: compact and move to the
+// grandparent, Algorithm 9).  After a successful link the optional Compress
+// (FindAtomicSplit / FindAtomicHalve) runs from both endpoints.
+template <int SPLICE, int FIND>
+struct UnionRem {
+    static constexpr int find_kind = FIND;
+    __device__ static __forceinline__ bool unite(uint32_t *P, uint32_t u, uint32_t v, uint32_t pu,
+                                                 uint32_t pv, const Dev &d) {
+        uint32_t ru = u, rv = v, pru = pu, prv = pv;
+        Guard g;
+        while (pru != prv) {
+            if (pru < prv) {
+                uint32_t t = ru; ru = rv; rv = t;
+                t = pru; pru = prv; prv = t;
+            }
+            if (ru == pru) {
+                uint32_t old = atomicCAS(P + ru, ru, prv);
+                if (old == ru) {
+                    if (FIND != FIND_NAIVE) {
+                        find_from<FIND>(P, u, ld_rel(P + u), d);
+                        find_from<FIND>(P, v, ld_rel(P + v), d);
+                    }
+                    return true;
+                }
+                pru = old;
+            } else if (SPLICE == SPLICE_SPLIT_ONE) {
+                uint32_t w = ld_rel(P + pru);
+                if (pru != w) atomicCAS(P + ru, pru, w);
+                ru = pru;
+                pru = w;
+            } else {
+                uint32_t w = ld_rel(P + pru);
+                if (pru != w) {
+                    atomicCAS(P + ru, pru, w);
+                    ru = w;
+                    pru = ld_rel(P + w);
+                } else {
+                    ru = pru;
+                }
+            }
+            if (!g.step(d)) return false;
+        }
+        return false;
+    }
+};
+
+// ---------------------------------------------------------------- CSR ranges
+template <typename OffT>
+__device__ __forceinline__ void vertex_range(const OffT *I, uint32_t u, uint64_t m, uint64_t &b,
+                                             uint64_t &e, const Dev &d) {
+    uint64_t s = (uint64_t)ld_off(I + u), t = (uint64_t)ld_off(I + u + 1);
+    if (t > m || s > t) {
+        atomicOr(d.err, ERR_BAD_OFFSETS);
+        if (t > m) t = m;
+        if (s > t) s = t;
+    }
+    b = s;
+    e = t;
+}
+
+// Exclusive append for a whole warp: EVERY lane of the warp must call it
+// (lanes with nothing to add pass 0).  Returns this lane's first slot.
+__device__ __forceinline__ uint32_t warp_append_full(uint32_t *counter, uint32_t count) {
+    const int lane = threadIdx.x & 31;
+    uint32_t incl = count;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    uint32_t base = 0;
+    if (lane == 31 && total) base = atomicAdd(counter, total);
+    base = __shfl_sync(0xFFFFFFFFu, base, 31);
+    return base + incl - count;
+}
+
+// Append one item from whichever lanes are active here (aggregated atomic).
+__device__ __forceinline__ uint32_t append_one(uint32_t *counter) {
+    cooperative_groups::coalesced_group g = cooperative_groups::coalesced_threads();
+    uint32_t base = 0;
+    if (g.thread_rank() == 0) base = atomicAdd(counter, g.size());
+    return g.shfl(base, 0) + g.thread_rank();
+}
+
+// ---------------------------------------------------------------- edge maps
+// Edge functors provide
+//   bool begin(u)                 -- false: skip u's edges (unused by callers here)
+//   void apply4(u, v[4], ok[4])   -- apply up to four edges (u, v_j) of one vertex
+// and are run over a vertex's edges in groups of four for memory-level
+// parallelism.  Bad edge ids (>= n) are dropped and flagged here.
+
+template <class F>
+__device__ __forceinline__ void light_edges(uint32_t u, uint64_t b, uint64_t e, const uint32_t *A,
+                                            uint32_t n, F &f, const Dev &d) {
+    for (uint64_t x = b; x < e; x += 4) {
+        uint32_t v[4];
+        bool ok[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            ok[j] = x + j < e;
+            v[j] = ok[j] ? ld_stream(A + x + j) : u;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (ok[j] && v[j] >= n) { atomicOr(d.err, ERR_BAD_EDGE); ok[j] = false; }
+        f.apply4(u, v, ok);
+    }
+}
+
+// One warp applies f to edges [b, e) of vertex u (e - b <= CHUNK).
+template <class F>
+__device__ __forceinline__ void warp_chunk_edges(uint32_t u, uint64_t b, uint64_t e,
+                                                 const uint32_t *A, uint32_t n, F &f, const Dev &d) {
+    const int lane = threadIdx.x & 31;
+    for (uint64_t x = b + lane; x < e; x += 128) {
+        uint32_t v[4];
+        bool ok[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            ok[j] = x + 32 * j < e;
+            v[j] = ok[j] ? ld_stream(A + x + 32 * j) : u;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (ok[j] && v[j] >= n) { atomicOr(d.err, ERR_BAD_EDGE); ok[j] = false; }
+        f.apply4(u, v, ok);
+    }
+}
+
+struct ChunkRef {
+    uint32_t u;   // vertex
+    uint32_t c;   // chunk index: edges [I[u] + c*CHUNK, min(I[u+1], I[u] + (c+1)*CHUNK))
+};
+
+// Chunk list capacity for a graph with m directed edges and n vertices:
+// each vertex of degree > LIGHT_MAX gives ceil(deg / CHUNK) chunks.
+__host__ __device__ inline uint64_t chunk_capacity(uint64_t n, uint64_t m) {
+    uint64_t heavy = m / (LIGHT_MAX + 1);
+    if (heavy > n) heavy = n;
+    return heavy + m / CHUNK + 1;
+}
+
+// Record the nc chunks of vertex u at slots [slot, slot + nc).
+__device__ __forceinline__ void write_chunks(ChunkRef *chunks, uint64_t cap, uint32_t slot, uint32_t nc,
+                                             uint32_t u, const Dev &d) {
+    if ((uint64_t)slot + nc > cap) { atomicOr(d.err, ERR_NONCONVERGED); return; }
+    for (uint32_t c = 0; c < nc; ++c) chunks[slot + c] = ChunkRef{u, c};
+}
+
+// Warps of the grid walk the chunk list [0, min(*count, cap)) (the count
+// can pass the capacity only on malformed offsets, which is flagged).
+template <typename OffT, class F>
+__device__ __forceinline__ void run_chunks(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m,
+                                           const ChunkRef *chunks, const uint32_t *count, uint64_t cap, F &f,
+                                           const Dev &d) {
+    const uint32_t total = (uint32_t)((uint64_t)*count < cap ? (uint64_t)*count : cap);
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t i = warp; i < total; i += nwarps) {
+        ChunkRef c = chunks[i];
+        uint64_t b, e;
+        vertex_range(I, c.u, m, b, e, d);
+        uint64_t cb = b + (uint64_t)c.c * CHUNK;
+        uint64_t ce = cb + CHUNK < e ? cb + CHUNK : e;
+        if (cb < ce) warp_chunk_edges(c.u, cb, ce, A, n, f, d);
+    }
+}
+
+// ---------------------------------------------------------------- functors
+// Union-find finish / sampling edge: apply Union(u, v) with the engine E.
+// lower_only: apply only edges to smaller neighbours (each undirected edge is
+// stored twice; used when no vertex is skipped, so the reverse copy exists).
+template <class E>
+struct UnionEdge {
+    uint32_t *P;
+    Dev d;
+    bool lower_only;
+    __device__ __forceinline__ void apply4(uint32_t u, const uint32_t (&v)[4], const bool (&ok)[4]) {
+        bool act[4];
+        uint32_t pv[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) act[j] = ok[j] && v[j] != u && (!lower_only || v[j] < u);
+        if (!(act[0] | act[1] | act[2] | act[3])) return;
+        uint32_t pu = ld_rel(P + u);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) pv[j] = act[j] ? ld_rel(P + v[j]) : pu;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (act[j] && pv[j] != pu) {
+                E::unite(P, u, v[j], pu, pv[j], d);
+                pu = ld_rel(P + u);
+            }
+        }
+    }
+    __device__ __forceinline__ void flush() {}
+};
+
+}  // namespace ccg

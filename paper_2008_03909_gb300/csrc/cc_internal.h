@@ -1,0 +1,114 @@
+// cc_internal.h -- host-side helpers shared by the library's translation
+// units (not part of the public ABI).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "connectit_gb.h"
+#include "cc_device.cuh"
+
+namespace ccg {
+
+// Per-device facts the launches need.
+struct DeviceInfo {
+    int device = -1;
+    int sms = 0;
+    uint32_t *err = nullptr;   // device address of the sticky error word
+};
+
+// Info for the current device (initialised once per device, thread safe).
+// Returns nullptr if the CUDA runtime fails.
+const DeviceInfo *device_info();
+
+// Iteration cap for one device loop on a graph of n vertices, and the cap on
+// rounds of the host-driven round loops (SV, LT, BFS levels).
+uint64_t loop_cap(uint64_t n);
+uint32_t round_cap();
+
+inline Dev make_dev(const DeviceInfo *di, uint64_t n) { return Dev{di->err, loop_cap(n)}; }
+
+cc_status from_cuda(cudaError_t e);
+
+// Grid for a loop over `work` items with `threads` per block, capped at a
+// few waves (kernels grid-stride beyond that).
+inline unsigned grid_for(const DeviceInfo *di, uint64_t work, unsigned threads, unsigned waves = 8) {
+    uint64_t b = (work + threads - 1) / threads;
+    uint64_t cap = (uint64_t)di->sms * waves;
+    if (b > cap) b = cap;
+    if (b == 0) b = 1;
+    return (unsigned)b;
+}
+
+// One stream-ordered scratch block carved into aligned pieces.
+class Scratch {
+  public:
+    // Reserve `bytes` (256-byte aligned); returns the offset.
+    size_t reserve(size_t bytes) {
+        size_t off = total_;
+        total_ += (bytes + 255) & ~size_t(255);
+        return off;
+    }
+    cc_status alloc(cudaStream_t s) {
+        if (total_ == 0) return CC_OK;
+        cudaError_t e = cudaMallocAsync(&base_, total_, s);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            base_ = nullptr;
+            return CC_ERR_OOM;
+        }
+        stream_ = s;
+        return CC_OK;
+    }
+    template <typename T>
+    T *at(size_t off) const { return reinterpret_cast<T *>(static_cast<char *>(base_) + off); }
+    void release() {
+        if (base_) cudaFreeAsync(base_, stream_);
+        base_ = nullptr;
+    }
+    ~Scratch() { release(); }
+    size_t total() const { return total_; }
+
+  private:
+    size_t total_ = 0;
+    void *base_ = nullptr;
+    cudaStream_t stream_ = nullptr;
+};
+
+// Control block of one call, in device memory.
+struct Ctl {
+    uint32_t nchunks;
+    uint32_t nlight;
+    uint32_t changed;
+    uint32_t minv;
+    uint32_t nfront[2];
+    uint32_t last_round;
+    uint32_t lmax;
+    unsigned long long key;
+    unsigned long long edges;
+    unsigned long long mf[2];
+    uint32_t pad[16];
+};
+
+// Launch accounting: one scope per kernel launch.  Counts every launch and,
+// while profiling is enabled, brackets it with CUDA events on its stream.
+class LaunchScope {
+  public:
+    LaunchScope(const char *name, cudaStream_t s);
+    ~LaunchScope();
+
+  private:
+    const char *name_;
+    cudaStream_t s_;
+    cudaEvent_t e0_ = nullptr, e1_ = nullptr;
+};
+#define CC_CAT2(a, b) a##b
+#define CC_CAT(a, b) CC_CAT2(a, b)
+#define CC_PROF(name, stream) ::ccg::LaunchScope CC_CAT(cc_prof_, __LINE__)(name, stream)
+
+// Validation shared by the entry points (host side, synchronous).
+cc_status check_graph(const void *offsets, int offsets_u64, const uint32_t *edges, uint32_t n, uint64_t m);
+cc_status check_sample(const cc_sample_opt &s);
+cc_status check_finish(const cc_finish_opt &f);
+
+}  // namespace ccg

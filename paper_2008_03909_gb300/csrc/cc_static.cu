@@ -1,0 +1,1208 @@
+// cc_static.cu -- static connectivity, Algorithm 1: labels <- identity,
+// SampleComponents (k-out / BFS / LDD, Section 3.2, Algorithms 4-6),
+// IdentifyFrequent, FinishComponents (union-find, Algorithm 7 with the
+// engines of Algorithms 8-10 and 14; Shiloach-Vishkin, Algorithm 15;
+// Liu-Tarjan PRF, Appendix D) and a final shortcut to min-id labels.
+//
+// The parent array P is the caller's labels_out buffer throughout.  Every
+// kernel grid-strides; edge work is degree-binned (cc_device.cuh) so that a
+// hub's edges spread over many warps.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "cc_internal.h"
+
+using namespace ccg;
+
+namespace {
+
+constexpr unsigned TPB = 256;
+
+// ================================================================ kernels
+__global__ void k_iota(uint32_t *P, uint32_t n) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        P[i] = (uint32_t)i;
+}
+
+__global__ void k_set_u32(uint32_t *p, uint32_t v) { *p = v; }
+__global__ void k_or_u32(uint32_t *p, uint32_t v) { atomicOr(p, v); }
+
+// Labels handed in by a caller must be a forest with P[v] <= v (sampled
+// labels as cc_sample writes them satisfy it).  Out-of-range or increasing
+// entries are flagged and reset to v so that every walk stays in bounds.
+__global__ void k_check_forest(uint32_t *P, uint32_t n, Dev d) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t p = P[i];
+        if (p > i) {
+            atomicOr(d.err, ERR_BAD_EDGE);
+            P[i] = (uint32_t)i;
+        }
+    }
+}
+
+// Point every vertex straight at its root: the full compression of
+// Algorithm 4, the FullShortcut of Algorithm 15 / Appendix D, and the final
+// shortcut to canonical labels (roots are component minima).  prev, when
+// given, receives the new parents (the round-start snapshot of SV / LT).
+__global__ void k_shortcut(uint32_t *P, uint32_t *prev, uint32_t n, Dev d) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t v = (uint32_t)i;
+        uint32_t p = ld_rel(P + v);
+        uint32_t r = find_from<FIND_NAIVE>(P, v, p, d);
+        if (r != p) P[v] = r;
+        if (prev) prev[v] = r;
+    }
+}
+
+// ---------------------------------------------------------------- k-out
+// Algorithm 4: each vertex of degree > 0 picks its first edge and k-1
+// uniform random edges (with replacement; pick j of v draws
+// out(seed ^ TAG_KOUT, v*k + j)), and each picked edge is a Union.
+template <typename OffT, class E>
+__global__ void k_kout(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, uint32_t k,
+                       uint64_t seed, uint32_t *P, Dev d) {
+    UnionEdge<E> f{P, d, false};
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t v = (uint32_t)i;
+        uint64_t b, e;
+        vertex_range(I, v, m, b, e, d);
+        uint64_t deg = e - b;
+        if (deg == 0) continue;
+        for (uint32_t j0 = 0; j0 < k; j0 += 4) {
+            uint32_t w[4];
+            bool ok[4];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                uint32_t j = j0 + jj;
+                ok[jj] = j < k;
+                uint64_t off = 0;
+                if (ok[jj] && j > 0) off = ((draw64(seed ^ TAG_KOUT, (uint64_t)v * k + j) >> 32) * deg) >> 32;
+                w[jj] = ok[jj] ? ld_stream(A + b + off) : v;
+                if (ok[jj] && w[jj] >= n) { atomicOr(d.err, ERR_BAD_EDGE); ok[jj] = false; }
+            }
+            f.apply4(v, w, ok);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- IdentifyFrequent
+// Exact: count every label (warp-aggregated atomics on a count array), then
+// the arg-max with ties to the smallest label via a packed 64-bit max key
+// (count << 32 | ~label).
+__global__ void k_count_labels(const uint32_t *L, uint32_t n, uint32_t *cnt, Dev d) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t base = warp * 32; base < n; base += nw * 32) {
+        uint64_t v = base + lane;
+        uint32_t l = v < n ? L[v] : NONE;
+        if (l != NONE && l >= n) { atomicOr(d.err, ERR_BAD_EDGE); l = NONE; }
+        unsigned grp = __match_any_sync(0xFFFFFFFFu, l);
+        if (l != NONE && lane == __ffs(grp) - 1) atomicAdd(cnt + l, (uint32_t)__popc(grp));
+    }
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long y = __shfl_xor_sync(0xFFFFFFFFu, x, o);
+        x = y > x ? y : x;
+    }
+    return x;
+}
+
+__global__ void k_argmax_counts(const uint32_t *cnt, uint32_t n, unsigned long long *key) {
+    __shared__ unsigned long long s[32];
+    unsigned long long best = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t c = cnt[i];
+        if (c) {
+            unsigned long long k2 = ((unsigned long long)c << 32) | (uint32_t)~(uint32_t)i;
+            best = k2 > best ? k2 : best;
+        }
+    }
+    best = warp_max_u64(best);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        best = threadIdx.x < (blockDim.x >> 5) ? s[threadIdx.x] : 0;
+        best = warp_max_u64(best);
+        if (threadIdx.x == 0 && best) atomicMax(key, best);
+    }
+}
+
+__global__ void k_key_to_label(const unsigned long long *key, uint32_t *lmax) {
+    unsigned long long k = *key;
+    *lmax = k ? ~(uint32_t)(k & 0xFFFFFFFFull) : NONE;
+}
+
+// Estimate: the labels at S seeded positions out(seed ^ TAG_FREQ, i) mod n,
+// counted in one block (S <= 4096 fits in shared memory).
+__global__ void k_freq_sampled(const uint32_t *L, uint32_t n, uint32_t S, uint64_t seed, uint32_t *lmax) {
+    __shared__ uint32_t lab[4096];
+    __shared__ unsigned long long red[32];
+    for (uint32_t i = threadIdx.x; i < S; i += blockDim.x)
+        lab[i] = L[draw64(seed ^ TAG_FREQ, i) % n];
+    __syncthreads();
+    unsigned long long best = 0;
+    for (uint32_t i = threadIdx.x; i < S; i += blockDim.x) {
+        uint32_t l = lab[i], c = 0;
+        for (uint32_t j = 0; j < S; ++j) c += lab[j] == l;
+        unsigned long long k2 = ((unsigned long long)c << 32) | (uint32_t)~l;
+        best = k2 > best ? k2 : best;
+    }
+    best = warp_max_u64(best);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        best = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0;
+        best = warp_max_u64(best);
+        if (threadIdx.x == 0) *lmax = best ? ~(uint32_t)(best & 0xFFFFFFFFull) : NONE;
+    }
+}
+
+// ---------------------------------------------------------------- edge passes
+// Edge pass over a vertex range (union-find finish with nothing skipped, or
+// a skip test on P[u] == L_max): light vertices run in the calling thread;
+// heavier ones are cut into chunks for k_chunks.
+template <typename OffT, class F>
+__global__ void k_range_bin(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, const uint32_t *P,
+                            const uint32_t *lmax_p, F f, ChunkRef *chunks, uint32_t *nchunks,
+                            uint64_t cap, unsigned long long *edges, Dev d) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint32_t lmax = lmax_p ? *lmax_p : NONE;
+    unsigned long long my_edges = 0;
+    for (uint64_t base = warp * 32; base < n; base += nw * 32) {
+        uint32_t u = (uint32_t)(base + lane);
+        bool act = base + lane < n;
+        uint64_t b = 0, e = 0;
+        if (act && lmax != NONE && ld_rel(P + u) == lmax) act = false;
+        if (act) vertex_range(I, u, m, b, e, d);
+        uint64_t deg = e - b;
+        my_edges += deg;
+        uint32_t nc = deg > LIGHT_MAX ? (uint32_t)((deg + CHUNK - 1) / CHUNK) : 0;
+        uint32_t slot = warp_append_full(nchunks, nc);
+        if (nc) write_chunks(chunks, cap, slot, nc, u, d);
+        else if (deg) light_edges(u, b, e, A, n, f, d);
+    }
+    f.flush();
+    for (int o = 16; o > 0; o >>= 1) my_edges += __shfl_xor_sync(0xFFFFFFFFu, my_edges, o);
+    if (lane == 0 && edges && my_edges) atomicAdd(edges, my_edges);
+}
+
+template <typename OffT, class F>
+__global__ void k_chunks(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, const ChunkRef *chunks,
+                         const uint32_t *nchunks, uint64_t cap, F f, Dev d) {
+    run_chunks(I, A, n, m, chunks, nchunks, cap, f, d);
+    f.flush();
+}
+
+// Vertex list (BFS / LDD frontiers): light vertices inline, heavier ones to
+// the chunk list.
+template <typename OffT, class F>
+__global__ void k_list_bin(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, const uint32_t *list,
+                           const uint32_t *count, F f, ChunkRef *chunks, uint32_t *nchunks, uint64_t cap,
+                           Dev d) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint32_t total = *count;
+    for (uint64_t base = warp * 32; base < total; base += nw * 32) {
+        bool act = base + lane < total;
+        uint32_t u = act ? list[base + lane] : 0;
+        uint64_t b = 0, e = 0;
+        if (act) vertex_range(I, u, m, b, e, d);
+        uint64_t deg = e - b;
+        uint32_t nc = deg > LIGHT_MAX ? (uint32_t)((deg + CHUNK - 1) / CHUNK) : 0;
+        uint32_t slot = warp_append_full(nchunks, nc);
+        if (nc) write_chunks(chunks, cap, slot, nc, u, d);
+        else if (deg) light_edges(u, b, e, A, n, f, d);
+    }
+    f.flush();
+}
+
+// Candidates of SV / LT (Algorithm 15's candidate set): vertices whose
+// sampled label is not L_max and that have edges; light ones to a list,
+// heavy ones to the chunk list.  Built once, reused every round.
+template <typename OffT>
+__global__ void k_cand_bin(const OffT *I, uint32_t n, uint64_t m, const uint32_t *P, const uint32_t *lmax_p,
+                           uint32_t *light, uint32_t *nlight, ChunkRef *chunks, uint32_t *nchunks, uint64_t cap,
+                           unsigned long long *edges, Dev d) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint32_t lmax = lmax_p ? *lmax_p : NONE;
+    unsigned long long my_edges = 0;
+    for (uint64_t base = warp * 32; base < n; base += nw * 32) {
+        uint32_t u = (uint32_t)(base + lane);
+        bool act = base + lane < n;
+        uint64_t b = 0, e = 0;
+        if (act && lmax != NONE && P[u] == lmax) act = false;
+        if (act) vertex_range(I, u, m, b, e, d);
+        uint64_t deg = e - b;
+        my_edges += deg;
+        uint32_t isl = (deg > 0 && deg <= LIGHT_MAX) ? 1u : 0u;
+        uint32_t nc = deg > LIGHT_MAX ? (uint32_t)((deg + CHUNK - 1) / CHUNK) : 0;
+        uint32_t sl = warp_append_full(nlight, isl);
+        if (isl) light[sl] = u;
+        uint32_t sc = warp_append_full(nchunks, nc);
+        if (nc) write_chunks(chunks, cap, sc, nc, u, d);
+    }
+    for (int o = 16; o > 0; o >>= 1) my_edges += __shfl_xor_sync(0xFFFFFFFFu, my_edges, o);
+    if (lane == 0 && edges && my_edges) atomicAdd(edges, my_edges);
+}
+
+template <typename OffT, class F>
+__global__ void k_light_list(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, const uint32_t *list,
+                             const uint32_t *count, F f, Dev d) {
+    const uint32_t total = *count;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t u = list[i];
+        uint64_t b, e;
+        vertex_range(I, u, m, b, e, d);
+        light_edges(u, b, e, A, n, f, d);
+    }
+    f.flush();
+}
+
+// ---------------------------------------------------------------- SV / LT edge rules
+// Shiloach-Vishkin hook (Algorithm 15): l = min(P[u], P[v]), h = max; if
+// l != h and h was a root at the round's start, writeMin(P[h], l).
+struct SVEdge {
+    uint32_t *P;
+    const uint32_t *prev;
+    uint32_t *changed;
+    bool hit;
+    __device__ __forceinline__ void apply4(uint32_t u, const uint32_t (&v)[4], const bool (&ok)[4]) {
+        uint32_t pu = ld_rel(P + u);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (!ok[j]) continue;
+            uint32_t pv = ld_rel(P + v[j]);
+            uint32_t l = pu < pv ? pu : pv, h = pu < pv ? pv : pu;
+            if (l != h && __ldg(prev + h) == h) {
+                atomicMin(P + h, l);
+                hit = true;
+            }
+        }
+    }
+    __device__ __forceinline__ void flush() {
+        if (hit) *changed = 1u;
+    }
+};
+
+// Liu-Tarjan ParentConnect with RootUpdate (Appendix D): the parents of an
+// edge's endpoints are candidates for each other; x = P[u] takes y = P[v]
+// (and symmetrically) when y is smaller and x was a root at the round's
+// start.  A round changes something iff some writeMin lowered a parent.
+struct LTEdge {
+    uint32_t *P;
+    const uint32_t *prev;
+    uint32_t *changed;
+    bool hit;
+    __device__ __forceinline__ void apply4(uint32_t u, const uint32_t (&v)[4], const bool (&ok)[4]) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (!ok[j]) continue;
+            uint32_t x = ld_rel(P + u), y = ld_rel(P + v[j]);
+            if (y < x && __ldg(prev + x) == x) hit |= atomicMin(P + x, y) > y;
+            if (x < y && __ldg(prev + y) == y) hit |= atomicMin(P + y, x) > x;
+        }
+    }
+    __device__ __forceinline__ void flush() {
+        if (hit) *changed = 1u;
+    }
+};
+
+// ---------------------------------------------------------------- BFS sampling
+// Top-down step of the label-spreading BFS (Algorithm 5): claim unvisited
+// neighbours in the visited bitmap, label them with the source, queue them.
+struct BFSEdge {
+    uint32_t *P;
+    uint32_t *vis;
+    uint32_t *next;
+    uint32_t *nnext;
+    uint32_t *minv;
+    uint32_t src;
+    uint32_t my_min;
+    __device__ __forceinline__ void apply4(uint32_t, const uint32_t (&v)[4], const bool (&ok)[4]) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (!ok[j]) continue;
+            uint32_t w = v[j], bit = 1u << (w & 31);
+            uint32_t *word = vis + (w >> 5);
+            if (ld_rel(word) & bit) continue;
+            if (atomicOr(word, bit) & bit) continue;
+            P[w] = src;
+            next[append_one(nnext)] = w;
+            my_min = w < my_min ? w : my_min;
+        }
+    }
+    __device__ __forceinline__ void flush() {
+        if (my_min != NONE && my_min < ld_rel(minv)) atomicMin(minv, my_min);
+    }
+};
+
+// Bottom-up step: every unvisited vertex looks for a neighbour in the
+// frontier bitmap and stops at the first one.
+template <typename OffT>
+__global__ void k_bfs_pull(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, uint32_t *P, uint32_t *vis,
+                           const uint32_t *front_bm, uint32_t *next_bm, uint32_t src, uint32_t *nnext,
+                           unsigned long long *next_edges, uint32_t *minv, Dev d) {
+    uint32_t cnt = 0, mn = NONE;
+    unsigned long long me = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t w = (uint32_t)i, bit = 1u << (w & 31);
+        if (vis[w >> 5] & bit) continue;
+        uint64_t b, e;
+        vertex_range(I, w, m, b, e, d);
+        for (uint64_t x = b; x < e; ++x) {
+            uint32_t y = ld_stream(A + x);
+            if (y >= n) { atomicOr(d.err, ERR_BAD_EDGE); continue; }
+            if (front_bm[y >> 5] & (1u << (y & 31))) {
+                P[w] = src;
+                atomicOr(next_bm + (w >> 5), bit);
+                atomicOr(vis + (w >> 5), bit);
+                ++cnt;
+                me += e - b;
+                mn = w < mn ? w : mn;
+                break;
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+        me += __shfl_xor_sync(0xFFFFFFFFu, me, o);
+        uint32_t t = __shfl_xor_sync(0xFFFFFFFFu, mn, o);
+        mn = t < mn ? t : mn;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (cnt) atomicAdd(nnext, cnt);
+        if (me) atomicAdd(next_edges, me);
+        if (mn != NONE && mn < ld_rel(minv)) atomicMin(minv, mn);
+    }
+}
+
+// Degree sum of a vertex list (frontier edges, for the direction switch).
+template <typename OffT>
+__global__ void k_list_degrees(const OffT *I, uint64_t m, const uint32_t *list, const uint32_t *count,
+                               unsigned long long *out, Dev d) {
+    const uint32_t total = *count;
+    unsigned long long s = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t b, e;
+        vertex_range(I, list[i], m, b, e, d);
+        s += e - b;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
+}
+
+__global__ void k_list_to_bitmap(const uint32_t *list, const uint32_t *count, uint32_t *bm) {
+    const uint32_t total = *count;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t w = list[i];
+        atomicOr(bm + (w >> 5), 1u << (w & 31));
+    }
+}
+
+__global__ void k_bitmap_to_list(const uint32_t *bm, uint32_t n, uint32_t *list, uint32_t *count) {
+    const uint32_t words = (n + 31) / 32;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < words;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t w = bm[i];
+        if (!w) continue;
+        uint32_t c = __popc(w);
+        uint32_t base = atomicAdd(count, c);
+        while (w) {
+            int b = __ffs(w) - 1;
+            w &= w - 1;
+            list[base++] = (uint32_t)(i * 32 + b);
+        }
+    }
+}
+
+// Relabel the reached set to its smallest member (a min-rooted star).
+__global__ void k_bfs_relabel(uint32_t *P, const uint32_t *vis, uint32_t n, const uint32_t *minv) {
+    const uint32_t mn = *minv;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        if (vis[i >> 5] & (1u << (i & 31))) P[i] = mn;
+}
+
+// ---------------------------------------------------------------- LDD sampling
+// Round r of the clustering (Algorithm 6): every uncovered id in [s0, s1)
+// becomes a centre; then the frontier claims uncovered neighbours, the
+// smallest claiming centre id winning (candidates first, commit after).
+__global__ void k_ldd_wake(uint32_t s0, uint32_t s1, uint32_t *P, uint32_t *vis, uint32_t *front,
+                           uint32_t *nfront, uint32_t *last_round, uint32_t round) {
+    bool any = false;
+    for (uint64_t i = s0 + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < s1;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t v = (uint32_t)i, bit = 1u << (v & 31);
+        if (vis[v >> 5] & bit) continue;
+        atomicOr(vis + (v >> 5), bit);
+        P[v] = v;
+        front[append_one(nfront)] = v;
+        any = true;
+    }
+    if (any) atomicMax(last_round, round + 1);
+}
+
+struct LDDEdge {
+    const uint32_t *P;
+    const uint32_t *vis;
+    uint32_t *cand;
+    uint32_t *next;
+    uint32_t *nnext;
+    __device__ __forceinline__ void apply4(uint32_t u, const uint32_t (&v)[4], const bool (&ok)[4]) {
+        uint32_t c = P[u];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (!ok[j]) continue;
+            uint32_t w = v[j];
+            if (vis[w >> 5] & (1u << (w & 31))) continue;
+            if (ld_rel(cand + w) <= c) continue;
+            if (atomicMin(cand + w, c) == NONE) next[append_one(nnext)] = w;
+        }
+    }
+    __device__ __forceinline__ void flush() {}
+};
+
+__global__ void k_ldd_commit(uint32_t *P, uint32_t *vis, uint32_t *cand, const uint32_t *next,
+                             const uint32_t *nnext, uint32_t *last_round, uint32_t round) {
+    const uint32_t total = *nnext;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t w = next[i];
+        P[w] = cand[w];
+        cand[w] = NONE;
+        atomicOr(vis + (w >> 5), 1u << (w & 31));
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && total) atomicMax(last_round, round + 1);
+}
+
+// Relabel clusters to their smallest members: cmin[c] = min{v : P[v] = c}
+// (warp-grouped by cluster, one atomicMin per group, skipped when it cannot
+// lower the current value), then P[v] = cmin[P[v]].
+__global__ void k_cluster_min(const uint32_t *P, uint32_t n, uint32_t *cmin) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t base = warp * 32; base < n; base += nw * 32) {
+        uint64_t v = base + lane;
+        uint32_t c = v < n ? P[v] : NONE;
+        unsigned grp = __match_any_sync(0xFFFFFFFFu, c);
+        uint32_t mn = __reduce_min_sync(grp, (uint32_t)(v < n ? v : NONE));
+        if (c != NONE && lane == __ffs(grp) - 1 && mn < ld_rel(cmin + c)) atomicMin(cmin + c, mn);
+    }
+}
+
+__global__ void k_apply_cluster_min(uint32_t *P, uint32_t n, const uint32_t *cmin) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        P[i] = cmin[P[i]];
+}
+
+// ================================================================ host side
+struct Graph {
+    const void *I;
+    bool u64;
+    const uint32_t *A;
+    uint32_t n;
+    uint64_t m;
+};
+
+// Scratch layout of one call.
+struct Work {
+    Scratch sc;
+    size_t o_ctl = 0, o_chunks = 0, o_counts = 0, o_prev = 0, o_light = 0, o_vis = 0, o_q0 = 0, o_q1 = 0,
+           o_bm0 = 0, o_bm1 = 0, o_cand = 0;
+    bool has_counts = false, has_sv = false, has_bfs = false, has_ldd = false;
+    uint64_t chunk_cap = 0;
+    Ctl *ctl() const { return sc.at<Ctl>(o_ctl); }
+};
+
+void plan(Work &w, const Graph &g, int sample_kind, uint32_t freq_samples, int finish_kind, bool finish_phase) {
+    const uint64_t n = g.n;
+    w.o_ctl = w.sc.reserve(sizeof(Ctl));
+    w.chunk_cap = chunk_capacity(n, g.m);
+    w.o_chunks = w.sc.reserve(w.chunk_cap * sizeof(ChunkRef));
+    if (sample_kind != CC_SAMPLE_NONE && freq_samples == 0) {
+        w.has_counts = true;
+        w.o_counts = w.sc.reserve(n * 4);
+    }
+    if (finish_phase) w.o_light = w.sc.reserve(n * 4);
+    if (finish_phase && (finish_kind == CC_FINISH_SV || finish_kind == CC_FINISH_LT_PRF)) {
+        w.has_sv = true;
+        w.o_prev = w.sc.reserve(n * 4);
+    }
+    const uint64_t words = (n + 31) / 32;
+    if (sample_kind == CC_SAMPLE_BFS) {
+        w.has_bfs = true;
+        w.o_vis = w.sc.reserve(words * 4);
+        w.o_q0 = w.sc.reserve(n * 4);
+        w.o_q1 = w.sc.reserve(n * 4);
+        w.o_bm0 = w.sc.reserve(words * 4);
+        w.o_bm1 = w.sc.reserve(words * 4);
+    }
+    if (sample_kind == CC_SAMPLE_LDD) {
+        w.has_ldd = true;
+        w.o_vis = w.sc.reserve(words * 4);
+        w.o_q0 = w.sc.reserve(n * 4);
+        w.o_q1 = w.sc.reserve(n * 4);
+        w.o_cand = w.sc.reserve(n * 4);
+    }
+}
+
+#define CC_TRY(x)                                   \
+    do {                                            \
+        cudaError_t e__ = (x);                      \
+        if (e__ != cudaSuccess) return from_cuda(e__); \
+    } while (0)
+#define CC_LAUNCH() CC_TRY(cudaGetLastError())
+
+template <class Fn>
+cc_status with_engine(const cc_finish_opt &f, Fn &&fn) {
+    if (f.kind == CC_FINISH_UF_ASYNC) {
+        switch (f.find) {
+            case CC_FIND_NAIVE: return fn(UnionAsync<FIND_NAIVE>{});
+            case CC_FIND_SPLIT: return fn(UnionAsync<FIND_SPLIT>{});
+            default: return fn(UnionAsync<FIND_HALVE>{});
+        }
+    }
+    // UF-Rem-CAS; also the engine of k-out sampling under SV / LT finishes.
+    const int key = (f.kind == CC_FINISH_UF_REM_CAS ? f.splice : CC_SPLICE_SPLIT_ONE) * 3 +
+                    (f.kind == CC_FINISH_UF_REM_CAS ? f.find : CC_FIND_NAIVE);
+    switch (key) {
+        case 0: return fn(UnionRem<SPLICE_SPLIT_ONE, FIND_NAIVE>{});
+        case 1: return fn(UnionRem<SPLICE_SPLIT_ONE, FIND_SPLIT>{});
+        case 2: return fn(UnionRem<SPLICE_SPLIT_ONE, FIND_HALVE>{});
+        case 3: return fn(UnionRem<SPLICE_HALVE_ONE, FIND_NAIVE>{});
+        case 4: return fn(UnionRem<SPLICE_HALVE_ONE, FIND_SPLIT>{});
+        default: return fn(UnionRem<SPLICE_HALVE_ONE, FIND_HALVE>{});
+    }
+}
+
+// ---------------------------------------------------------------- phases
+template <typename OffT>
+cc_status bfs_sample(const Graph &g, const cc_sample_opt &so, uint32_t *P, Work &w, const DeviceInfo *di,
+                     const Dev &d, cudaStream_t s, int32_t *info) {
+    const OffT *I = static_cast<const OffT *>(g.I);
+    const uint32_t n = g.n;
+    const uint64_t words = (n + 31) / 32;
+    Ctl *ctl = w.ctl();
+    uint32_t *vis = w.sc.at<uint32_t>(w.o_vis);
+    uint32_t *q[2] = {w.sc.at<uint32_t>(w.o_q0), w.sc.at<uint32_t>(w.o_q1)};
+    uint32_t *bm[2] = {w.sc.at<uint32_t>(w.o_bm0), w.sc.at<uint32_t>(w.o_bm1)};
+    ChunkRef *chunks = w.sc.at<ChunkRef>(w.o_chunks);
+    const unsigned gv = grid_for(di, n, TPB);
+    // host-visible copies of the per-level counters
+    struct Lv {
+        uint32_t nnext;
+        uint32_t pad;
+        unsigned long long mf;
+    };
+    Lv *hl = nullptr;
+    CC_TRY(cudaMallocHost(&hl, sizeof(Lv)));
+    struct Free {
+        Lv *p;
+        ~Free() { cudaFreeHost(p); }
+    } fr{hl};
+    *info = -1;
+    for (uint32_t t = 0; t < so.bfs_tries; ++t) {
+        const uint32_t src = (uint32_t)(draw64(so.seed ^ TAG_BFS, t) % n);
+        {
+            CC_PROF("k_iota", s);
+            k_iota<<<gv, TPB, 0, s>>>(P, n);
+        }
+        CC_TRY(cudaMemsetAsync(vis, 0, words * 4, s));
+        CC_TRY(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+        {
+            CC_PROF("k_set_u32", s);
+            k_set_u32<<<1, 1, 0, s>>>(&ctl->minv, src);
+        }
+        {
+            CC_PROF("k_set_u32", s);
+            k_set_u32<<<1, 1, 0, s>>>(q[0], src);
+        }
+        {
+            CC_PROF("k_set_u32", s);
+            k_set_u32<<<1, 1, 0, s>>>(&ctl->nfront[0], 1);
+        }
+        {
+            CC_PROF("k_list_to_bitmap", s);
+            k_list_to_bitmap<<<1, 32, 0, s>>>(q[0], &ctl->nfront[0], vis);
+        }
+        CC_LAUNCH();
+        uint64_t reached = 1, nf = 1, explored_edges = 0;
+        int cur = 0;
+        bool pull = false;   // frontier kept as a bitmap (bm[cur]) when pulling
+        // frontier edge count of the source
+        CC_TRY(cudaMemsetAsync(&ctl->mf[0], 0, 8, s));
+        {
+            CC_PROF("k_list_degrees", s);
+            k_list_degrees<OffT><<<1, 32, 0, s>>>(I, g.m, q[0], &ctl->nfront[0], &ctl->mf[0], d);
+        }
+        CC_TRY(cudaMemcpyAsync(&hl->mf, &ctl->mf[0], 8, cudaMemcpyDeviceToHost, s));
+        CC_TRY(cudaStreamSynchronize(s));
+        uint64_t mf = hl->mf;
+        for (uint64_t level = 0; nf > 0 && level <= n; ++level) {
+            // Direction choice (Beamer et al.'s heuristic, as in
+            // direction-optimizing BFS): pull when the frontier's edges
+            // exceed 1/14 of the unexplored edges, push when the frontier
+            // is below n/24 vertices.
+            const uint64_t unexplored = g.m > explored_edges ? g.m - explored_edges : 0;
+            bool want_pull = pull ? (nf >= n / 24) : (mf > unexplored / 14);
+            if (want_pull && !pull) {
+                CC_TRY(cudaMemsetAsync(bm[cur], 0, words * 4, s));
+                {
+                    CC_PROF("k_list_to_bitmap", s);
+                    k_list_to_bitmap<<<gv, TPB, 0, s>>>(q[cur], &ctl->nfront[cur], bm[cur]);
+                }
+                CC_LAUNCH();
+            } else if (!want_pull && pull) {
+                CC_TRY(cudaMemsetAsync(&ctl->nfront[cur], 0, 4, s));
+                {
+                    CC_PROF("k_bitmap_to_list", s);
+                    k_bitmap_to_list<<<grid_for(di, words, TPB), TPB, 0, s>>>(bm[cur], n, q[cur], &ctl->nfront[cur]);
+                }
+                CC_LAUNCH();
+            }
+            pull = want_pull;
+            const int nx = cur ^ 1;
+            CC_TRY(cudaMemsetAsync(&ctl->nfront[nx], 0, 4, s));
+            CC_TRY(cudaMemsetAsync(&ctl->mf[nx], 0, 8, s));
+            if (pull) {
+                CC_TRY(cudaMemsetAsync(bm[nx], 0, words * 4, s));
+                {
+                    CC_PROF("k_bfs_pull", s);
+                    k_bfs_pull<OffT><<<gv, TPB, 0, s>>>(I, g.A, n, g.m, P, vis, bm[cur], bm[nx], src, &ctl->nfront[nx],
+                                                        &ctl->mf[nx], &ctl->minv, d);
+                }
+                CC_LAUNCH();
+            } else {
+                CC_TRY(cudaMemsetAsync(&ctl->nchunks, 0, 4, s));
+                BFSEdge f{P, vis, q[nx], &ctl->nfront[nx], &ctl->minv, src, NONE};
+                {
+                    CC_PROF("k_list_bin", s);
+                    k_list_bin<OffT, BFSEdge><<<gv, TPB, 0, s>>>(I, g.A, n, g.m, q[cur], &ctl->nfront[cur], f, chunks,
+                                                                 &ctl->nchunks, w.chunk_cap, d);
+                }
+                {
+                    CC_PROF("k_chunks", s);
+                    k_chunks<OffT, BFSEdge><<<grid_for(di, (uint64_t)1 << 40, TPB), TPB, 0, s>>>(
+                        I, g.A, n, g.m, chunks, &ctl->nchunks, w.chunk_cap, f, d);
+                }
+                {
+                    CC_PROF("k_list_degrees", s);
+                    k_list_degrees<OffT><<<gv, TPB, 0, s>>>(I, g.m, q[nx], &ctl->nfront[nx], &ctl->mf[nx], d);
+                }
+                CC_LAUNCH();
+            }
+            explored_edges += mf;
+            CC_TRY(cudaMemcpyAsync(&hl->nnext, &ctl->nfront[nx], 4, cudaMemcpyDeviceToHost, s));
+            CC_TRY(cudaMemcpyAsync(&hl->mf, &ctl->mf[nx], 8, cudaMemcpyDeviceToHost, s));
+            CC_TRY(cudaStreamSynchronize(s));
+            nf = hl->nnext;
+            mf = hl->mf;
+            reached += nf;
+            cur = nx;
+        }
+        // the most frequent label is the source's (count = reached)
+        if (10 * reached > (uint64_t)n) {
+            {
+                CC_PROF("k_bfs_relabel", s);
+                k_bfs_relabel<<<gv, TPB, 0, s>>>(P, vis, n, &ctl->minv);
+            }
+            CC_LAUNCH();
+            *info = (int32_t)t;
+            return CC_OK;
+        }
+    }
+    {
+        CC_PROF("k_iota", s);
+        k_iota<<<gv, TPB, 0, s>>>(P, n);
+    }
+    CC_LAUNCH();
+    return CC_OK;
+}
+
+template <typename OffT>
+cc_status ldd_sample(const Graph &g, const cc_sample_opt &so, uint32_t *P, Work &w, const DeviceInfo *di,
+                     const Dev &d, cudaStream_t s, int32_t *info) {
+    const OffT *I = static_cast<const OffT *>(g.I);
+    const uint32_t n = g.n;
+    const uint64_t words = (n + 31) / 32;
+    Ctl *ctl = w.ctl();
+    uint32_t *vis = w.sc.at<uint32_t>(w.o_vis);
+    uint32_t *q[2] = {w.sc.at<uint32_t>(w.o_q0), w.sc.at<uint32_t>(w.o_q1)};
+    uint32_t *cand = w.sc.at<uint32_t>(w.o_cand);
+    ChunkRef *chunks = w.sc.at<ChunkRef>(w.o_chunks);
+    const unsigned gv = grid_for(di, n, TPB);
+    const unsigned gc = grid_for(di, (uint64_t)1 << 40, TPB);
+    CC_TRY(cudaMemsetAsync(vis, 0, words * 4, s));
+    CC_TRY(cudaMemsetAsync(cand, 0xFF, (size_t)n * 4, s));
+    CC_TRY(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+    uint64_t S = 0;
+    int cur = 0;
+    uint32_t r = 0;
+    // Start schedule: round r starts the next floor(exp(beta r)) ids; the
+    // rounds run until every id has been started, by which time every
+    // vertex is covered.
+    for (; S < n; ++r) {
+        double x = std::floor(std::exp((double)so.ldd_beta * (double)r));
+        if (x < 1.0) x = 1.0;
+        if (x > 4294967295.0) x = 4294967295.0;
+        uint64_t S1 = std::min<uint64_t>(n, S + (uint64_t)x);
+        const int nx = cur ^ 1;
+        {
+            CC_PROF("k_ldd_wake", s);
+            k_ldd_wake<<<grid_for(di, S1 - S, TPB), TPB, 0, s>>>((uint32_t)S, (uint32_t)S1, P, vis, q[cur],
+                                                                  &ctl->nfront[cur], &ctl->last_round, r);
+        }
+        CC_TRY(cudaMemsetAsync(&ctl->nfront[nx], 0, 4, s));
+        CC_TRY(cudaMemsetAsync(&ctl->nchunks, 0, 4, s));
+        LDDEdge f{P, vis, cand, q[nx], &ctl->nfront[nx]};
+        {
+            CC_PROF("k_list_bin", s);
+            k_list_bin<OffT, LDDEdge><<<gv, TPB, 0, s>>>(I, g.A, n, g.m, q[cur], &ctl->nfront[cur], f, chunks,
+                                                         &ctl->nchunks, w.chunk_cap, d);
+        }
+        {
+            CC_PROF("k_chunks", s);
+            k_chunks<OffT, LDDEdge><<<gc, TPB, 0, s>>>(I, g.A, n, g.m, chunks, &ctl->nchunks, w.chunk_cap, f, d);
+        }
+        {
+            CC_PROF("k_ldd_commit", s);
+            k_ldd_commit<<<gv, TPB, 0, s>>>(P, vis, cand, q[nx], &ctl->nfront[nx], &ctl->last_round, r);
+        }
+        CC_TRY(cudaMemsetAsync(&ctl->nfront[cur], 0, 4, s));
+        CC_LAUNCH();
+        S = S1;
+        cur = nx;
+    }
+    // the last frontier may still claim: run expansion rounds until it is empty
+    for (uint32_t extra = 0; extra <= n; ++extra) {
+        uint32_t nf = 0;
+        CC_TRY(cudaMemcpyAsync(&nf, &ctl->nfront[cur], 4, cudaMemcpyDeviceToHost, s));
+        CC_TRY(cudaStreamSynchronize(s));
+        if (nf == 0) break;
+        const int nx = cur ^ 1;
+        CC_TRY(cudaMemsetAsync(&ctl->nfront[nx], 0, 4, s));
+        CC_TRY(cudaMemsetAsync(&ctl->nchunks, 0, 4, s));
+        LDDEdge f{P, vis, cand, q[nx], &ctl->nfront[nx]};
+        {
+            CC_PROF("k_list_bin", s);
+            k_list_bin<OffT, LDDEdge><<<gv, TPB, 0, s>>>(I, g.A, n, g.m, q[cur], &ctl->nfront[cur], f, chunks,
+                                                         &ctl->nchunks, w.chunk_cap, d);
+        }
+        {
+            CC_PROF("k_chunks", s);
+            k_chunks<OffT, LDDEdge><<<gc, TPB, 0, s>>>(I, g.A, n, g.m, chunks, &ctl->nchunks, w.chunk_cap, f, d);
+        }
+        {
+            CC_PROF("k_ldd_commit", s);
+            k_ldd_commit<<<gv, TPB, 0, s>>>(P, vis, cand, q[nx], &ctl->nfront[nx], &ctl->last_round, r);
+        }
+        CC_TRY(cudaMemsetAsync(&ctl->nfront[cur], 0, 4, s));
+        CC_LAUNCH();
+        cur = nx;
+        ++r;
+    }
+    // clusters -> min-id stars (cand is all NONE again and serves as cmin)
+    {
+        CC_PROF("k_cluster_min", s);
+        k_cluster_min<<<gv, TPB, 0, s>>>(P, n, cand);
+    }
+    {
+        CC_PROF("k_apply_cluster_min", s);
+        k_apply_cluster_min<<<gv, TPB, 0, s>>>(P, n, cand);
+    }
+    CC_LAUNCH();
+    uint32_t lr = 0;
+    CC_TRY(cudaMemcpyAsync(&lr, &ctl->last_round, 4, cudaMemcpyDeviceToHost, s));
+    CC_TRY(cudaStreamSynchronize(s));
+    *info = (int32_t)lr;
+    return CC_OK;
+}
+
+template <typename OffT>
+cc_status sample_phase(const Graph &g, const cc_sample_opt &so, const cc_finish_opt &fo, uint32_t *P, Work &w,
+                       const DeviceInfo *di, const Dev &d, cudaStream_t s, int32_t *info) {
+    const unsigned gv = grid_for(di, g.n, TPB);
+    *info = 0;
+    if (so.kind == CC_SAMPLE_BFS) return bfs_sample<OffT>(g, so, P, w, di, d, s, info);
+    if (so.kind == CC_SAMPLE_LDD) return ldd_sample<OffT>(g, so, P, w, di, d, s, info);
+    {
+        CC_PROF("k_iota", s);
+        k_iota<<<gv, TPB, 0, s>>>(P, g.n);
+    }
+    CC_LAUNCH();
+    if (so.kind == CC_SAMPLE_NONE) return CC_OK;
+    // k-out: union-find over the picked edges, then full compression
+    return with_engine(fo, [&](auto eng) -> cc_status {
+        using E = decltype(eng);
+        {
+            CC_PROF("k_kout", s);
+            k_kout<OffT, E><<<gv, TPB, 0, s>>>(static_cast<const OffT *>(g.I), g.A, g.n, g.m, so.k, so.seed, P, d);
+        }
+        {
+            CC_PROF("k_shortcut", s);
+            k_shortcut<<<gv, TPB, 0, s>>>(P, nullptr, g.n, d);
+        }
+        CC_LAUNCH();
+        return CC_OK;
+    });
+}
+
+cc_status identify_phase(const uint32_t *L, uint32_t n, uint32_t samples, uint64_t seed, uint32_t *lmax_out,
+                         Work &w, const DeviceInfo *di, const Dev &d, cudaStream_t s) {
+    if (samples) {
+        {
+            CC_PROF("k_freq_sampled", s);
+            k_freq_sampled<<<1, 1024, 0, s>>>(L, n, samples, seed, lmax_out);
+        }
+        CC_LAUNCH();
+        return CC_OK;
+    }
+    uint32_t *cnt = w.sc.at<uint32_t>(w.o_counts);
+    Ctl *ctl = w.ctl();
+    const unsigned gv = grid_for(di, n, TPB);
+    CC_TRY(cudaMemsetAsync(cnt, 0, (size_t)n * 4, s));
+    CC_TRY(cudaMemsetAsync(&ctl->key, 0, 8, s));
+    {
+        CC_PROF("k_count_labels", s);
+        k_count_labels<<<gv, TPB, 0, s>>>(L, n, cnt, d);
+    }
+    {
+        CC_PROF("k_argmax_counts", s);
+        k_argmax_counts<<<gv, TPB, 0, s>>>(cnt, n, &ctl->key);
+    }
+    {
+        CC_PROF("k_key_to_label", s);
+        k_key_to_label<<<1, 1, 0, s>>>(&ctl->key, lmax_out);
+    }
+    CC_LAUNCH();
+    return CC_OK;
+}
+
+// lmax_p: device pointer to L_max, or nullptr for "skip nothing".
+template <typename OffT>
+cc_status finish_phase(const Graph &g, const cc_finish_opt &fo, const uint32_t *lmax_p, uint32_t *P, Work &w,
+                       const DeviceInfo *di, const Dev &d, cudaStream_t s, uint32_t *rounds_out) {
+    const OffT *I = static_cast<const OffT *>(g.I);
+    const uint32_t n = g.n;
+    Ctl *ctl = w.ctl();
+    ChunkRef *chunks = w.sc.at<ChunkRef>(w.o_chunks);
+    const unsigned gv = grid_for(di, n, TPB);
+    const unsigned gc = grid_for(di, (uint64_t)1 << 40, TPB);
+    if (rounds_out) *rounds_out = 0;
+    CC_TRY(cudaMemsetAsync(&ctl->nchunks, 0, 4, s));
+    CC_TRY(cudaMemsetAsync(&ctl->edges, 0, 8, s));
+    uint32_t *light = w.sc.at<uint32_t>(w.o_light);
+    if (fo.kind == CC_FINISH_UF_REM_CAS || fo.kind == CC_FINISH_UF_ASYNC) {
+        // No vertex skipped: one pass, each undirected edge applied once
+        // (from its larger endpoint).  With L_max: the candidate set
+        // {u : label[u] != L_max} is fixed first (Algorithm 7's filter),
+        // then its edges are applied.
+        const bool lower_only = (lmax_p == nullptr);
+        if (!lower_only) {
+            CC_TRY(cudaMemsetAsync(&ctl->nlight, 0, 4, s));
+            {
+                CC_PROF("k_cand_bin", s);
+                k_cand_bin<OffT><<<gv, TPB, 0, s>>>(I, n, g.m, P, lmax_p, light, &ctl->nlight, chunks, &ctl->nchunks,
+                                                    w.chunk_cap, &ctl->edges, d);
+            }
+            CC_LAUNCH();
+        }
+        cc_status st = with_engine(fo, [&](auto eng) -> cc_status {
+            using E = decltype(eng);
+            UnionEdge<E> f{P, d, lower_only};
+            if (lower_only)
+                {
+                    CC_PROF("k_range_bin", s);
+                    k_range_bin<OffT, UnionEdge<E>><<<gv, TPB, 0, s>>>(I, g.A, n, g.m, P, nullptr, f, chunks,
+                                                                       &ctl->nchunks, w.chunk_cap, &ctl->edges, d);
+                }
+            else
+                {
+                    CC_PROF("k_light_list", s);
+                    k_light_list<OffT, UnionEdge<E>><<<gv, TPB, 0, s>>>(I, g.A, n, g.m, light, &ctl->nlight, f, d);
+                }
+            {
+                CC_PROF("k_chunks", s);
+                k_chunks<OffT, UnionEdge<E>><<<gc, TPB, 0, s>>>(I, g.A, n, g.m, chunks, &ctl->nchunks, w.chunk_cap, f, d);
+            }
+            CC_LAUNCH();
+            return CC_OK;
+        });
+        if (st != CC_OK) return st;
+        {
+            CC_PROF("k_shortcut", s);
+            k_shortcut<<<gv, TPB, 0, s>>>(P, nullptr, n, d);
+        }
+        CC_LAUNCH();
+        return CC_OK;
+    }
+    // SV / LT-PRF: candidate lists once, then rounds until nothing changes.
+    uint32_t *prev = w.sc.at<uint32_t>(w.o_prev);
+    CC_TRY(cudaMemsetAsync(&ctl->nlight, 0, 4, s));
+    {
+        CC_PROF("k_cand_bin", s);
+        k_cand_bin<OffT><<<gv, TPB, 0, s>>>(I, n, g.m, P, lmax_p, light, &ctl->nlight, chunks, &ctl->nchunks,
+                                            w.chunk_cap, &ctl->edges, d);
+    }
+    CC_TRY(cudaMemcpyAsync(prev, P, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+    CC_LAUNCH();
+    uint32_t *hchanged = nullptr;
+    CC_TRY(cudaMallocHost(&hchanged, 4));
+    struct Free {
+        uint32_t *p;
+        ~Free() { cudaFreeHost(p); }
+    } fr{hchanged};
+    const uint32_t cap = round_cap();
+    uint32_t rounds = 0;
+    for (;;) {
+        if (rounds >= cap) {
+            {
+                CC_PROF("k_or_u32", s);
+                k_or_u32<<<1, 1, 0, s>>>(di->err, CC_DEVERR_NONCONVERGED);
+            }
+            CC_LAUNCH();
+            break;
+        }
+        CC_TRY(cudaMemsetAsync(&ctl->changed, 0, 4, s));
+        if (fo.kind == CC_FINISH_SV) {
+            SVEdge f{P, prev, &ctl->changed, false};
+            {
+                CC_PROF("k_light_list", s);
+                k_light_list<OffT, SVEdge><<<gv, TPB, 0, s>>>(I, g.A, n, g.m, light, &ctl->nlight, f, d);
+            }
+            {
+                CC_PROF("k_chunks", s);
+                k_chunks<OffT, SVEdge><<<gc, TPB, 0, s>>>(I, g.A, n, g.m, chunks, &ctl->nchunks, w.chunk_cap, f, d);
+            }
+        } else {
+            LTEdge f{P, prev, &ctl->changed, false};
+            {
+                CC_PROF("k_light_list", s);
+                k_light_list<OffT, LTEdge><<<gv, TPB, 0, s>>>(I, g.A, n, g.m, light, &ctl->nlight, f, d);
+            }
+            {
+                CC_PROF("k_chunks", s);
+                k_chunks<OffT, LTEdge><<<gc, TPB, 0, s>>>(I, g.A, n, g.m, chunks, &ctl->nchunks, w.chunk_cap, f, d);
+            }
+        }
+        {
+            CC_PROF("k_shortcut", s);
+            k_shortcut<<<gv, TPB, 0, s>>>(P, prev, n, d);
+        }
+        CC_LAUNCH();
+        ++rounds;
+        CC_TRY(cudaMemcpyAsync(hchanged, &ctl->changed, 4, cudaMemcpyDeviceToHost, s));
+        CC_TRY(cudaStreamSynchronize(s));
+        if (*hchanged == 0) break;
+    }
+    if (rounds_out) *rounds_out = rounds;
+    return CC_OK;
+}
+
+void resolve_opts(const cc_sample_opt *sp, const cc_finish_opt *fp, cc_sample_opt &so, cc_finish_opt &fo) {
+    cc_default_opts(&so, &fo);
+    if (sp) so = *sp;
+    if (fp) fo = *fp;
+}
+
+template <typename OffT>
+cc_status run_static(const Graph &g, const cc_sample_opt &so, const cc_finish_opt &fo, uint32_t *P,
+                     cc_stats *stats, cudaStream_t s) {
+    const DeviceInfo *di = device_info();
+    if (!di) return CC_ERR_CUDA;
+    const Dev d = make_dev(di, g.n);
+    Work w;
+    plan(w, g, so.kind, so.freq_samples, fo.kind, true);
+    cc_status st = w.sc.alloc(s);
+    if (st != CC_OK) return st;
+    CC_TRY(cudaMemsetAsync(w.ctl(), 0, sizeof(Ctl), s));
+    int32_t info = 0;
+    st = sample_phase<OffT>(g, so, fo, P, w, di, d, s, &info);
+    if (st != CC_OK) return st;
+    const uint32_t *lmax_p = nullptr;
+    if (so.kind != CC_SAMPLE_NONE) {
+        st = identify_phase(P, g.n, so.freq_samples, so.seed, &w.ctl()->lmax, w, di, d, s);
+        if (st != CC_OK) return st;
+        lmax_p = &w.ctl()->lmax;
+    }
+    uint32_t rounds = 0;
+    st = finish_phase<OffT>(g, fo, lmax_p, P, w, di, d, s, &rounds);
+    if (st != CC_OK) return st;
+    if (stats) {
+        Ctl h;
+        CC_TRY(cudaMemcpyAsync(&h, w.ctl(), sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+        CC_TRY(cudaStreamSynchronize(s));
+        stats->lmax = lmax_p ? h.lmax : NONE;
+        stats->sample_info = info;
+        stats->rounds = rounds;
+        stats->reserved = 0;
+        stats->edges_finish = h.edges;
+    }
+    return CC_OK;
+}
+
+}  // namespace
+
+// ================================================================ C ABI
+extern "C" {
+
+cc_status cc_static_ex(const void *offsets, int offsets_u64, const uint32_t *edges, uint32_t n, uint64_t m,
+                       const cc_sample_opt *sample, const cc_finish_opt *finish, uint32_t *labels_out,
+                       cc_stats *stats, void *stream) {
+    cc_status st = check_graph(offsets, offsets_u64, edges, n, m);
+    if (st != CC_OK) return st;
+    cc_sample_opt so;
+    cc_finish_opt fo;
+    resolve_opts(sample, finish, so, fo);
+    if ((st = check_sample(so)) != CC_OK || (st = check_finish(fo)) != CC_OK) return st;
+    if (n > 0 && !labels_out) return CC_ERR_INVALID;
+    if (n == 0) {
+        if (stats) *stats = cc_stats{NONE, 0, 0, 0, 0};
+        return CC_OK;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Graph g{offsets, offsets_u64 != 0, edges, n, m};
+    st = offsets_u64 ? run_static<uint64_t>(g, so, fo, labels_out, stats, s)
+                     : run_static<uint32_t>(g, so, fo, labels_out, stats, s);
+    if (st != CC_OK || !stats) return st;
+    return cc_device_error(stream, nullptr);
+}
+
+cc_status cc_static(const void *offsets, int offsets_u64, const uint32_t *edges, uint32_t n, uint64_t m,
+                    const cc_sample_opt *sample, const cc_finish_opt *finish, uint32_t *labels_out, void *stream) {
+    return cc_static_ex(offsets, offsets_u64, edges, n, m, sample, finish, labels_out, nullptr, stream);
+}
+
+cc_status cc_static_host(const void *offsets, int offsets_u64, const uint32_t *edges, uint32_t n, uint64_t m,
+                         const cc_sample_opt *sample, const cc_finish_opt *finish, uint32_t *labels_out,
+                         void *stream) {
+    cc_status st = check_graph(offsets, offsets_u64, edges, n, m);
+    if (st != CC_OK) return st;
+    if (n == 0) return CC_OK;
+    if (!labels_out) return CC_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t ob = (size_t)(n + 1ull) * (offsets_u64 ? 8 : 4);
+    Scratch sc;
+    const size_t o_off = sc.reserve(ob), o_edg = sc.reserve((size_t)m * 4), o_lab = sc.reserve((size_t)n * 4);
+    if ((st = sc.alloc(s)) != CC_OK) return st;
+    CC_TRY(cudaMemcpyAsync(sc.at<void>(o_off), offsets, ob, cudaMemcpyHostToDevice, s));
+    if (m) CC_TRY(cudaMemcpyAsync(sc.at<void>(o_edg), edges, (size_t)m * 4, cudaMemcpyHostToDevice, s));
+    st = cc_static(sc.at<void>(o_off), offsets_u64, m ? sc.at<uint32_t>(o_edg) : nullptr, n, m, sample, finish,
+                   sc.at<uint32_t>(o_lab), stream);
+    if (st != CC_OK) return st;
+    CC_TRY(cudaMemcpyAsync(labels_out, sc.at<uint32_t>(o_lab), (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+    sc.release();
+    return cc_device_error(stream, nullptr);
+}
+
+cc_status cc_sample(const void *offsets, int offsets_u64, const uint32_t *edges, uint32_t n, uint64_t m,
+                    const cc_sample_opt *sample, uint32_t *labels_out, int32_t *sample_info_out, void *stream) {
+    cc_status st = check_graph(offsets, offsets_u64, edges, n, m);
+    if (st != CC_OK) return st;
+    cc_sample_opt so;
+    cc_finish_opt fo;
+    resolve_opts(sample, nullptr, so, fo);
+    if ((st = check_sample(so)) != CC_OK) return st;
+    if (n == 0) return CC_OK;
+    if (!labels_out) return CC_ERR_INVALID;
+    const DeviceInfo *di = device_info();
+    if (!di) return CC_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Graph g{offsets, offsets_u64 != 0, edges, n, m};
+    Work w;
+    plan(w, g, so.kind, 1 /* no count array */, fo.kind, false);
+    if ((st = w.sc.alloc(s)) != CC_OK) return st;
+    CC_TRY(cudaMemsetAsync(w.ctl(), 0, sizeof(Ctl), s));
+    int32_t info = 0;
+    const Dev d = make_dev(di, n);
+    st = offsets_u64 ? sample_phase<uint64_t>(g, so, fo, labels_out, w, di, d, s, &info)
+                     : sample_phase<uint32_t>(g, so, fo, labels_out, w, di, d, s, &info);
+    if (st != CC_OK) return st;
+    if (sample_info_out) {
+        CC_TRY(cudaStreamSynchronize(s));
+        *sample_info_out = info;
+    }
+    return CC_OK;
+}
+
+cc_status cc_identify_frequent(const uint32_t *labels, uint32_t n, uint32_t freq_samples, uint64_t seed,
+                               uint32_t *lmax_out, void *stream) {
+    if (n == 0xFFFFFFFFu || freq_samples > 4096) return CC_ERR_INVALID;
+    if (!lmax_out || (n > 0 && !labels)) return CC_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (n == 0) {
+        {
+            CC_PROF("k_set_u32", s);
+            k_set_u32<<<1, 1, 0, s>>>(lmax_out, NONE);
+        }
+        return from_cuda(cudaGetLastError());
+    }
+    const DeviceInfo *di = device_info();
+    if (!di) return CC_ERR_CUDA;
+    Work w;
+    w.o_ctl = w.sc.reserve(sizeof(Ctl));
+    if (freq_samples == 0) w.o_counts = w.sc.reserve((size_t)n * 4);
+    cc_status st = w.sc.alloc(s);
+    if (st != CC_OK) return st;
+    return identify_phase(labels, n, freq_samples, seed, lmax_out, w, di, make_dev(di, n), s);
+}
+
+cc_status cc_finish(const void *offsets, int offsets_u64, const uint32_t *edges, uint32_t n, uint64_t m,
+                    const cc_finish_opt *finish, uint32_t lmax, uint32_t *labels_inout, uint32_t *rounds_out,
+                    void *stream) {
+    cc_status st = check_graph(offsets, offsets_u64, edges, n, m);
+    if (st != CC_OK) return st;
+    cc_sample_opt so;
+    cc_finish_opt fo;
+    resolve_opts(nullptr, finish, so, fo);
+    if ((st = check_finish(fo)) != CC_OK) return st;
+    if (n == 0) return CC_OK;
+    if (!labels_inout) return CC_ERR_INVALID;
+    const DeviceInfo *di = device_info();
+    if (!di) return CC_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Graph g{offsets, offsets_u64 != 0, edges, n, m};
+    Work w;
+    plan(w, g, CC_SAMPLE_NONE, 1, fo.kind, true);
+    if ((st = w.sc.alloc(s)) != CC_OK) return st;
+    const Dev d = make_dev(di, n);
+    CC_TRY(cudaMemsetAsync(w.ctl(), 0, sizeof(Ctl), s));
+    {
+        CC_PROF("k_check_forest", s);
+        k_check_forest<<<grid_for(di, n, TPB), TPB, 0, s>>>(labels_inout, n, d);
+    }
+    {
+        CC_PROF("k_set_u32", s);
+        k_set_u32<<<1, 1, 0, s>>>(&w.ctl()->lmax, lmax);
+    }
+    CC_LAUNCH();
+    const uint32_t *lmax_p = lmax == NONE ? nullptr : &w.ctl()->lmax;
+    uint32_t rounds = 0;
+    st = offsets_u64 ? finish_phase<uint64_t>(g, fo, lmax_p, labels_inout, w, di, d, s, &rounds)
+                     : finish_phase<uint32_t>(g, fo, lmax_p, labels_inout, w, di, d, s, &rounds);
+    if (rounds_out) *rounds_out = rounds;
+    return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,102 @@
+"""C-ABI checks that need no GPU: the library builds, loads and exports every
+function include/connectit_gb.h declares; argument validation rejects bad
+calls before anything reaches the device; the build is sm_103a-only."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_2008_03909_gb300 as cc
+from paper_2008_03909_gb300 import build as ccbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*(cc_[a-z0-9_]+)\s*\(", src, re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    path = ccbuild.build()
+    L = ctypes.CDLL(path)
+    names = declared_functions()
+    assert len(names) >= 15
+    for nm in names:
+        assert hasattr(L, nm), nm
+    # the Python binding wraps every declared function
+    assert set(names) <= set(cc.exported_symbols())
+
+
+def test_built_for_sm103a_only():
+    path = ccbuild.build()
+    out = subprocess.run(["/usr/local/cuda/bin/cuobjdump", "--list-elf", path], capture_output=True, text=True)
+    if out.returncode != 0:
+        pytest.skip("cuobjdump unavailable")
+    arches = set(re.findall(r"sm_(\d+a?)", out.stdout))
+    assert arches == {"103a"}, arches
+
+
+def test_status_strings_and_version():
+    L = cc.lib()
+    assert L.cc_status_str(0) == b"ok"
+    assert b"sm_103a" in L.cc_version()
+
+
+def _call_static(offsets, u64, edges, n, m, so=None, fo=None, labels=None):
+    L = cc.lib()
+    return L.cc_static(ctypes.c_void_p(offsets), u64, ctypes.c_void_p(edges), n, m,
+                       ctypes.byref(so) if so is not None else None, ctypes.byref(fo) if fo is not None else None,
+                       ctypes.c_void_p(labels), None)
+
+
+def test_validation_rejects_before_any_device_work():
+    # None of these reach a CUDA call, so they run without a GPU.
+    assert _call_static(0, 0, 0, 10, 5, labels=1) == 1           # null offsets
+    assert _call_static(8, 0, 0, 10, 5, labels=1) == 1           # null edges with m > 0
+    assert _call_static(8, 0, 8, 10, 2**32, labels=1) == 1       # 32-bit offsets, m >= 2^32
+    assert _call_static(8, 0, 8, 0xFFFFFFFF, 5, labels=1) == 1   # reserved n
+    assert _call_static(8, 0, 8, 10, 5, labels=0) == 1           # null labels
+    bad_k = cc.sample_opt("kout", k=0)
+    assert _call_static(8, 0, 8, 10, 5, so=bad_k, labels=1) == 1
+    bad_beta = cc.sample_opt("ldd", ldd_beta=0.0)
+    assert _call_static(8, 0, 8, 10, 5, so=bad_beta, labels=1) == 1
+    bad_freq = cc.sample_opt("kout", freq_samples=5000)
+    assert _call_static(8, 0, 8, 10, 5, so=bad_freq, labels=1) == 1
+    bad_fin = cc.finish_opt("uf_rem_cas")
+    bad_fin.find = 7
+    assert _call_static(8, 0, 8, 10, 5, fo=bad_fin, labels=1) == 1
+    res = cc.sample_opt()
+    res.reserved = 3
+    assert _call_static(8, 0, 8, 10, 5, so=res, labels=1) == 1
+
+
+def test_empty_graph_is_a_no_op():
+    assert _call_static(0, 0, 0, 0, 0) == 0
+
+
+def test_incremental_rejects_sv_lt():
+    L = cc.lib()
+    h = ctypes.c_void_p(0)
+    fo = cc.finish_opt("sv")
+    so = cc.sample_opt()
+    # n = 0 keeps this off the device: the finish kind is checked first
+    assert L.cc_incr_create(None, 0, None, 0, 0, ctypes.byref(so), ctypes.byref(fo), None, ctypes.byref(h)) == 6
+    assert L.cc_incr_create(None, 0, None, 0, 0, ctypes.byref(so), None, None, None) == 1
+
+
+def test_no_cpu_fallback():
+    import torch
+    off = torch.zeros(3, dtype=torch.int64)
+    edg = torch.zeros(0, dtype=torch.int32)
+    with pytest.raises(TypeError):
+        cc.cc_static(off, edg)

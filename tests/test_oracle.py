@@ -121,6 +121,20 @@ def test_o1_equals_o2_and_scipy_on_workload_shapes():
         check_invariants(g, a)
 
 
+def test_uf_prefix_is_o1_slice():
+    g = synth.rmat(12, 8, seed=4)
+    off, edg = g.numpy()
+    full, _ = oracle.cc_uf(off, edg)
+    P, cnt = oracle.uf_prefix(off, edg, g.n)
+    assert cnt == g.m
+    roots = np.array([P[v] for v in range(g.n)])
+    for _ in range(20):
+        roots = P[roots]
+    assert np.array_equal(roots, full)
+    P, cnt = oracle.uf_prefix(off, edg, 100)
+    assert cnt == int(off[100])
+
+
 # ---------------------------------------------------------------- closed forms
 @pytest.mark.parametrize("s,f", COMBOS)
 def test_closed_forms(s, f):

@@ -1,0 +1,229 @@
+"""Parity of the CUDA static-connectivity path with the CPU oracle: labels,
+sampled labels, L_max and finish work counts, element by element and bit for
+bit, through the C ABI, on graphs that span many warps, chunks and a ragged
+tail; plus the edge cases the method has."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2008_03909_gb300 as cc
+import synth
+
+pytestmark = pytest.mark.gpu
+
+SAMPLES = ["none", "kout", "bfs", "ldd"]
+UF_VARIANTS = [("uf_rem_cas", "naive", "split_one"), ("uf_rem_cas", "naive", "halve_one"),
+               ("uf_rem_cas", "split", "split_one"), ("uf_rem_cas", "halve", "halve_one"),
+               ("uf_async", "naive", "split_one"), ("uf_async", "split", "split_one"),
+               ("uf_async", "halve", "split_one")]
+FINISHES = UF_VARIANTS + [("sv", "naive", "split_one"), ("lt_prf", "naive", "split_one")]
+
+
+def on_gpu(g, u64=True):
+    off = g.offsets if u64 else g.offsets_u32()
+    return off.cuda(), g.edges.cuda()
+
+
+def gpu_labels(g, sample="none", fin=("uf_rem_cas", "naive", "split_one"), u64=True, **kw):
+    off, edg = on_gpu(g, u64)
+    so = cc.sample_opt(sample, **kw)
+    fo = cc.finish_opt(*fin)
+    lab, st = cc.cc_static(off, edg, so, fo, stats=True)
+    torch.cuda.synchronize()
+    return lab.cpu().numpy().view(np.uint32), st
+
+
+def graphs_small():
+    return [synth.rmat(12, 8, seed=3), synth.grid2d(61, 47, 0.3, seed=2), synth.erdos_renyi(20011, 1.2, seed=4),
+            synth.cliques([1, 5, 40, 3, 300, 2]), synth.star(5000, centre=4321), synth.path(3001),
+            synth.counterexample(), synth.empty(1), synth.empty(77)]
+
+
+@pytest.fixture(scope="module")
+def small():
+    gs = graphs_small()
+    return [(g, oracle.cc_uf(*g.numpy())[0]) for g in gs]
+
+
+@pytest.mark.parametrize("fin", FINISHES, ids=lambda f: "-".join(f))
+@pytest.mark.parametrize("sample", SAMPLES)
+def test_labels_match_oracle_small(small, sample, fin):
+    for g, want in small:
+        got, _ = gpu_labels(g, sample, fin, seed=5)
+        assert np.array_equal(got, want), (g.name, sample, fin)
+    assert cc.device_error() == 0
+
+
+@pytest.mark.parametrize("sample", SAMPLES)
+def test_u32_offsets_match(sample):
+    g = synth.rmat(14, 8, seed=9)
+    want, _ = oracle.cc_uf(*g.numpy())
+    got, _ = gpu_labels(g, sample, u64=False, seed=3)
+    assert np.array_equal(got, want)
+
+
+def test_rmat16_config1():
+    """RMAT scale 16, edge factor 8, (0.57, 0.19, 0.19, 0.05), seed 1, uint32
+    offsets, no sampling, union-find finish."""
+    g = synth.rmat(16, 8, seed=1)
+    want, _ = oracle.cc_uf(*g.numpy())
+    got, st = gpu_labels(g, "none", ("uf_rem_cas", "naive", "split_one"), u64=False)
+    assert np.array_equal(got, want)
+    assert st["lmax"] == 0xFFFFFFFF and st["edges_finish"] == g.m
+
+
+@pytest.mark.parametrize("sample", ["kout", "bfs", "ldd"])
+@pytest.mark.parametrize("fin", [("uf_rem_cas", "naive", "split_one"), ("uf_async", "halve", "split_one"),
+                                 ("sv", "naive", "split_one"), ("lt_prf", "naive", "split_one")],
+                         ids=lambda f: f[0])
+def test_medium_graphs_and_work_counts(sample, fin):
+    """RMAT-18 / grid / ER: labels bit-exact; with exact IdentifyFrequent the
+    GPU picks the oracle's L_max and reads exactly the oracle's finish edges."""
+    for g in (synth.rmat(18, 16, seed=1), synth.grid2d(700, 650, 0.3, seed=1),
+              synth.erdos_renyi(1 << 19, 1.2, seed=1)):
+        off, edg = g.numpy()
+        want, ost = oracle.connectivity(off, edg, sample, fin[0], seed=11, tries=3, beta=0.2)
+        got, st = gpu_labels(g, sample, fin, seed=11)
+        assert np.array_equal(got, want), (g.name, sample, fin)
+        assert st["lmax"] == ost["lmax"]
+        deg = np.diff(off)
+        sampled = {"kout": lambda: oracle.kout_sample(off, edg, 2, 11),
+                   "bfs": lambda: oracle.bfs_sample(off, edg, 3, 11)[0],
+                   "ldd": lambda: oracle.ldd_sample(off, edg, 0.2)[0]}[sample]()
+        assert st["edges_finish"] == int(deg[sampled != ost["lmax"]].sum())
+        if sample == "bfs":
+            assert st["sample_info"] == ost["sample_info"]
+        if sample == "ldd":
+            assert st["sample_info"] == ost["sample_info"]
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 5])
+def test_kout_sampled_labels_bit_exact(k):
+    for g in (synth.rmat(15, 8, seed=2), synth.grid2d(300, 200, 0.3, seed=3)):
+        off, edg = on_gpu(g)
+        lab, info = cc.cc_sample(off, edg, cc.sample_opt("kout", k=k, seed=77))
+        want = oracle.kout_sample(*g.numpy(), k=k, seed=77)
+        assert np.array_equal(lab.cpu().numpy().view(np.uint32), want)
+
+
+@pytest.mark.parametrize("tries,seed", [(3, 1), (1, 2), (3, 7)])
+def test_bfs_sampled_labels_bit_exact(tries, seed):
+    for g in (synth.rmat(16, 8, seed=5), synth.grid2d(400, 300, 0.3, seed=1), synth.erdos_renyi(1 << 17, 1.1)):
+        off, edg = on_gpu(g)
+        lab, info = cc.cc_sample(off, edg, cc.sample_opt("bfs", bfs_tries=tries, seed=seed))
+        want, t = oracle.bfs_sample(*g.numpy(), tries=tries, seed=seed)
+        assert info == t
+        assert np.array_equal(lab.cpu().numpy().view(np.uint32), want)
+
+
+def test_bfs_sample_retries_and_fallback():
+    # 40% in one clique, 60% isolated: tries succeed or fall back per the draws
+    n = 1000
+    g = synth.from_edge_list(n, [(i, j) for i in range(600, 1000, 3) for j in range(i + 1, min(i + 40, 1000))])
+    off, edg = on_gpu(g)
+    for seed in range(12):
+        lab, info = cc.cc_sample(off, edg, cc.sample_opt("bfs", bfs_tries=2, seed=seed))
+        want, t = oracle.bfs_sample(*g.numpy(), tries=2, seed=seed)
+        assert info == t and np.array_equal(lab.cpu().numpy().view(np.uint32), want)
+
+
+@pytest.mark.parametrize("beta", [0.05, 0.2, 1.0, 50.0])
+def test_ldd_sampled_labels_bit_exact(beta):
+    for g in (synth.rmat(15, 8, seed=4), synth.grid2d(250, 250, 0.3, seed=2), synth.path(500)):
+        off, edg = on_gpu(g)
+        lab, rounds = cc.cc_sample(off, edg, cc.sample_opt("ldd", ldd_beta=beta))
+        want, r = oracle.ldd_sample(*g.numpy(), beta=beta)
+        assert rounds == r
+        assert np.array_equal(lab.cpu().numpy().view(np.uint32), want)
+
+
+@pytest.mark.parametrize("samples", [0, 1, 100, 4096])
+def test_identify_frequent_bit_exact(samples):
+    rng = np.random.default_rng(3)
+    for n in (1, 31, 1000, 200_003):
+        lab = rng.integers(0, max(1, n // 7), size=n).astype(np.uint32)
+        lab[: n // 3] = n // 11  # a frequent label
+        got = cc.cc_identify_frequent(torch.from_numpy(lab.view(np.int32)).cuda(), samples, seed=9)
+        want, _ = oracle.identify_frequent(lab, samples, 9)
+        assert int(got.item()) & 0xFFFFFFFF == want
+
+
+@pytest.mark.parametrize("fin", FINISHES, ids=lambda f: "-".join(f))
+def test_finish_from_oracle_sampled_labels(fin):
+    """cc_finish on the oracle's sampled labels and L_max (phase parity)."""
+    g = synth.rmat(16, 8, seed=6)
+    off, edg = g.numpy()
+    lab = oracle.kout_sample(off, edg, 2, 3)
+    lm, _ = oracle.identify_frequent(lab)
+    want, _ = oracle.finish(off, edg, lab, lm, fin[0])
+    t = torch.from_numpy(lab.astype(np.uint32).view(np.int32)).cuda()
+    o, e = on_gpu(g)
+    cc.cc_finish(o, e, t, lm, cc.finish_opt(*fin))
+    assert np.array_equal(t.cpu().numpy().view(np.uint32), want)
+    # and with nothing to skip
+    t = torch.arange(g.n, dtype=torch.int32, device="cuda")
+    cc.cc_finish(o, e, t, 0xFFFFFFFF, cc.finish_opt(*fin))
+    assert np.array_equal(t.cpu().numpy().view(np.uint32), want)
+
+
+def test_rmat22_all_combinations_agree_with_oracle():
+    g = synth.rmat(22, 16, seed=1, device="cuda").to("cpu")
+    want, _ = oracle.cc_uf(*g.numpy())
+    for sample in SAMPLES:
+        for fin in [("uf_rem_cas", "naive", "split_one"), ("uf_async", "split", "split_one"),
+                    ("sv", "naive", "split_one"), ("lt_prf", "naive", "split_one")]:
+            got, _ = gpu_labels(g, sample, fin)
+            assert np.array_equal(got, want), (sample, fin)
+    assert cc.device_error() == 0
+
+
+def test_repeat_runs_identical():
+    """Nondeterministic atomics, deterministic output."""
+    g = synth.rmat(17, 16, seed=8)
+    first, _ = gpu_labels(g, "kout")
+    for _ in range(5):
+        again, _ = gpu_labels(g, "kout")
+        assert np.array_equal(first, again)
+
+
+def test_host_buffer_entry_point():
+    g = synth.rmat(15, 8, seed=2)
+    want, _ = oracle.cc_uf(*g.numpy())
+    lab = cc.cc_static_host(g.offsets.pin_memory(), g.edges.pin_memory())
+    assert np.array_equal(lab.numpy().view(np.uint32), want)
+    lab = cc.cc_static_host(g.offsets_u32(), g.edges, sample=cc.sample_opt("ldd"))  # pageable host memory
+    assert np.array_equal(lab.numpy().view(np.uint32), want)
+
+
+def test_bad_edge_ids_are_flagged_not_faulted():
+    g = synth.path(100)
+    off, edg = on_gpu(g)
+    edg = edg.clone()
+    edg[7] = 100 + 12345  # out of range
+    lab = cc.cc_static(off, edg, cc.sample_opt("none"))
+    bits = cc.device_error()
+    assert bits & 1
+    lab = cc.cc_static(off, edg, cc.sample_opt("kout"))
+    assert cc.device_error() & 1
+    # offsets past m
+    off2 = off.clone()
+    off2[50] = 10**6
+    cc.cc_static(off2, edg, cc.sample_opt("none"))
+    assert cc.device_error() & 2
+    assert cc.device_error() == 0
+
+
+def test_iteration_cap_reports_nonconvergence():
+    g = synth.path(4000)
+    off, edg = on_gpu(g)
+    try:
+        cc.set_iteration_cap(2)
+        with pytest.raises(cc.CCError) as ei:
+            cc.cc_static(off, edg, cc.sample_opt("none"), cc.finish_opt("sv"), stats=True)
+        assert ei.value.status == 4
+    finally:
+        cc.set_iteration_cap(0)
+    cc.device_error()
+    got, _ = gpu_labels(g, "none", ("sv", "naive", "split_one"))
+    assert np.all(got == 0)
