@@ -135,21 +135,28 @@ def make_graph(scale, ef, device):
 
 
 def algorithmic_bytes(kernel, n, m, m_finish, n_nz, k, off_bytes):
-    """Compulsory bytes of one launch of `kernel` (word granularity):
-    offsets 8 B (or 4 B) per vertex, edges 4 B each, parent words 4 B each.
-    n_nz: vertices with at least one edge; m_finish: edges out of non-L_max
-    vertices."""
+    """Compulsory bytes of one launch of `kernel`, counted at word
+    granularity: offsets `off_bytes` per vertex, edges 4 B, parent / label
+    words 4 B.  n_nz: vertices with at least one edge; m_finish: edges out of
+    vertices whose sampled label is not L_max."""
     ob = off_bytes
     table = {
-        "k_iota": 4 * n,                                          # write P
-        "k_kout": ob * (n + 1) + n_nz * k * (4 + 4) + 4 * n + 4 * n_nz,   # offsets, k edges + k parents, own parent, one link
-        "k_shortcut": 8 * n,                                      # read + write P
-        "k_count_labels": 4 * n + 4 * n,                          # read labels, count RMW
+        "k_iota": 4 * n,                                            # write P
+        # offsets, first edge of each non-isolated vertex, write P
+        "k_kout_hook_first": ob * (n + 1) + 4 * n_nz + 4 * n,
+        # offsets, (k-1) picked edges, own parent and picked parent per pick
+        "k_kout_rest": ob * (n + 1) + n_nz * (k - 1) * (4 + 4 + 4),
+        "k_compress_mid": 8 * n,                                    # read + write P
+        "k_compress_count": 8 * n,
+        "k_compress": 8 * n,
+        "k_final_shortcut": 8 * n,
+        "k_count_labels": 4 * n,
         "k_argmax_counts": 4 * n,
-        "k_cand_bin": 4 * n + ob * (n + 1),                       # labels + offsets
-        "k_light_list": 4 * m_finish * 2,                         # edges + parent of each neighbour
+        "k_cand_bin": 4 * n + ob * (n + 1),                         # labels + offsets
+        "k_light_list": 4 * m_finish * 2,                           # edges + parent of each neighbour
         "k_chunks": 4 * m_finish * 2,
-        "k_range_bin": ob * (n + 1) + 4 * n + 4 * m + 4 * m // 2,  # offsets, own parent, edges, parents of lower neighbours
+        # offsets, own parent, every edge, parent of each lower neighbour
+        "k_range_bin": ob * (n + 1) + 4 * n + 4 * m + 4 * (m // 2),
     }
     return table.get(kernel)
 

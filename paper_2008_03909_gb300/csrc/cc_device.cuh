@@ -43,6 +43,12 @@ __device__ __forceinline__ uint32_t ld_rel(const uint32_t *p) {
 __device__ __forceinline__ uint32_t ld_stream(const uint32_t *p) { return __ldcs(p); }
 template <typename T>
 __device__ __forceinline__ T ld_off(const T *p) { return __ldg(p); }
+// L1-cacheable read of a parent slot, for first reads whose staleness is
+// harmless: parent values only ever decrease within one tree, so an older
+// value is still an ancestor in the same set, two equal reads still prove
+// "same set", and every CAS re-validates.  Hub slots read by millions of
+// threads then hit in L1 instead of hammering one L2 slice.
+__device__ __forceinline__ uint32_t ld_ca(const uint32_t *p) { return __ldca(p); }
 
 __device__ __forceinline__ uint64_t gtimer() {
     uint64_t t;
@@ -199,6 +205,17 @@ struct UnionRem {
 };
 
 // ---------------------------------------------------------------- CSR ranges
+__device__ __forceinline__ void clamp_range(uint64_t s, uint64_t t, uint64_t m, uint64_t &b, uint64_t &e,
+                                            const Dev &d) {
+    if (t > m || s > t) {
+        atomicOr(d.err, ERR_BAD_OFFSETS);
+        if (t > m) t = m;
+        if (s > t) s = t;
+    }
+    b = s;
+    e = t;
+}
+
 template <typename OffT>
 __device__ __forceinline__ void vertex_range(const OffT *I, uint32_t u, uint64_t m, uint64_t &b,
                                              uint64_t &e, const Dev &d) {
@@ -210,6 +227,41 @@ __device__ __forceinline__ void vertex_range(const OffT *I, uint32_t u, uint64_t
     }
     b = s;
     e = t;
+}
+
+// Vertex-group loads: lane L of a warp owns vertices v0 = base + 4L ..
+// v0 + 3 and reads their four labels and five offsets with 16-byte vector
+// loads when the arrays are aligned (I[v0+4] comes from the next lane).
+// Entries past n read as NONE / 0.  Every lane of the warp must call them.
+__device__ __forceinline__ void load_labels4(const uint32_t *P, uint64_t v0, uint64_t n, uint32_t (&l)[4]) {
+    if (v0 + 3 < n && ((reinterpret_cast<uintptr_t>(P) & 15) == 0)) {
+        uint4 q = __ldcg(reinterpret_cast<const uint4 *>(P + v0));
+        l[0] = q.x; l[1] = q.y; l[2] = q.z; l[3] = q.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) l[j] = v0 + j < n ? P[v0 + j] : NONE;
+    }
+}
+
+template <typename OffT>
+__device__ __forceinline__ void load_offsets5(const OffT *I, uint64_t v0, uint64_t n, uint64_t (&o)[5]) {
+    const int lane = threadIdx.x & 31;
+    if (v0 + 3 < n && ((reinterpret_cast<uintptr_t>(I) & 15) == 0)) {
+        if (sizeof(OffT) == 8) {
+            const ulonglong2 *q = reinterpret_cast<const ulonglong2 *>(I + v0);
+            ulonglong2 a = __ldg(q), b = __ldg(q + 1);
+            o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+        } else {
+            uint4 a = __ldg(reinterpret_cast<const uint4 *>(I + v0));
+            o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) o[j] = v0 + j <= n ? (uint64_t)ld_off(I + v0 + j) : 0;
+    }
+    uint64_t nxt = __shfl_down_sync(0xFFFFFFFFu, o[0], 1);
+    if (lane == 31 || v0 + 4 >= n) nxt = v0 + 4 <= n ? (uint64_t)ld_off(I + v0 + 4) : 0;
+    o[4] = nxt;
 }
 
 // Exclusive append for a whole warp: EVERY lane of the warp must call it
@@ -325,6 +377,23 @@ __device__ __forceinline__ void run_chunks(const OffT *I, const uint32_t *A, uin
 // Union-find finish / sampling edge: apply Union(u, v) with the engine E.
 // lower_only: apply only edges to smaller neighbours (each undirected edge is
 // stored twice; used when no vertex is skipped, so the reverse copy exists).
+// Union of NB independent pairs: all first parent reads are issued
+// together (memory-level parallelism), then the pairs whose parents differ
+// go through the engine.
+template <class E, int NB>
+__device__ __forceinline__ void unite_pairs(uint32_t *P, const uint32_t (&u)[NB], const uint32_t (&v)[NB],
+                                            const bool (&ok)[NB], const Dev &d) {
+    uint32_t pu[NB], pv[NB];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+        pu[q] = ok[q] ? ld_ca(P + u[q]) : 0;
+        pv[q] = ok[q] ? ld_ca(P + v[q]) : 0;
+    }
+#pragma unroll
+    for (int q = 0; q < NB; ++q)
+        if (ok[q] && pu[q] != pv[q]) E::unite(P, u[q], v[q], pu[q], pv[q], d);
+}
+
 template <class E>
 struct UnionEdge {
     uint32_t *P;
@@ -336,9 +405,9 @@ struct UnionEdge {
 #pragma unroll
         for (int j = 0; j < 4; ++j) act[j] = ok[j] && v[j] != u && (!lower_only || v[j] < u);
         if (!(act[0] | act[1] | act[2] | act[3])) return;
-        uint32_t pu = ld_rel(P + u);
+        uint32_t pu = ld_ca(P + u);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) pv[j] = act[j] ? ld_rel(P + v[j]) : pu;
+        for (int j = 0; j < 4; ++j) pv[j] = act[j] ? ld_ca(P + v[j]) : pu;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             if (act[j] && pv[j] != pu) {
@@ -348,6 +417,35 @@ struct UnionEdge {
         }
     }
     __device__ __forceinline__ void flush() {}
+};
+
+// Label counting with little atomic contention: a thread keeps a sticky
+// "hot" label and a candidate in registers (a two-slot heavy-hitter
+// counter); other labels go straight to the count array.  flush() folds
+// the warp's hot slots together, one atomic per distinct label.
+struct LabelCounter {
+    uint32_t hot = NONE, hot_c = 0, cand = NONE, cand_c = 0;
+    __device__ __forceinline__ void add(uint32_t *cnt, uint32_t l) {
+        if (l == hot) { ++hot_c; return; }
+        if (l == cand) {
+            if (++cand_c > hot_c) {
+                uint32_t t = hot; hot = cand; cand = t;
+                t = hot_c; hot_c = cand_c; cand_c = t;
+            }
+            return;
+        }
+        if (cand_c) atomicAdd(cnt + cand, cand_c);
+        cand = l;
+        cand_c = 1;
+    }
+    // every lane of the warp must call this
+    __device__ __forceinline__ void flush(uint32_t *cnt) {
+        if (cand_c) atomicAdd(cnt + cand, cand_c);
+        const int lane = threadIdx.x & 31;
+        unsigned grp = __match_any_sync(0xFFFFFFFFu, hot);
+        uint32_t sum = __reduce_add_sync(grp, hot_c);
+        if (hot != NONE && sum && lane == __ffs(grp) - 1) atomicAdd(cnt + hot, sum);
+    }
 };
 
 }  // namespace ccg

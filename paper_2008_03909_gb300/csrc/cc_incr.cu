@@ -20,7 +20,7 @@ namespace {
 
 constexpr unsigned TPB = 256;
 
-__global__ void k_incr_iota(uint32_t *P, uint32_t n) {
+__global__ void __launch_bounds__(256, 8) k_incr_iota(uint32_t *P, uint32_t n) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x)
         P[i] = (uint32_t)i;
@@ -29,7 +29,7 @@ __global__ void k_incr_iota(uint32_t *P, uint32_t n) {
 // Insert(u, v) = Union(u, v) for every pair; four pairs per thread step so
 // their parent loads overlap.
 template <class E>
-__global__ void k_incr_insert(uint32_t *P, uint32_t n, const uint32_t *pairs, uint64_t k, Dev d) {
+__global__ void __launch_bounds__(256, 8) k_incr_insert(uint32_t *P, uint32_t n, const uint32_t *pairs, uint64_t k, Dev d) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i0 < k; i0 += 4 * stride) {
         uint32_t u[4], v[4], pu[4], pv[4];
@@ -55,7 +55,7 @@ __global__ void k_incr_insert(uint32_t *P, uint32_t n, const uint32_t *pairs, ui
 
 // IsConnected(u, v): Find(u) == Find(v) with the handle's find option.
 template <int FIND>
-__global__ void k_incr_query(uint32_t *P, uint32_t n, const uint32_t *pairs, uint64_t q, uint8_t *ans, Dev d) {
+__global__ void __launch_bounds__(256, 8) k_incr_query(uint32_t *P, uint32_t n, const uint32_t *pairs, uint64_t q, uint8_t *ans, Dev d) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < q;
          i += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t u = __ldcs(pairs + 2 * i), v = __ldcs(pairs + 2 * i + 1);
@@ -73,7 +73,7 @@ __global__ void k_incr_query(uint32_t *P, uint32_t n, const uint32_t *pairs, uin
 }
 
 // Canonical labels of the current forest (roots are component minima).
-__global__ void k_incr_labels(const uint32_t *P, uint32_t n, uint32_t *out, Dev d) {
+__global__ void __launch_bounds__(256, 8) k_incr_labels(const uint32_t *P, uint32_t n, uint32_t *out, Dev d) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t v = (uint32_t)i;

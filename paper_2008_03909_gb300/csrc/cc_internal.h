@@ -84,10 +84,11 @@ struct Ctl {
     uint32_t nfront[2];
     uint32_t last_round;
     uint32_t lmax;
+    uint32_t ndefer;
     unsigned long long key;
     unsigned long long edges;
     unsigned long long mf[2];
-    uint32_t pad[16];
+    uint32_t pad[15];
 };
 
 // Launch accounting: one scope per kernel launch.  Counts every launch and,

@@ -20,7 +20,7 @@ namespace {
 constexpr unsigned TPB = 256;
 
 // ================================================================ kernels
-__global__ void k_iota(uint32_t *P, uint32_t n) {
+__global__ void __launch_bounds__(256, 8) k_iota(uint32_t *P, uint32_t n) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x)
         P[i] = (uint32_t)i;
@@ -32,7 +32,7 @@ __global__ void k_or_u32(uint32_t *p, uint32_t v) { atomicOr(p, v); }
 // Labels handed in by a caller must be a forest with P[v] <= v (sampled
 // labels as cc_sample writes them satisfy it).  Out-of-range or increasing
 // entries are flagged and reset to v so that every walk stays in bounds.
-__global__ void k_check_forest(uint32_t *P, uint32_t n, Dev d) {
+__global__ void __launch_bounds__(256, 8) k_check_forest(uint32_t *P, uint32_t n, Dev d) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t p = P[i];
@@ -47,64 +47,218 @@ __global__ void k_check_forest(uint32_t *P, uint32_t n, Dev d) {
 // Algorithm 4, the FullShortcut of Algorithm 15 / Appendix D, and the final
 // shortcut to canonical labels (roots are component minima).  prev, when
 // given, receives the new parents (the round-start snapshot of SV / LT).
-__global__ void k_shortcut(uint32_t *P, uint32_t *prev, uint32_t n, Dev d) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t v = (uint32_t)i;
+// No link happens while it runs (only compression), so a root seen through
+// L1 is a root and the walks use L1-cacheable loads; four vertices per
+// thread step walk their chains in lock-step.  With COUNT, every non-root
+// vertex also counts one for its root (IdentifyFrequent on flat labels, see
+// identify_phase).
+__device__ __forceinline__ void roots4(const uint32_t *P, uint32_t v0, uint32_t (&x)[4], uint32_t (&px)[4],
+                                       const Dev &d) {
+    bool act[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        x[j] = v0 + j;
+        act[j] = px[j] != x[j];
+    }
+    Guard g;
+    while (act[0] | act[1] | act[2] | act[3]) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (act[j]) {
+                x[j] = px[j];
+                px[j] = ld_ca(P + x[j]);
+            }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) act[j] = act[j] && px[j] != x[j];
+        if (!g.step(d)) break;
+    }
+}
+
+template <bool COUNT>
+__global__ void __launch_bounds__(256, 8) k_shortcut(uint32_t *P, uint32_t *prev, uint32_t n, uint32_t *cnt, Dev d) {
+    const uint64_t n4 = n / 4;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    LabelCounter lc;
+    for (uint64_t i = tid; i < n4; i += stride) {
+        uint4 p = __ldcg(reinterpret_cast<const uint4 *>(P) + i);
+        uint32_t x[4], px[4] = {p.x, p.y, p.z, p.w};
+        const uint32_t v0 = (uint32_t)(4 * i);
+        roots4(P, v0, x, px, d);
+        uint4 r = make_uint4(x[0], x[1], x[2], x[3]);
+        if (r.x != p.x || r.y != p.y || r.z != p.z || r.w != p.w) __stcg(reinterpret_cast<uint4 *>(P) + i, r);
+        if (prev) __stcg(reinterpret_cast<uint4 *>(prev) + i, r);
+        if (COUNT) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (x[j] != v0 + j) lc.add(cnt, x[j]);
+        }
+    }
+    for (uint64_t v = 4 * n4 + tid; v < n; v += stride) {
         uint32_t p = ld_rel(P + v);
-        uint32_t r = find_from<FIND_NAIVE>(P, v, p, d);
+        uint32_t r = find_from<FIND_NAIVE>(P, (uint32_t)v, p, d);
         if (r != p) P[v] = r;
         if (prev) prev[v] = r;
+        if (COUNT && r != v) lc.add(cnt, r);
     }
+    if (COUNT) lc.flush(cnt);
 }
 
 // ---------------------------------------------------------------- k-out
 // Algorithm 4: each vertex of degree > 0 picks its first edge and k-1
 // uniform random edges (with replacement; pick j of v draws
-// out(seed ^ TAG_KOUT, v*k + j)), and each picked edge is a Union.
-template <typename OffT, class E>
-__global__ void k_kout(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, uint32_t k,
-                       uint64_t seed, uint32_t *P, Dev d) {
-    UnionEdge<E> f{P, d, false};
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t v = (uint32_t)i;
-        uint64_t b, e;
-        vertex_range(I, v, m, b, e, d);
-        uint64_t deg = e - b;
+// out(seed ^ TAG_KOUT, v*k + j)), and each picked edge is a Union.  The
+// picked edges are applied in two launches, picks [jb, je) each: the first
+// edges, a full compression, then the random picks, whose unions then mostly
+// find both endpoints already under one root (Afforest's schedule; the
+// union-find result and the compressed labels are the same for any order).
+// One vertex per thread step at full occupancy (launch bounds for eight
+// 256-thread blocks per SM), with the next vertex's offsets prefetched.
+constexpr int KOUT_MINB = 8;
+
+template <typename OffT, class E, int NB>
+__global__ void __launch_bounds__(256, KOUT_MINB)
+k_kout(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, uint32_t k, uint64_t seed, uint32_t *P,
+       Dev d, uint32_t jb, uint32_t je) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    // software pipeline: the next vertex's offsets are in flight while the
+    // current vertex's edges and parents are read
+    uint64_t o0 = 0, o1 = 0;
+    if (v < n) { o0 = ld_off(I + v); o1 = ld_off(I + v + 1); }
+    for (; v < n; v += stride) {
+        const uint64_t vn = v + stride;
+        uint64_t n0 = 0, n1 = 0;
+        if (vn < n) { n0 = ld_off(I + vn); n1 = ld_off(I + vn + 1); }
+        uint64_t b = 0, e = 0;
+        clamp_range(o0, o1, m, b, e, d);
+        const uint64_t deg = e - b;
+        o0 = n0;
+        o1 = n1;
         if (deg == 0) continue;
-        for (uint32_t j0 = 0; j0 < k; j0 += 4) {
-            uint32_t w[4];
-            bool ok[4];
+        for (uint32_t j0 = jb; j0 < je; j0 += NB) {
+            uint32_t u[NB], w[NB];
+            bool ok[NB];
 #pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {
-                uint32_t j = j0 + jj;
-                ok[jj] = j < k;
+            for (int q = 0; q < NB; ++q) {
+                const uint32_t pick = j0 + q;
+                u[q] = (uint32_t)v;
+                ok[q] = pick < je;
                 uint64_t off = 0;
-                if (ok[jj] && j > 0) off = ((draw64(seed ^ TAG_KOUT, (uint64_t)v * k + j) >> 32) * deg) >> 32;
-                w[jj] = ok[jj] ? ld_stream(A + b + off) : v;
-                if (ok[jj] && w[jj] >= n) { atomicOr(d.err, ERR_BAD_EDGE); ok[jj] = false; }
+                if (ok[q] && pick > 0) off = ((draw64(seed ^ TAG_KOUT, v * k + pick) >> 32) * deg) >> 32;
+                w[q] = ok[q] ? ld_stream(A + b + off) : u[q];
+                if (ok[q] && w[q] >= n) { atomicOr(d.err, ERR_BAD_EDGE); ok[q] = false; }
+                if (ok[q] && w[q] == u[q]) ok[q] = false;
             }
-            f.apply4(v, w, ok);
+            unite_pairs<E, NB>(P, u, w, ok, d);
         }
     }
 }
 
-// ---------------------------------------------------------------- IdentifyFrequent
-// Exact: count every label (warp-aggregated atomics on a count array), then
-// the arg-max with ties to the smallest label via a packed 64-bit max key
-// (count << 32 | ~label).
-__global__ void k_count_labels(const uint32_t *L, uint32_t n, uint32_t *cnt, Dev d) {
+// picks per thread step: one when a round has a single pick (k = 2), else four
+template <typename OffT, class E>
+void launch_kout(unsigned grid, cudaStream_t s, const OffT *I, const uint32_t *A, uint32_t n, uint64_t m,
+                 uint32_t k, uint64_t seed, uint32_t *P, Dev d, uint32_t jb, uint32_t je) {
+    if (je - jb == 1) k_kout<OffT, E, 1><<<grid, 256, 0, s>>>(I, A, n, m, k, seed, P, d, jb, je);
+    else k_kout<OffT, E, 4><<<grid, 256, 0, s>>>(I, A, n, m, k, seed, P, d, jb, je);
+}
+
+// First edges, part one (replaces the identity initialisation): each
+// vertex v reads its first edge (v, w0).  If w0 < v, v is linked under w0
+// with a plain store: in this pass only v's thread writes P[v], so v is
+// still a root and the link keeps P[x] <= x.  Otherwise P[v] = v, and a
+// vertex with w0 > v (all its neighbours larger) is queued for a real Union
+// in part two.  Four vertices per lane, vector loads and stores.
+template <typename OffT>
+__global__ void __launch_bounds__(256, 8) k_kout_hook_first(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, uint32_t *P,
+                                  uint32_t *defer, uint32_t *ndefer, Dev d) {
     const int lane = threadIdx.x & 31;
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t base = warp * 32; base < n; base += nw * 32) {
-        uint64_t v = base + lane;
-        uint32_t l = v < n ? L[v] : NONE;
-        if (l != NONE && l >= n) { atomicOr(d.err, ERR_BAD_EDGE); l = NONE; }
-        unsigned grp = __match_any_sync(0xFFFFFFFFu, l);
-        if (l != NONE && lane == __ffs(grp) - 1) atomicAdd(cnt + l, (uint32_t)__popc(grp));
+    uint64_t base = warp * 128;
+    uint64_t o[5];
+    if (base < n) load_offsets5(I, base + 4 * lane, n, o);
+    for (; base < n; base += nw * 128) {
+        const uint64_t v0 = base + 4 * lane;
+        uint32_t w[4], p[4], nd = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            uint64_t b = 0, e = 0;
+            if (v0 + j < n) clamp_range(o[j], o[j + 1], m, b, e, d);
+            w[j] = e > b ? ld_stream(A + b) : NONE;
+        }
+        // the next step's offsets load while this step's first edges are read
+        if (base + nw * 128 < n) load_offsets5(I, base + nw * 128 + 4 * lane, n, o);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t v = (uint32_t)(v0 + j);
+            if (w[j] != NONE && w[j] >= n) { atomicOr(d.err, ERR_BAD_EDGE); w[j] = NONE; }
+            p[j] = (w[j] != NONE && w[j] < v) ? w[j] : v;
+            nd += (w[j] != NONE && w[j] > v);
+        }
+        if (v0 + 3 < n && ((reinterpret_cast<uintptr_t>(P) & 15) == 0)) {
+            __stcg(reinterpret_cast<uint4 *>(P + v0), make_uint4(p[0], p[1], p[2], p[3]));
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (v0 + j < n) P[v0 + j] = p[j];
+        }
+        uint32_t slot = warp_append_full(ndefer, nd);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (w[j] != NONE && w[j] > (uint32_t)(v0 + j)) defer[slot++] = (uint32_t)(v0 + j);
     }
+}
+
+// First edges, part two: Union(v, w0) for the queued vertices.
+template <typename OffT, class E>
+__global__ void __launch_bounds__(256, KOUT_MINB)
+k_kout_defer(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, uint32_t *P, const uint32_t *defer,
+             const uint32_t *ndefer, Dev d) {
+    const uint32_t total = *ndefer;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = defer[i];
+        uint64_t b, e;
+        vertex_range(I, v, m, b, e, d);
+        if (e == b) continue;
+        uint32_t u1[1] = {v}, w1[1] = {ld_stream(A + b)};
+        bool ok[1] = {w1[0] < n && w1[0] != v};
+        unite_pairs<E, 1>(P, u1, w1, ok, d);
+    }
+}
+
+// ---------------------------------------------------------------- IdentifyFrequent
+// Exact: count every label into a count array (register heavy-hitter slots
+// keep the frequent label's atomics off one address), then the arg-max with
+// ties to the smallest label via a packed 64-bit max key
+// (count << 32 | ~label).
+// FLAT: the labels are a flat forest (label[v] = root of v, every root its
+// own label, vertex 0 a root), as sampling leaves them.  Then a root's count
+// is 1 + its non-root members and a non-root label counts 0, so the arg-max
+// (ties to the smallest) is unchanged when only non-root vertices are
+// counted; with none, every root ties at 1 and the answer is root 0.
+template <bool FLAT>
+__global__ void __launch_bounds__(256, 8) k_count_labels(const uint32_t *L, uint32_t n, uint32_t *cnt, Dev d) {
+    const uint64_t n4 = n / 4;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    LabelCounter lc;
+    for (uint64_t i = tid; i < n4; i += stride) {
+        uint4 q = __ldcs(reinterpret_cast<const uint4 *>(L) + i);
+        uint32_t l[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (l[j] >= n) atomicOr(d.err, ERR_BAD_EDGE);
+            else if (!FLAT || l[j] != 4 * i + j) lc.add(cnt, l[j]);
+        }
+    }
+    for (uint64_t v = 4 * n4 + tid; v < n; v += stride) {
+        uint32_t l = L[v];
+        if (l >= n) atomicOr(d.err, ERR_BAD_EDGE);
+        else if (!FLAT || l != v) lc.add(cnt, l);
+    }
+    lc.flush(cnt);
 }
 
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long x) {
@@ -116,17 +270,27 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long x)
     return x;
 }
 
-__global__ void k_argmax_counts(const uint32_t *cnt, uint32_t n, unsigned long long *key) {
+__device__ __forceinline__ void keep_max(unsigned long long &best, uint32_t c, uint64_t i) {
+    if (c) {
+        unsigned long long k2 = ((unsigned long long)c << 32) | (uint32_t)~(uint32_t)i;
+        best = k2 > best ? k2 : best;
+    }
+}
+
+__global__ void __launch_bounds__(256, 8) k_argmax_counts(const uint32_t *cnt, uint32_t n, unsigned long long *key) {
     __shared__ unsigned long long s[32];
     unsigned long long best = 0;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t c = cnt[i];
-        if (c) {
-            unsigned long long k2 = ((unsigned long long)c << 32) | (uint32_t)~(uint32_t)i;
-            best = k2 > best ? k2 : best;
-        }
+    const uint64_t n4 = n / 4;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    for (uint64_t i = tid; i < n4; i += stride) {
+        uint4 c = __ldcs(reinterpret_cast<const uint4 *>(cnt) + i);
+        keep_max(best, c.x, 4 * i);
+        keep_max(best, c.y, 4 * i + 1);
+        keep_max(best, c.z, 4 * i + 2);
+        keep_max(best, c.w, 4 * i + 3);
     }
+    for (uint64_t i = 4 * n4 + tid; i < n; i += stride) keep_max(best, cnt[i], i);
     best = warp_max_u64(best);
     if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = best;
     __syncthreads();
@@ -137,9 +301,11 @@ __global__ void k_argmax_counts(const uint32_t *cnt, uint32_t n, unsigned long l
     }
 }
 
+// (an empty key only arises from flat counting with no non-root vertex,
+// where every root ties and the smallest, vertex 0, wins)
 __global__ void k_key_to_label(const unsigned long long *key, uint32_t *lmax) {
     unsigned long long k = *key;
-    *lmax = k ? ~(uint32_t)(k & 0xFFFFFFFFull) : NONE;
+    *lmax = k ? ~(uint32_t)(k & 0xFFFFFFFFull) : 0u;
 }
 
 // Estimate: the labels at S seeded positions out(seed ^ TAG_FREQ, i) mod n,
@@ -172,7 +338,7 @@ __global__ void k_freq_sampled(const uint32_t *L, uint32_t n, uint32_t S, uint64
 // a skip test on P[u] == L_max): light vertices run in the calling thread;
 // heavier ones are cut into chunks for k_chunks.
 template <typename OffT, class F>
-__global__ void k_range_bin(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, const uint32_t *P,
+__global__ void __launch_bounds__(256, 8) k_range_bin(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, const uint32_t *P,
                             const uint32_t *lmax_p, F f, ChunkRef *chunks, uint32_t *nchunks,
                             uint64_t cap, unsigned long long *edges, Dev d) {
     const int lane = threadIdx.x & 31;
@@ -199,7 +365,7 @@ __global__ void k_range_bin(const OffT *I, const uint32_t *A, uint32_t n, uint64
 }
 
 template <typename OffT, class F>
-__global__ void k_chunks(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, const ChunkRef *chunks,
+__global__ void __launch_bounds__(256, 8) k_chunks(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, const ChunkRef *chunks,
                          const uint32_t *nchunks, uint64_t cap, F f, Dev d) {
     run_chunks(I, A, n, m, chunks, nchunks, cap, f, d);
     f.flush();
@@ -208,7 +374,7 @@ __global__ void k_chunks(const OffT *I, const uint32_t *A, uint32_t n, uint64_t 
 // Vertex list (BFS / LDD frontiers): light vertices inline, heavier ones to
 // the chunk list.
 template <typename OffT, class F>
-__global__ void k_list_bin(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, const uint32_t *list,
+__global__ void __launch_bounds__(256, 8) k_list_bin(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, const uint32_t *list,
                            const uint32_t *count, F f, ChunkRef *chunks, uint32_t *nchunks, uint64_t cap,
                            Dev d) {
     const int lane = threadIdx.x & 31;
@@ -233,7 +399,7 @@ __global__ void k_list_bin(const OffT *I, const uint32_t *A, uint32_t n, uint64_
 // sampled label is not L_max and that have edges; light ones to a list,
 // heavy ones to the chunk list.  Built once, reused every round.
 template <typename OffT>
-__global__ void k_cand_bin(const OffT *I, uint32_t n, uint64_t m, const uint32_t *P, const uint32_t *lmax_p,
+__global__ void __launch_bounds__(256, 8) k_cand_bin(const OffT *I, uint32_t n, uint64_t m, const uint32_t *P, const uint32_t *lmax_p,
                            uint32_t *light, uint32_t *nlight, ChunkRef *chunks, uint32_t *nchunks, uint64_t cap,
                            unsigned long long *edges, Dev d) {
     const int lane = threadIdx.x & 31;
@@ -241,27 +407,44 @@ __global__ void k_cand_bin(const OffT *I, uint32_t n, uint64_t m, const uint32_t
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint32_t lmax = lmax_p ? *lmax_p : NONE;
     unsigned long long my_edges = 0;
-    for (uint64_t base = warp * 32; base < n; base += nw * 32) {
-        uint32_t u = (uint32_t)(base + lane);
-        bool act = base + lane < n;
-        uint64_t b = 0, e = 0;
-        if (act && lmax != NONE && P[u] == lmax) act = false;
-        if (act) vertex_range(I, u, m, b, e, d);
-        uint64_t deg = e - b;
-        my_edges += deg;
-        uint32_t isl = (deg > 0 && deg <= LIGHT_MAX) ? 1u : 0u;
-        uint32_t nc = deg > LIGHT_MAX ? (uint32_t)((deg + CHUNK - 1) / CHUNK) : 0;
-        uint32_t sl = warp_append_full(nlight, isl);
-        if (isl) light[sl] = u;
-        uint32_t sc = warp_append_full(nchunks, nc);
-        if (nc) write_chunks(chunks, cap, sc, nc, u, d);
+    // a warp step covers 128 vertices, four per lane, read with vector loads
+    for (uint64_t base = warp * 128; base < n; base += nw * 128) {
+        const uint64_t v0 = base + 4 * lane;
+        uint32_t pl[4];
+        uint64_t o[5];
+        load_labels4(P, v0, n, pl);
+        load_offsets5(I, v0, n, o);
+        uint32_t nl = 0, ncs = 0, nc[4];
+        uint64_t bb[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            uint64_t b = 0, e = 0;
+            bool act = v0 + j < n && !(lmax != NONE && pl[j] == lmax);
+            if (act) clamp_range(o[j], o[j + 1], m, b, e, d);
+            uint64_t deg = e - b;
+            my_edges += deg;
+            bb[j] = deg;
+            nl += (deg > 0 && deg <= LIGHT_MAX);
+            nc[j] = deg > LIGHT_MAX ? (uint32_t)((deg + CHUNK - 1) / CHUNK) : 0;
+            ncs += nc[j];
+        }
+        uint32_t sl = warp_append_full(nlight, nl);
+        uint32_t sc = warp_append_full(nchunks, ncs);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (bb[j] > 0 && bb[j] <= LIGHT_MAX) light[sl++] = (uint32_t)(v0 + j);
+            if (nc[j]) {
+                write_chunks(chunks, cap, sc, nc[j], (uint32_t)(v0 + j), d);
+                sc += nc[j];
+            }
+        }
     }
     for (int o = 16; o > 0; o >>= 1) my_edges += __shfl_xor_sync(0xFFFFFFFFu, my_edges, o);
     if (lane == 0 && edges && my_edges) atomicAdd(edges, my_edges);
 }
 
 template <typename OffT, class F>
-__global__ void k_light_list(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, const uint32_t *list,
+__global__ void __launch_bounds__(256, 8) k_light_list(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, const uint32_t *list,
                              const uint32_t *count, F f, Dev d) {
     const uint32_t total = *count;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
@@ -355,7 +538,7 @@ struct BFSEdge {
 // Bottom-up step: every unvisited vertex looks for a neighbour in the
 // frontier bitmap and stops at the first one.
 template <typename OffT>
-__global__ void k_bfs_pull(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, uint32_t *P, uint32_t *vis,
+__global__ void __launch_bounds__(256, 8) k_bfs_pull(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, uint32_t *P, uint32_t *vis,
                            const uint32_t *front_bm, uint32_t *next_bm, uint32_t src, uint32_t *nnext,
                            unsigned long long *next_edges, uint32_t *minv, Dev d) {
     uint32_t cnt = 0, mn = NONE;
@@ -395,7 +578,7 @@ __global__ void k_bfs_pull(const OffT *I, const uint32_t *A, uint32_t n, uint64_
 
 // Degree sum of a vertex list (frontier edges, for the direction switch).
 template <typename OffT>
-__global__ void k_list_degrees(const OffT *I, uint64_t m, const uint32_t *list, const uint32_t *count,
+__global__ void __launch_bounds__(256, 8) k_list_degrees(const OffT *I, uint64_t m, const uint32_t *list, const uint32_t *count,
                                unsigned long long *out, Dev d) {
     const uint32_t total = *count;
     unsigned long long s = 0;
@@ -409,7 +592,7 @@ __global__ void k_list_degrees(const OffT *I, uint64_t m, const uint32_t *list, 
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
 }
 
-__global__ void k_list_to_bitmap(const uint32_t *list, const uint32_t *count, uint32_t *bm) {
+__global__ void __launch_bounds__(256, 8) k_list_to_bitmap(const uint32_t *list, const uint32_t *count, uint32_t *bm) {
     const uint32_t total = *count;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
          i += (uint64_t)gridDim.x * blockDim.x) {
@@ -418,7 +601,7 @@ __global__ void k_list_to_bitmap(const uint32_t *list, const uint32_t *count, ui
     }
 }
 
-__global__ void k_bitmap_to_list(const uint32_t *bm, uint32_t n, uint32_t *list, uint32_t *count) {
+__global__ void __launch_bounds__(256, 8) k_bitmap_to_list(const uint32_t *bm, uint32_t n, uint32_t *list, uint32_t *count) {
     const uint32_t words = (n + 31) / 32;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < words;
          i += (uint64_t)gridDim.x * blockDim.x) {
@@ -435,7 +618,7 @@ __global__ void k_bitmap_to_list(const uint32_t *bm, uint32_t n, uint32_t *list,
 }
 
 // Relabel the reached set to its smallest member (a min-rooted star).
-__global__ void k_bfs_relabel(uint32_t *P, const uint32_t *vis, uint32_t n, const uint32_t *minv) {
+__global__ void __launch_bounds__(256, 8) k_bfs_relabel(uint32_t *P, const uint32_t *vis, uint32_t n, const uint32_t *minv) {
     const uint32_t mn = *minv;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x)
@@ -446,7 +629,7 @@ __global__ void k_bfs_relabel(uint32_t *P, const uint32_t *vis, uint32_t n, cons
 // Round r of the clustering (Algorithm 6): every uncovered id in [s0, s1)
 // becomes a centre; then the frontier claims uncovered neighbours, the
 // smallest claiming centre id winning (candidates first, commit after).
-__global__ void k_ldd_wake(uint32_t s0, uint32_t s1, uint32_t *P, uint32_t *vis, uint32_t *front,
+__global__ void __launch_bounds__(256, 8) k_ldd_wake(uint32_t s0, uint32_t s1, uint32_t *P, uint32_t *vis, uint32_t *front,
                            uint32_t *nfront, uint32_t *last_round, uint32_t round) {
     bool any = false;
     for (uint64_t i = s0 + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < s1;
@@ -481,7 +664,7 @@ struct LDDEdge {
     __device__ __forceinline__ void flush() {}
 };
 
-__global__ void k_ldd_commit(uint32_t *P, uint32_t *vis, uint32_t *cand, const uint32_t *next,
+__global__ void __launch_bounds__(256, 8) k_ldd_commit(uint32_t *P, uint32_t *vis, uint32_t *cand, const uint32_t *next,
                              const uint32_t *nnext, uint32_t *last_round, uint32_t round) {
     const uint32_t total = *nnext;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
@@ -497,7 +680,7 @@ __global__ void k_ldd_commit(uint32_t *P, uint32_t *vis, uint32_t *cand, const u
 // Relabel clusters to their smallest members: cmin[c] = min{v : P[v] = c}
 // (warp-grouped by cluster, one atomicMin per group, skipped when it cannot
 // lower the current value), then P[v] = cmin[P[v]].
-__global__ void k_cluster_min(const uint32_t *P, uint32_t n, uint32_t *cmin) {
+__global__ void __launch_bounds__(256, 8) k_cluster_min(const uint32_t *P, uint32_t n, uint32_t *cmin) {
     const int lane = threadIdx.x & 31;
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -510,7 +693,7 @@ __global__ void k_cluster_min(const uint32_t *P, uint32_t n, uint32_t *cmin) {
     }
 }
 
-__global__ void k_apply_cluster_min(uint32_t *P, uint32_t n, const uint32_t *cmin) {
+__global__ void __launch_bounds__(256, 8) k_apply_cluster_min(uint32_t *P, uint32_t n, const uint32_t *cmin) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x)
         P[i] = cmin[P[i]];
@@ -528,6 +711,7 @@ struct Graph {
 // Scratch layout of one call.
 struct Work {
     Scratch sc;
+    size_t o_defer = 0;
     size_t o_ctl = 0, o_chunks = 0, o_counts = 0, o_prev = 0, o_light = 0, o_vis = 0, o_q0 = 0, o_q1 = 0,
            o_bm0 = 0, o_bm1 = 0, o_cand = 0;
     bool has_counts = false, has_sv = false, has_bfs = false, has_ldd = false;
@@ -540,6 +724,7 @@ void plan(Work &w, const Graph &g, int sample_kind, uint32_t freq_samples, int f
     w.o_ctl = w.sc.reserve(sizeof(Ctl));
     w.chunk_cap = chunk_capacity(n, g.m);
     w.o_chunks = w.sc.reserve(w.chunk_cap * sizeof(ChunkRef));
+    if (sample_kind == CC_SAMPLE_KOUT) w.o_defer = w.sc.reserve(n * 4);
     if (sample_kind != CC_SAMPLE_NONE && freq_samples == 0) {
         w.has_counts = true;
         w.o_counts = w.sc.reserve(n * 4);
@@ -839,37 +1024,63 @@ cc_status ldd_sample(const Graph &g, const cc_sample_opt &so, uint32_t *P, Work 
     return CC_OK;
 }
 
+// count_into: when not null (k-out with exact IdentifyFrequent), the
+// compression also counts the flat labels into this (zeroed here) array.
 template <typename OffT>
 cc_status sample_phase(const Graph &g, const cc_sample_opt &so, const cc_finish_opt &fo, uint32_t *P, Work &w,
-                       const DeviceInfo *di, const Dev &d, cudaStream_t s, int32_t *info) {
+                       const DeviceInfo *di, const Dev &d, cudaStream_t s, int32_t *info, uint32_t *count_into) {
     const unsigned gv = grid_for(di, g.n, TPB);
     *info = 0;
     if (so.kind == CC_SAMPLE_BFS) return bfs_sample<OffT>(g, so, P, w, di, d, s, info);
     if (so.kind == CC_SAMPLE_LDD) return ldd_sample<OffT>(g, so, P, w, di, d, s, info);
-    {
-        CC_PROF("k_iota", s);
-        k_iota<<<gv, TPB, 0, s>>>(P, g.n);
+    if (so.kind == CC_SAMPLE_NONE) {
+        {
+            CC_PROF("k_iota", s);
+            k_iota<<<gv, TPB, 0, s>>>(P, g.n);
+        }
+        CC_LAUNCH();
+        return CC_OK;
     }
-    CC_LAUNCH();
-    if (so.kind == CC_SAMPLE_NONE) return CC_OK;
     // k-out: union-find over the picked edges, then full compression
     return with_engine(fo, [&](auto eng) -> cc_status {
         using E = decltype(eng);
+        const OffT *I = static_cast<const OffT *>(g.I);
+        uint32_t *defer = w.sc.at<uint32_t>(w.o_defer);
+        Ctl *ctl = w.ctl();
+        CC_TRY(cudaMemsetAsync(&ctl->ndefer, 0, 4, s));
         {
-            CC_PROF("k_kout", s);
-            k_kout<OffT, E><<<gv, TPB, 0, s>>>(static_cast<const OffT *>(g.I), g.A, g.n, g.m, so.k, so.seed, P, d);
+            CC_PROF("k_kout_hook_first", s);
+            k_kout_hook_first<OffT><<<gv, TPB, 0, s>>>(I, g.A, g.n, g.m, P, defer, &ctl->ndefer, d);
         }
         {
-            CC_PROF("k_shortcut", s);
-            k_shortcut<<<gv, TPB, 0, s>>>(P, nullptr, g.n, d);
+            CC_PROF("k_kout_defer", s);
+            k_kout_defer<OffT, E><<<gv, TPB, 0, s>>>(I, g.A, g.n, g.m, P, defer, &ctl->ndefer, d);
+        }
+        if (so.k > 1) {
+            {
+                CC_PROF("k_compress_mid", s);
+                k_shortcut<false><<<gv, TPB, 0, s>>>(P, nullptr, g.n, nullptr, d);
+            }
+            CC_PROF("k_kout_rest", s);
+            launch_kout<OffT, E>(gv, s, I, g.A, g.n, g.m, so.k, so.seed, P, d, 1u, so.k);
+        }
+        if (count_into) {
+            CC_TRY(cudaMemsetAsync(count_into, 0, (size_t)g.n * 4, s));
+            CC_PROF("k_compress_count", s);
+            k_shortcut<true><<<gv, TPB, 0, s>>>(P, nullptr, g.n, count_into, d);
+        } else {
+            CC_PROF("k_compress", s);
+            k_shortcut<false><<<gv, TPB, 0, s>>>(P, nullptr, g.n, nullptr, d);
         }
         CC_LAUNCH();
         return CC_OK;
     });
 }
 
+// flat: labels form a flat forest (as sampling leaves them); counted: the
+// count array was already filled (k-out's compression counts as it goes).
 cc_status identify_phase(const uint32_t *L, uint32_t n, uint32_t samples, uint64_t seed, uint32_t *lmax_out,
-                         Work &w, const DeviceInfo *di, const Dev &d, cudaStream_t s) {
+                         Work &w, const DeviceInfo *di, const Dev &d, cudaStream_t s, bool flat, bool counted) {
     if (samples) {
         {
             CC_PROF("k_freq_sampled", s);
@@ -881,12 +1092,13 @@ cc_status identify_phase(const uint32_t *L, uint32_t n, uint32_t samples, uint64
     uint32_t *cnt = w.sc.at<uint32_t>(w.o_counts);
     Ctl *ctl = w.ctl();
     const unsigned gv = grid_for(di, n, TPB);
-    CC_TRY(cudaMemsetAsync(cnt, 0, (size_t)n * 4, s));
-    CC_TRY(cudaMemsetAsync(&ctl->key, 0, 8, s));
-    {
+    if (!counted) {
+        CC_TRY(cudaMemsetAsync(cnt, 0, (size_t)n * 4, s));
         CC_PROF("k_count_labels", s);
-        k_count_labels<<<gv, TPB, 0, s>>>(L, n, cnt, d);
+        if (flat) k_count_labels<true><<<gv, TPB, 0, s>>>(L, n, cnt, d);
+        else k_count_labels<false><<<gv, TPB, 0, s>>>(L, n, cnt, d);
     }
+    CC_TRY(cudaMemsetAsync(&ctl->key, 0, 8, s));
     {
         CC_PROF("k_argmax_counts", s);
         k_argmax_counts<<<gv, TPB, 0, s>>>(cnt, n, &ctl->key);
@@ -951,8 +1163,8 @@ cc_status finish_phase(const Graph &g, const cc_finish_opt &fo, const uint32_t *
         });
         if (st != CC_OK) return st;
         {
-            CC_PROF("k_shortcut", s);
-            k_shortcut<<<gv, TPB, 0, s>>>(P, nullptr, n, d);
+            CC_PROF("k_final_shortcut", s);
+            k_shortcut<false><<<gv, TPB, 0, s>>>(P, nullptr, n, nullptr, d);
         }
         CC_LAUNCH();
         return CC_OK;
@@ -1008,7 +1220,7 @@ cc_status finish_phase(const Graph &g, const cc_finish_opt &fo, const uint32_t *
         }
         {
             CC_PROF("k_shortcut", s);
-            k_shortcut<<<gv, TPB, 0, s>>>(P, prev, n, d);
+            k_shortcut<false><<<gv, TPB, 0, s>>>(P, prev, n, nullptr, d);
         }
         CC_LAUNCH();
         ++rounds;
@@ -1038,11 +1250,12 @@ cc_status run_static(const Graph &g, const cc_sample_opt &so, const cc_finish_op
     if (st != CC_OK) return st;
     CC_TRY(cudaMemsetAsync(w.ctl(), 0, sizeof(Ctl), s));
     int32_t info = 0;
-    st = sample_phase<OffT>(g, so, fo, P, w, di, d, s, &info);
+    const bool fused = so.kind == CC_SAMPLE_KOUT && so.freq_samples == 0;
+    st = sample_phase<OffT>(g, so, fo, P, w, di, d, s, &info, fused ? w.sc.at<uint32_t>(w.o_counts) : nullptr);
     if (st != CC_OK) return st;
     const uint32_t *lmax_p = nullptr;
     if (so.kind != CC_SAMPLE_NONE) {
-        st = identify_phase(P, g.n, so.freq_samples, so.seed, &w.ctl()->lmax, w, di, d, s);
+        st = identify_phase(P, g.n, so.freq_samples, so.seed, &w.ctl()->lmax, w, di, d, s, true, fused);
         if (st != CC_OK) return st;
         lmax_p = &w.ctl()->lmax;
     }
@@ -1136,8 +1349,8 @@ cc_status cc_sample(const void *offsets, int offsets_u64, const uint32_t *edges,
     CC_TRY(cudaMemsetAsync(w.ctl(), 0, sizeof(Ctl), s));
     int32_t info = 0;
     const Dev d = make_dev(di, n);
-    st = offsets_u64 ? sample_phase<uint64_t>(g, so, fo, labels_out, w, di, d, s, &info)
-                     : sample_phase<uint32_t>(g, so, fo, labels_out, w, di, d, s, &info);
+    st = offsets_u64 ? sample_phase<uint64_t>(g, so, fo, labels_out, w, di, d, s, &info, nullptr)
+                     : sample_phase<uint32_t>(g, so, fo, labels_out, w, di, d, s, &info, nullptr);
     if (st != CC_OK) return st;
     if (sample_info_out) {
         CC_TRY(cudaStreamSynchronize(s));
@@ -1165,7 +1378,7 @@ cc_status cc_identify_frequent(const uint32_t *labels, uint32_t n, uint32_t freq
     if (freq_samples == 0) w.o_counts = w.sc.reserve((size_t)n * 4);
     cc_status st = w.sc.alloc(s);
     if (st != CC_OK) return st;
-    return identify_phase(labels, n, freq_samples, seed, lmax_out, w, di, make_dev(di, n), s);
+    return identify_phase(labels, n, freq_samples, seed, lmax_out, w, di, make_dev(di, n), s, false, false);
 }
 
 cc_status cc_finish(const void *offsets, int offsets_u64, const uint32_t *edges, uint32_t n, uint64_t m,
