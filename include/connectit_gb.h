@@ -146,6 +146,26 @@ cc_status cc_finish(const void *offsets, int offsets_u64, const uint32_t *edges,
                     uint64_t m, const cc_finish_opt *finish, uint32_t lmax, uint32_t *labels_inout,
                     uint32_t *rounds_out, void *stream);
 
+/* IdentifyFrequent without allocating (no counterpart in the paper: it is
+ * for callers that cannot allocate device memory where they need L_max,
+ * e.g. a latency-critical serving loop where cudaMalloc / cudaFree would
+ * synchronise the device, a host callback where allocation calls are not
+ * allowed, or a process whose device memory another allocator owns).
+ * Same result as cc_identify_frequent with freq_samples = 0: *lmax_out
+ * (DEVICE uint32) <- the most frequent label of labels[0..n), ties to the
+ * smallest (0xFFFFFFFF when n == 0).  Its count scratch is a fixed
+ * file-scope device array of CC_NOALLOC_MAX_LABELS uint32 (16 MiB plus one
+ * word), reserved on every GPU that loads the library until the process
+ * exits.  n > CC_NOALLOC_MAX_LABELS returns CC_ERR_INVALID before anything
+ * is enqueued.  The first call on a device looks up the scratch's device
+ * address (a one-time set-up, done with that device current); make that
+ * first call before any stream capture.  Every call reuses the same
+ * scratch and zeroes the part it needs first, so calls whose work could
+ * overlap on the GPU (unordered streams) race and must not be issued.
+ * Label ids >= n are skipped and flagged (CC_DEVERR_BAD_EDGE). */
+#define CC_NOALLOC_MAX_LABELS (1u << 22)
+cc_status cc_identify_frequent_noalloc(const uint32_t *labels, uint32_t n, uint32_t *lmax_out, void *stream);
+
 /* Batch-incremental connectivity (Section 3.5, Algorithm 3; Appendix B.4).
  * A handle owns a resident parent array P (n uint32 in device memory).
  * cc_incr_create runs Initialize: static connectivity of the base graph

@@ -79,6 +79,8 @@ _SIGS = {
                                  ctypes.c_void_p]),
     "cc_identify_frequent": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64,
                                             ctypes.c_void_p, ctypes.c_void_p]),
+    "cc_identify_frequent_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p,
+                                                    ctypes.c_void_p]),
     "cc_finish": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64,
                                  ctypes.POINTER(FinishOpt), ctypes.c_uint32, ctypes.c_void_p,
                                  ctypes.POINTER(ctypes.c_uint32), ctypes.c_void_p]),
@@ -219,6 +221,23 @@ def cc_identify_frequent(labels: torch.Tensor, freq_samples: int = 0, seed: int 
         out = torch.empty(1, dtype=torch.int32, device=labels.device)
     _check(lib().cc_identify_frequent(ctypes.c_void_p(labels.data_ptr()), labels.numel(), freq_samples, seed,
                                       ctypes.c_void_p(out.data_ptr()), _stream(stream)), "cc_identify_frequent")
+    return out
+
+
+NOALLOC_MAX_LABELS = 1 << 22
+
+
+def cc_identify_frequent_noalloc(labels: torch.Tensor, out=None, stream=None):
+    """Exact IdentifyFrequent that allocates nothing on the device (for
+    callers that cannot allocate there); at most NOALLOC_MAX_LABELS labels.
+    Calls must not overlap on the GPU: they share one scratch array."""
+    _dev(labels, (torch.int32,), "labels")
+    if out is None:
+        raise ValueError("pass a preallocated 1-element int32 CUDA tensor as out")
+    _dev(out, (torch.int32,), "out")
+    _check(lib().cc_identify_frequent_noalloc(ctypes.c_void_p(labels.data_ptr()), labels.numel(),
+                                              ctypes.c_void_p(out.data_ptr()), _stream(stream)),
+           "cc_identify_frequent_noalloc")
     return out
 
 
