@@ -58,6 +58,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--combos", action="store_true", help="also time every sampling x finish combination")
+    p.add_argument("--batched-graphs", type=int, default=10000)
+    p.add_argument("--no-batched", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     return p.parse_args()
 
@@ -293,6 +295,9 @@ def run_ours(args):
     if args.combos:
         out["combos"] = bench_combos(args, cc, off, edg, labels, lab, m)
 
+    if not args.no_batched:
+        out["batched"] = bench_batched(args, cc, synth, dev)
+
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(off, edg, args.cpu_seconds)
     if dist:
@@ -320,6 +325,46 @@ def bench_combos(args, cc, off, edg, labels, ref, m):
             ms = e0.elapsed_time(e1) / reps
             res[f"{s}+{f}"] = {"ms": round(ms, 3), "gedges_s": round(m / (ms * 1e-3) / 1e9, 2), "exact": same}
     return res
+
+
+def bench_batched(args, cc, synth, dev):
+    """Many small graphs: one autotuned persistent launch vs one cc_static
+    call per graph (no sampling, union-find finish), same labels."""
+    import torch
+    t0 = time.time()
+    gs = synth.batch_config3(args.batched_graphs, seed=1)
+    gv, off, edg = synth.pack(gs)
+    gen_s = time.time() - t0
+    gv, off, edg = gv.to(dev), off.to(dev), edg.to(dev)
+    V, M = off.numel() - 1, edg.numel()
+    lab, best, tune_ms = cc.cc_batched_autotune(gv, off, edg)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 10
+    e0.record()
+    for _ in range(reps):
+        cc.cc_batched(gv, off, edg, best, lab)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_batched = e0.elapsed_time(e1) / reps
+    # one plain launch per graph, on the same packed arrays
+    ref = torch.empty_like(lab)
+    gvh = gv.cpu().tolist()
+    so, fo = cc.sample_opt("none"), cc.finish_opt("uf_rem_cas")
+    torch.cuda.synchronize()
+    e0.record()
+    for i in range(len(gs)):
+        b, e = gvh[i], gvh[i + 1]
+        if e > b:
+            cc.cc_static(off[b:e + 1], edg, so, fo, ref[b:e])
+    e1.record()
+    torch.cuda.synchronize()
+    ms_plain = e0.elapsed_time(e1)
+    return {"graphs": len(gs), "vertices": V, "edges": M, "gen_s": round(gen_s, 1),
+            "schedule": {"threads": best.threads, "smem_max_vertices": best.smem_max_vertices,
+                         "vertex_mode": best.vertex_mode},
+            "ms_batched": round(ms_batched, 4), "edges_per_s_batched": round(M / (ms_batched * 1e-3), 1),
+            "ms_per_graph_launches": round(ms_plain, 3), "edges_per_s_per_graph_launches": round(M / (ms_plain * 1e-3), 1),
+            "speedup": round(ms_plain / ms_batched, 2), "labels_equal": bool(torch.equal(lab, ref))}
 
 
 def bench_incremental(args, cc, synth, dev):

@@ -16,6 +16,10 @@
  * Result: canonical labels, labels[v] = the smallest vertex id of v's
  *   connected component (a connectivity labelling, Section 2, in the unique
  *   min-id form).  Every sampling x finish combination writes the same array.
+ * Alignment: every array must be aligned to its element size (uint64 to 8,
+ *   uint32 to 4 bytes); a misaligned pointer returns CC_ERR_INVALID.  Any
+ *   sub-slice of an array is fine; wider vector accesses are used only where
+ *   the library has checked the address.
  * Memory: every array argument is a DEVICE pointer owned by the caller,
  *   except in cc_static_host, whose arrays are host pointers.  The library
  *   allocates only its own scratch (stream-ordered, cudaMallocAsync on the
@@ -165,6 +169,39 @@ cc_status cc_finish(const void *offsets, int offsets_u64, const uint32_t *edges,
  * Label ids >= n are skipped and flagged (CC_DEVERR_BAD_EDGE). */
 #define CC_NOALLOC_MAX_LABELS (1u << 22)
 cc_status cc_identify_frequent_noalloc(const uint32_t *labels, uint32_t n, uint32_t *lmax_out, void *stream);
+
+/* Batched static connectivity of many independent graphs in one persistent
+ * launch (no counterpart in the paper, which labels one graph per call).
+ * Each graph is labelled as Algorithm 1 with no sampling would label it:
+ * union-find finish (Rem's CAS rule, Algorithm 14) and final shortcut.
+ * Packing: G graphs; gv (DEVICE uint64[G+1], gv[0] = 0, non-decreasing,
+ *   gv[G] = V) gives graph g the packed vertices [gv[g], gv[g+1]).
+ *   offsets (DEVICE, V+1 entries, uint32 or uint64 per offsets_u64) is one
+ *   packed CSR: local vertex i of graph g has its neighbours at
+ *   edges[offsets[gv[g]+i] .. offsets[gv[g]+i+1]), stored as LOCAL ids in
+ *   [0, n_g).  M = total directed edges.  Every graph must be symmetric.
+ * labels_out (DEVICE uint32[V]): local vertex i of graph g gets the smallest
+ *   local id of its component.
+ * opt: schedule; NULL = cc_batch_default_opt.  threads per CTA in
+ *   {128, 256, 512, 1024}; graphs of at most smem_max_vertices vertices
+ *   (<= 51200) keep their parent array in shared memory, larger ones in
+ *   their slice of labels_out; vertex_mode 0 = one thread per vertex,
+ *   1 = one warp per vertex.  Any schedule gives the same labels.
+ * cc_batched_autotune times every candidate schedule on this batch (it
+ *   synchronises), writes the fastest to *best_out (host) and its time in
+ *   ms to *best_ms_out (host, may be NULL), and leaves labels_out computed. */
+typedef struct cc_batch_opt {
+    uint32_t threads;
+    uint32_t smem_max_vertices;
+    uint32_t vertex_mode;
+    uint32_t reserved;      /* must be 0 */
+} cc_batch_opt;
+void cc_batch_default_opt(cc_batch_opt *opt);
+cc_status cc_batched(const uint64_t *gv, uint32_t G, const void *offsets, int offsets_u64, const uint32_t *edges,
+                     uint64_t V, uint64_t M, const cc_batch_opt *opt, uint32_t *labels_out, void *stream);
+cc_status cc_batched_autotune(const uint64_t *gv, uint32_t G, const void *offsets, int offsets_u64,
+                              const uint32_t *edges, uint64_t V, uint64_t M, uint32_t *labels_out,
+                              cc_batch_opt *best_out, float *best_ms_out, void *stream);
 
 /* Batch-incremental connectivity (Section 3.5, Algorithm 3; Appendix B.4).
  * A handle owns a resident parent array P (n uint32 in device memory).

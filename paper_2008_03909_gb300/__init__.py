@@ -55,6 +55,11 @@ class KernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_uint64), ("ms", ctypes.c_double)]
 
 
+class BatchOpt(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_uint32), ("smem_max_vertices", ctypes.c_uint32),
+                ("vertex_mode", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("lmax", ctypes.c_uint32), ("sample_info", ctypes.c_int32), ("rounds", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32), ("edges_finish", ctypes.c_uint64)]
@@ -84,6 +89,14 @@ _SIGS = {
     "cc_finish": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64,
                                  ctypes.POINTER(FinishOpt), ctypes.c_uint32, ctypes.c_void_p,
                                  ctypes.POINTER(ctypes.c_uint32), ctypes.c_void_p]),
+    "cc_batch_default_opt": (None, [ctypes.POINTER(BatchOpt)]),
+    "cc_batched": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                  ctypes.c_uint64, ctypes.c_uint64, ctypes.POINTER(BatchOpt), ctypes.c_void_p,
+                                  ctypes.c_void_p]),
+    "cc_batched_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_int,
+                                           ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p,
+                                           ctypes.POINTER(BatchOpt), ctypes.POINTER(ctypes.c_float),
+                                           ctypes.c_void_p]),
     "cc_incr_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint32,
                                       ctypes.c_uint64, ctypes.POINTER(SampleOpt), ctypes.POINTER(FinishOpt),
                                       ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
@@ -279,6 +292,41 @@ def profile_read() -> dict:
     arr = (KernelTime * max(cnt, 1))()
     cnt = L.cc_profile_read(ctypes.cast(arr, ctypes.c_void_p), cnt)
     return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].ms)) for i in range(cnt)}
+
+
+def batch_opt(threads=256, smem_max_vertices=12288, vertex_mode=0) -> BatchOpt:
+    return BatchOpt(threads, smem_max_vertices, vertex_mode, 0)
+
+
+def _batch_args(gv, offsets, edges):
+    _dev(gv, (torch.int64,), "gv")
+    _dev(offsets, (torch.int32, torch.int64), "offsets")
+    _dev(edges, (torch.int32,), "edges")
+    return (ctypes.c_void_p(gv.data_ptr()), gv.numel() - 1, ctypes.c_void_p(offsets.data_ptr()),
+            1 if offsets.dtype == torch.int64 else 0, ctypes.c_void_p(edges.data_ptr() if edges.numel() else 0),
+            offsets.numel() - 1, edges.numel())
+
+
+def cc_batched(gv, offsets, edges, opt: BatchOpt | None = None, labels_out=None, stream=None):
+    """Local min-id labels of every packed graph (see connectit_gb.h)."""
+    a = _batch_args(gv, offsets, edges)
+    if labels_out is None:
+        labels_out = torch.empty(a[5], dtype=torch.int32, device=offsets.device)
+    _check(lib().cc_batched(*a, ctypes.byref(opt) if opt is not None else None,
+                            ctypes.c_void_p(labels_out.data_ptr()), _stream(stream)), "cc_batched")
+    return labels_out
+
+
+def cc_batched_autotune(gv, offsets, edges, labels_out=None, stream=None):
+    """Time every schedule on this batch; returns (labels, best BatchOpt, best ms)."""
+    a = _batch_args(gv, offsets, edges)
+    if labels_out is None:
+        labels_out = torch.empty(a[5], dtype=torch.int32, device=offsets.device)
+    best = BatchOpt()
+    ms = ctypes.c_float(0)
+    _check(lib().cc_batched_autotune(*a, ctypes.c_void_p(labels_out.data_ptr()), ctypes.byref(best),
+                                     ctypes.byref(ms), _stream(stream)), "cc_batched_autotune")
+    return labels_out, best, ms.value
 
 
 class Incremental:

@@ -65,6 +65,9 @@ cc_status check_graph(const void *offsets, int offsets_u64, const uint32_t *edge
     if (n == 0) return CC_OK;
     if (!offsets) return CC_ERR_INVALID;
     if (m > 0 && !edges) return CC_ERR_INVALID;
+    // naturally aligned elements (the kernels never assume more than this)
+    if (reinterpret_cast<uintptr_t>(offsets) % (offsets_u64 ? 8 : 4) != 0) return CC_ERR_INVALID;
+    if (edges && reinterpret_cast<uintptr_t>(edges) % 4 != 0) return CC_ERR_INVALID;
     if (!offsets_u64 && m > 0xFFFFFFFFull) return CC_ERR_INVALID;
     return CC_OK;
 }

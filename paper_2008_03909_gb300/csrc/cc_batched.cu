@@ -1,0 +1,244 @@
+// cc_batched.cu -- static connectivity of many independent small graphs in
+// one persistent launch (a packed form of Algorithm 1 with no sampling: the
+// union-find finish of Algorithm 7 with Rem's CAS rule, Algorithm 14, then
+// the final shortcut).  There is no counterpart in the paper, which labels
+// one graph per call.
+//
+// Each CTA takes whole graphs from a global queue.  A graph of at most
+// `smem_max_vertices` vertices keeps its parent array in shared memory
+// (block-local atomics, one global write per vertex at the end); a larger
+// one uses its own slice of the output as the parent array.  Vertices are
+// mapped one per thread or one per warp.  cc_batched_autotune times the
+// candidate schedules on the caller's batch and returns the fastest.
+#include <vector>
+
+#include "cc_internal.h"
+
+using namespace ccg;
+
+namespace {
+
+// Rem-CAS union on a parent array in shared or global memory, read through
+// volatile loads (coherent for the block in shared memory, L2 in global).
+__device__ __forceinline__ void unite_any(uint32_t *P, uint32_t u, uint32_t v, const Dev &d) {
+    volatile uint32_t *VP = P;
+    uint32_t ru = u, rv = v, pru = VP[ru], prv = VP[rv];
+    Guard g;
+    while (pru != prv) {
+        if (pru < prv) {
+            uint32_t t = ru; ru = rv; rv = t;
+            t = pru; pru = prv; prv = t;
+        }
+        if (ru == pru) {
+            uint32_t old = atomicCAS(P + ru, ru, prv);
+            if (old == ru) return;
+            pru = old;
+        } else {
+            uint32_t w = VP[pru];
+            if (pru != w) atomicCAS(P + ru, pru, w);
+            ru = pru;
+            pru = w;
+        }
+        if (!g.step(d)) return;
+    }
+}
+
+__device__ __forceinline__ uint32_t root_any(const uint32_t *P, uint32_t x, const Dev &d) {
+    const volatile uint32_t *VP = P;
+    uint32_t p = VP[x];
+    Guard g;
+    while (p != x) {
+        x = p;
+        p = VP[x];
+        if (!g.step(d)) break;
+    }
+    return x;
+}
+
+// MODE 0: one thread per vertex; MODE 1: one warp per vertex.
+template <typename OffT, int MODE>
+__global__ void k_batched(const uint64_t *gv, uint32_t G, uint64_t V, const OffT *I, const uint32_t *A, uint64_t M,
+                          uint32_t *labels, uint32_t *queue, uint32_t smem_max, Dev d) {
+    extern __shared__ uint32_t Ps[];
+    __shared__ uint32_t g_cur;
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        if (threadIdx.x == 0) g_cur = atomicAdd(queue, 1u);
+        __syncthreads();
+        const uint32_t g = g_cur;
+        __syncthreads();
+        if (g >= G) break;
+        const uint64_t vb = gv[g], ve = gv[g + 1];
+        if (ve < vb || ve > V || ve - vb > 0xFFFFFFFEull) {
+            if (threadIdx.x == 0) atomicOr(d.err, ERR_BAD_OFFSETS);
+            continue;
+        }
+        const uint32_t ng = (uint32_t)(ve - vb);
+        const bool local = ng <= smem_max;
+        uint32_t *P = local ? Ps : labels + vb;
+        Dev dg = d;
+        if (dg.cap == 0) dg.cap = 2ull * ng + 1024;
+        for (uint32_t i = threadIdx.x; i < ng; i += blockDim.x) P[i] = i;
+        __syncthreads();
+        // apply each undirected edge once, from its larger endpoint
+        if (MODE == 0) {
+            for (uint32_t i = threadIdx.x; i < ng; i += blockDim.x) {
+                uint64_t b, e;
+                clamp_range((uint64_t)ld_off(I + vb + i), (uint64_t)ld_off(I + vb + i + 1), M, b, e, d);
+                for (uint64_t x = b; x < e; ++x) {
+                    const uint32_t v = ld_stream(A + x);
+                    if (v >= ng) { atomicOr(d.err, ERR_BAD_EDGE); continue; }
+                    if (v < i) unite_any(P, i, v, dg);
+                }
+            }
+        } else {
+            const uint32_t wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+            for (uint32_t i = wid; i < ng; i += nwarp) {
+                uint64_t b, e;
+                clamp_range((uint64_t)ld_off(I + vb + i), (uint64_t)ld_off(I + vb + i + 1), M, b, e, d);
+                for (uint64_t x = b + lane; x < e; x += 32) {
+                    const uint32_t v = ld_stream(A + x);
+                    if (v >= ng) { atomicOr(d.err, ERR_BAD_EDGE); continue; }
+                    if (v < i) unite_any(P, i, v, dg);
+                }
+            }
+        }
+        __syncthreads();
+        // final shortcut: the root of each tree is its smallest vertex
+        if (local) {
+            for (uint32_t i = threadIdx.x; i < ng; i += blockDim.x) labels[vb + i] = root_any(P, i, dg);
+        } else {
+            for (uint32_t i = threadIdx.x; i < ng; i += blockDim.x) P[i] = root_any(P, i, dg);
+        }
+        __syncthreads();
+    }
+}
+
+cc_status check_batch_opt(const cc_batch_opt &o) {
+    if (o.threads != 128 && o.threads != 256 && o.threads != 512 && o.threads != 1024) return CC_ERR_INVALID;
+    if (o.smem_max_vertices > (200u * 1024u) / 4u) return CC_ERR_INVALID;
+    if (o.vertex_mode > 1 || o.reserved != 0) return CC_ERR_INVALID;
+    return CC_OK;
+}
+
+template <typename OffT>
+cc_status launch_batched(const uint64_t *gv, uint32_t G, uint64_t V, const void *offsets, const uint32_t *edges,
+                         uint64_t M, const cc_batch_opt &o, uint32_t *labels, uint32_t *queue, cudaStream_t s) {
+    const DeviceInfo *di = device_info();
+    if (!di) return CC_ERR_CUDA;
+    const size_t smem = (size_t)o.smem_max_vertices * 4;
+    const void *fn = o.vertex_mode ? (const void *)k_batched<OffT, 1> : (const void *)k_batched<OffT, 0>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, (int)o.threads, smem);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (per_sm < 1) return CC_ERR_INVALID;
+    uint64_t grid = (uint64_t)per_sm * di->sms;
+    if (grid > G) grid = G;
+    if (grid == 0) grid = 1;
+    // cap 0: each graph gets 2 n_g + 1024 steps per loop (a test override wins)
+    const uint64_t lc = loop_cap(0);
+    const Dev d = Dev{di->err, lc == 1024 ? 0 : lc};
+    e = cudaMemsetAsync(queue, 0, 4, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    CC_PROF("k_batched", s);
+    if (o.vertex_mode)
+        k_batched<OffT, 1><<<(unsigned)grid, o.threads, smem, s>>>(gv, G, V, static_cast<const OffT *>(offsets),
+                                                                    edges, M, labels, queue, o.smem_max_vertices, d);
+    else
+        k_batched<OffT, 0><<<(unsigned)grid, o.threads, smem, s>>>(gv, G, V, static_cast<const OffT *>(offsets),
+                                                                    edges, M, labels, queue, o.smem_max_vertices, d);
+    return from_cuda(cudaGetLastError());
+}
+
+cc_status batched_args(const uint64_t *gv, uint32_t G, const void *offsets, int offsets_u64, const uint32_t *edges,
+                       uint64_t V, uint64_t M, uint32_t *labels_out) {
+    if (G == 0 || V == 0) return CC_OK;
+    if (!gv || !offsets || !labels_out || (M > 0 && !edges)) return CC_ERR_INVALID;
+    if (!aligned(gv, 8) || !aligned(offsets, offsets_u64 ? 8 : 4) || !aligned(labels_out, 4) ||
+        (edges && !aligned(edges, 4)))
+        return CC_ERR_INVALID;
+    if (!offsets_u64 && M > 0xFFFFFFFFull) return CC_ERR_INVALID;
+    return CC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void cc_batch_default_opt(cc_batch_opt *o) {
+    if (!o) return;
+    o->threads = 256;
+    o->smem_max_vertices = 12288;
+    o->vertex_mode = 0;
+    o->reserved = 0;
+}
+
+cc_status cc_batched(const uint64_t *gv, uint32_t G, const void *offsets, int offsets_u64, const uint32_t *edges,
+                     uint64_t V, uint64_t M, const cc_batch_opt *opt, uint32_t *labels_out, void *stream) {
+    cc_status st = batched_args(gv, G, offsets, offsets_u64, edges, V, M, labels_out);
+    if (st != CC_OK || G == 0 || V == 0) return st;
+    cc_batch_opt o;
+    cc_batch_default_opt(&o);
+    if (opt) o = *opt;
+    if ((st = check_batch_opt(o)) != CC_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Scratch sc;
+    const size_t oq = sc.reserve(4);
+    if ((st = sc.alloc(s)) != CC_OK) return st;
+    return offsets_u64 ? launch_batched<uint64_t>(gv, G, V, offsets, edges, M, o, labels_out, sc.at<uint32_t>(oq), s)
+                       : launch_batched<uint32_t>(gv, G, V, offsets, edges, M, o, labels_out, sc.at<uint32_t>(oq), s);
+}
+
+cc_status cc_batched_autotune(const uint64_t *gv, uint32_t G, const void *offsets, int offsets_u64,
+                              const uint32_t *edges, uint64_t V, uint64_t M, uint32_t *labels_out,
+                              cc_batch_opt *best_out, float *best_ms_out, void *stream) {
+    cc_status st = batched_args(gv, G, offsets, offsets_u64, edges, V, M, labels_out);
+    if (st != CC_OK) return st;
+    if (!best_out) return CC_ERR_INVALID;
+    cc_batch_default_opt(best_out);
+    if (best_ms_out) *best_ms_out = 0.f;
+    if (G == 0 || V == 0) return CC_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<cc_batch_opt> cands;
+    for (uint32_t mode : {0u, 1u})
+        for (uint32_t threads : {128u, 256u, 512u, 1024u})
+            for (uint32_t smem : {0u, 4096u, 12288u, 24576u, 49152u})
+                cands.push_back(cc_batch_opt{threads, smem, mode, 0});
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return CC_ERR_CUDA;
+    float best = -1.f;
+    for (const cc_batch_opt &c : cands) {
+        // one untimed run, then the better of two timed runs
+        st = cc_batched(gv, G, offsets, offsets_u64, edges, V, M, &c, labels_out, stream);
+        if (st == CC_ERR_INVALID) continue;
+        if (st != CC_OK) break;
+        float ms = 1e30f;
+        for (int r = 0; r < 2; ++r) {
+            cudaEventRecord(e0, s);
+            st = cc_batched(gv, G, offsets, offsets_u64, edges, V, M, &c, labels_out, stream);
+            cudaEventRecord(e1, s);
+            if (st != CC_OK) break;
+            cudaEventSynchronize(e1);
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            ms = t < ms ? t : ms;
+        }
+        if (st != CC_OK) break;
+        if (best < 0.f || ms < best) {
+            best = ms;
+            *best_out = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != CC_OK && st != CC_ERR_INVALID) return st;
+    if (best_ms_out) *best_ms_out = best;
+    // leave labels_out computed with the winning schedule
+    return cc_batched(gv, G, offsets, offsets_u64, edges, V, M, best_out, labels_out, stream);
+}
+
+}  // extern "C"

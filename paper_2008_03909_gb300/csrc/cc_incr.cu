@@ -154,7 +154,7 @@ cc_status cc_incr_create(const void *offsets, int offsets_u64, const uint32_t *e
 cc_status cc_incr_insert_batch(cc_incr *h, const uint32_t *pairs, uint64_t k, void *stream) {
     if (!h) return CC_ERR_INVALID;
     if (k == 0) return CC_OK;
-    if (!pairs) return CC_ERR_INVALID;
+    if (!pairs || !aligned(pairs, 4)) return CC_ERR_INVALID;
     if (h->n == 0) return CC_ERR_INVALID;
     const DeviceInfo *di = device_info();
     if (!di) return CC_ERR_CUDA;
@@ -174,7 +174,7 @@ cc_status cc_incr_insert_batch(cc_incr *h, const uint32_t *pairs, uint64_t k, vo
 cc_status cc_incr_query_batch(cc_incr *h, const uint32_t *pairs, uint64_t q, uint8_t *answers_out, void *stream) {
     if (!h) return CC_ERR_INVALID;
     if (q == 0) return CC_OK;
-    if (!pairs || !answers_out || h->n == 0) return CC_ERR_INVALID;
+    if (!pairs || !answers_out || h->n == 0 || !aligned(pairs, 4)) return CC_ERR_INVALID;
     const DeviceInfo *di = device_info();
     if (!di) return CC_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -191,7 +191,7 @@ cc_status cc_incr_query_batch(cc_incr *h, const uint32_t *pairs, uint64_t q, uin
 cc_status cc_incr_labels(cc_incr *h, uint32_t *labels_out, void *stream) {
     if (!h) return CC_ERR_INVALID;
     if (h->n == 0) return CC_OK;
-    if (!labels_out) return CC_ERR_INVALID;
+    if (!labels_out || !aligned(labels_out, 4)) return CC_ERR_INVALID;
     const DeviceInfo *di = device_info();
     if (!di) return CC_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -28,6 +28,8 @@ uint32_t round_cap();
 
 inline Dev make_dev(const DeviceInfo *di, uint64_t n) { return Dev{di->err, loop_cap(n)}; }
 
+// CUDA error -> status (an allocation failure is CC_ERR_OOM, anything else,
+// e.g. an earlier sticky fault, CC_ERR_CUDA).
 cc_status from_cuda(cudaError_t e);
 
 // Grid for a loop over `work` items with `threads` per block, capped at a
@@ -53,9 +55,8 @@ class Scratch {
         if (total_ == 0) return CC_OK;
         cudaError_t e = cudaMallocAsync(&base_, total_, s);
         if (e != cudaSuccess) {
-            (void)cudaGetLastError();
             base_ = nullptr;
-            return CC_ERR_OOM;
+            return from_cuda(e);
         }
         stream_ = s;
         return CC_OK;
@@ -108,6 +109,7 @@ class LaunchScope {
 #define CC_PROF(name, stream) ::ccg::LaunchScope CC_CAT(cc_prof_, __LINE__)(name, stream)
 
 // Validation shared by the entry points (host side, synchronous).
+inline bool aligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 cc_status check_graph(const void *offsets, int offsets_u64, const uint32_t *edges, uint32_t n, uint64_t m);
 cc_status check_sample(const cc_sample_opt &s);
 cc_status check_finish(const cc_finish_opt &f);

@@ -106,6 +106,7 @@ extern "C" cc_status cc_identify_frequent_noalloc(const uint32_t *labels, uint32
                                                   void *stream) {
     if (!lmax_out || (n > 0 && !labels)) return CC_ERR_INVALID;
     if (n > CC_NOALLOC_MAX_LABELS) return CC_ERR_INVALID;
+    if (!aligned(lmax_out, 4) || (labels && !aligned(labels, 4))) return CC_ERR_INVALID;
     NoAllocScratch *sc = nullptr;
     cc_status st = noalloc_scratch(&sc);
     if (st != CC_OK) return st;

@@ -76,7 +76,11 @@ __device__ __forceinline__ void roots4(const uint32_t *P, uint32_t v0, uint32_t 
 
 template <bool COUNT>
 __global__ void __launch_bounds__(256, 8) k_shortcut(uint32_t *P, uint32_t *prev, uint32_t n, uint32_t *cnt, Dev d) {
-    const uint64_t n4 = n / 4;
+    // 16-byte vector accesses only when both arrays are 16-byte aligned (a
+    // caller's label buffer may be any 4-byte-aligned slice)
+    const bool vec = (reinterpret_cast<uintptr_t>(P) & 15) == 0 &&
+                     (prev == nullptr || (reinterpret_cast<uintptr_t>(prev) & 15) == 0);
+    const uint64_t n4 = vec ? n / 4 : 0;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     LabelCounter lc;
@@ -170,43 +174,57 @@ void launch_kout(unsigned grid, cudaStream_t s, const OffT *I, const uint32_t *A
 // vertex with w0 > v (all its neighbours larger) is queued for a real Union
 // in part two.  Four vertices per lane, vector loads and stores.
 template <typename OffT>
-__global__ void __launch_bounds__(256, 8) k_kout_hook_first(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, uint32_t *P,
-                                  uint32_t *defer, uint32_t *ndefer, Dev d) {
+__global__ void __launch_bounds__(256, 8) k_kout_hook_first(const OffT *I, const uint32_t *A, uint32_t n,
+                                                            uint64_t m, uint32_t *P, uint32_t *defer,
+                                                            uint32_t *ndefer, Dev d) {
     const int lane = threadIdx.x & 31;
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    uint64_t base = warp * 128;
+    // A warp step covers 128 consecutive vertices as four groups of 32;
+    // lane L owns vertex base + 32j + L, so each load instruction touches a
+    // contiguous stretch of offsets, first edges and labels.
+    // o[j] = I[base + 32j + L] (j < 4), o[4] = I[base + 128 + L].
     uint64_t o[5];
-    if (base < n) load_offsets5(I, base + 4 * lane, n, o);
+    uint64_t base = warp * 128;
+    auto load = [&](uint64_t bs) {
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            const uint64_t idx = bs + 32 * j + lane;
+            o[j] = idx <= n ? (uint64_t)ld_off(I + idx) : 0;
+        }
+    };
+    if (base < n) load(base);
     for (; base < n; base += nw * 128) {
-        const uint64_t v0 = base + 4 * lane;
-        uint32_t w[4], p[4], nd = 0;
+        uint64_t beg[4], end[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
+            const uint64_t nxt = __shfl_down_sync(0xFFFFFFFFu, o[j], 1);
+            const uint64_t first = __shfl_sync(0xFFFFFFFFu, o[j + 1], 0);
+            beg[j] = o[j];
+            end[j] = lane < 31 ? nxt : first;
+        }
+        uint32_t w[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint64_t v = base + 32 * j + lane;
             uint64_t b = 0, e = 0;
-            if (v0 + j < n) clamp_range(o[j], o[j + 1], m, b, e, d);
+            if (v < n) clamp_range(beg[j], end[j], m, b, e, d);
             w[j] = e > b ? ld_stream(A + b) : NONE;
         }
         // the next step's offsets load while this step's first edges are read
-        if (base + nw * 128 < n) load_offsets5(I, base + nw * 128 + 4 * lane, n, o);
+        if (base + nw * 128 < n) load(base + nw * 128);
+        uint32_t nd = 0;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const uint32_t v = (uint32_t)(v0 + j);
+            const uint64_t v = base + 32 * j + lane;
             if (w[j] != NONE && w[j] >= n) { atomicOr(d.err, ERR_BAD_EDGE); w[j] = NONE; }
-            p[j] = (w[j] != NONE && w[j] < v) ? w[j] : v;
+            if (v < n) P[v] = (w[j] != NONE && w[j] < v) ? w[j] : (uint32_t)v;
             nd += (w[j] != NONE && w[j] > v);
-        }
-        if (v0 + 3 < n && ((reinterpret_cast<uintptr_t>(P) & 15) == 0)) {
-            __stcg(reinterpret_cast<uint4 *>(P + v0), make_uint4(p[0], p[1], p[2], p[3]));
-        } else {
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (v0 + j < n) P[v0 + j] = p[j];
         }
         uint32_t slot = warp_append_full(ndefer, nd);
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-            if (w[j] != NONE && w[j] > (uint32_t)(v0 + j)) defer[slot++] = (uint32_t)(v0 + j);
+            if (w[j] != NONE && w[j] > base + 32 * j + lane) defer[slot++] = (uint32_t)(base + 32 * j + lane);
     }
 }
 
@@ -240,7 +258,7 @@ k_kout_defer(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, uint32_t 
 // counted; with none, every root ties at 1 and the answer is root 0.
 template <bool FLAT>
 __global__ void __launch_bounds__(256, 8) k_count_labels(const uint32_t *L, uint32_t n, uint32_t *cnt, Dev d) {
-    const uint64_t n4 = n / 4;
+    const uint64_t n4 = (reinterpret_cast<uintptr_t>(L) & 15) == 0 ? n / 4 : 0;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     LabelCounter lc;
@@ -280,7 +298,7 @@ __device__ __forceinline__ void keep_max(unsigned long long &best, uint32_t c, u
 __global__ void __launch_bounds__(256, 8) k_argmax_counts(const uint32_t *cnt, uint32_t n, unsigned long long *key) {
     __shared__ unsigned long long s[32];
     unsigned long long best = 0;
-    const uint64_t n4 = n / 4;
+    const uint64_t n4 = (reinterpret_cast<uintptr_t>(cnt) & 15) == 0 ? n / 4 : 0;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     for (uint64_t i = tid; i < n4; i += stride) {
@@ -1289,7 +1307,7 @@ cc_status cc_static_ex(const void *offsets, int offsets_u64, const uint32_t *edg
     cc_finish_opt fo;
     resolve_opts(sample, finish, so, fo);
     if ((st = check_sample(so)) != CC_OK || (st = check_finish(fo)) != CC_OK) return st;
-    if (n > 0 && !labels_out) return CC_ERR_INVALID;
+    if (n > 0 && (!labels_out || !aligned(labels_out, 4))) return CC_ERR_INVALID;
     if (n == 0) {
         if (stats) *stats = cc_stats{NONE, 0, 0, 0, 0};
         return CC_OK;
@@ -1338,7 +1356,7 @@ cc_status cc_sample(const void *offsets, int offsets_u64, const uint32_t *edges,
     resolve_opts(sample, nullptr, so, fo);
     if ((st = check_sample(so)) != CC_OK) return st;
     if (n == 0) return CC_OK;
-    if (!labels_out) return CC_ERR_INVALID;
+    if (!labels_out || !aligned(labels_out, 4)) return CC_ERR_INVALID;
     const DeviceInfo *di = device_info();
     if (!di) return CC_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1362,7 +1380,8 @@ cc_status cc_sample(const void *offsets, int offsets_u64, const uint32_t *edges,
 cc_status cc_identify_frequent(const uint32_t *labels, uint32_t n, uint32_t freq_samples, uint64_t seed,
                                uint32_t *lmax_out, void *stream) {
     if (n == 0xFFFFFFFFu || freq_samples > 4096) return CC_ERR_INVALID;
-    if (!lmax_out || (n > 0 && !labels)) return CC_ERR_INVALID;
+    if (!lmax_out || (n > 0 && !labels) || !aligned(lmax_out, 4) || (labels && !aligned(labels, 4)))
+        return CC_ERR_INVALID;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (n == 0) {
         {
@@ -1391,7 +1410,7 @@ cc_status cc_finish(const void *offsets, int offsets_u64, const uint32_t *edges,
     resolve_opts(nullptr, finish, so, fo);
     if ((st = check_finish(fo)) != CC_OK) return st;
     if (n == 0) return CC_OK;
-    if (!labels_inout) return CC_ERR_INVALID;
+    if (!labels_inout || !aligned(labels_inout, 4)) return CC_ERR_INVALID;
     const DeviceInfo *di = device_info();
     if (!di) return CC_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -284,3 +284,37 @@ def log_uniform_sizes(count: int, lo: float, hi: float, seed: int, stream: int) 
     h = hash3(seed, stream, torch.arange(count, dtype=torch.int64)).to(torch.float64) / 2**32
     vals = torch.exp(math.log(lo) + h * (math.log(hi) - math.log(lo)))
     return [int(round(x)) for x in vals.tolist()]
+
+
+def pack(graphs):
+    """Pack graphs into one CSR with per-graph vertex offsets: returns
+    (gv int64[G+1], offsets int64[V+1] with global edge positions, edges
+    int32[M] holding each graph's LOCAL vertex ids)."""
+    nv = [g.n for g in graphs]
+    gv = torch.zeros(len(graphs) + 1, dtype=torch.int64)
+    gv[1:] = torch.cumsum(torch.tensor(nv, dtype=torch.int64), 0)
+    offs, edgs, ebase = [torch.zeros(1, dtype=torch.int64)], [], 0
+    for g in graphs:
+        o = g.offsets.cpu()
+        offs.append(o[1:] + ebase)
+        edgs.append(g.edges.cpu())
+        ebase += g.m
+    return gv, torch.cat(offs), (torch.cat(edgs) if edgs else torch.zeros(0, dtype=torch.int32))
+
+
+def batch_config3(count: int, seed: int = 1, lo: int = 6, hi: int = 16):
+    """The batched workload: graph sizes log-uniform in [2^lo, 2^hi]; even
+    indices G(n, M) with average degree uniform in [0.5, 4], odd indices
+    w x h grids (w = floor(sqrt(n)), h = floor(n / w)) with drop probability
+    uniform in [0, 0.5]."""
+    sizes = log_uniform_sizes(count, 2.0 ** lo, 2.0 ** hi, seed, 500)
+    u = hash3(seed, 501, torch.arange(count, dtype=torch.int64)).to(torch.float64) / 2**32
+    graphs = []
+    for i, n in enumerate(sizes):
+        if i % 2 == 0:
+            graphs.append(erdos_renyi(n, 0.5 + 3.5 * float(u[i]), seed=seed * 100003 + i))
+        else:
+            w = max(1, int(math.isqrt(n)))
+            h = max(1, n // w)
+            graphs.append(grid2d(w, h, 0.5 * float(u[i]), seed=seed * 100003 + i))
+    return graphs

@@ -75,6 +75,9 @@ def test_validation_rejects_before_any_device_work():
     bad_fin = cc.finish_opt("uf_rem_cas")
     bad_fin.find = 7
     assert _call_static(8, 0, 8, 10, 5, fo=bad_fin, labels=1) == 1
+    assert _call_static(6, 1, 8, 10, 5, labels=16) == 1           # uint64 offsets not 8-aligned
+    assert _call_static(8, 0, 6, 10, 5, labels=16) == 1           # edges not 4-aligned
+    assert _call_static(8, 0, 8, 10, 5, labels=18) == 1           # labels not 4-aligned
     res = cc.sample_opt()
     res.reserved = 3
     assert _call_static(8, 0, 8, 10, 5, so=res, labels=1) == 1

@@ -227,3 +227,22 @@ def test_iteration_cap_reports_nonconvergence():
     cc.device_error()
     got, _ = gpu_labels(g, "none", ("sv", "naive", "split_one"))
     assert np.all(got == 0)
+
+
+def test_unaligned_label_slices():
+    """Label buffers that are 4-byte- but not 16-byte-aligned slices work
+    (vector accesses only where the address allows them)."""
+    g = synth.rmat(14, 8, seed=3)
+    want, _ = oracle.cc_uf(*g.numpy())
+    off, edg = on_gpu(g)
+    buf = torch.full((g.n + 7,), -1, dtype=torch.int32, device="cuda")
+    for shift in (1, 2, 3):
+        out = buf[shift:shift + g.n]
+        for s in ("none", "kout", "bfs", "ldd"):
+            cc.cc_static(off, edg, cc.sample_opt(s), labels_out=out)
+            assert np.array_equal(out.cpu().numpy().view(np.uint32), want), (shift, s)
+        lab, _ = cc.cc_sample(off, edg, cc.sample_opt("kout"), labels_out=out)
+        lm = cc.cc_identify_frequent(out)
+        wl, _ = oracle.identify_frequent(oracle.kout_sample(*g.numpy(), 2, 1))
+        assert int(lm.item()) == wl
+    assert cc.device_error() == 0
