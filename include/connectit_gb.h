@@ -228,6 +228,37 @@ cc_status cc_incr_labels(cc_incr *h, uint32_t *labels_out, void *stream);
 uint32_t cc_incr_num_vertices(const cc_incr *h);
 cc_status cc_incr_destroy(cc_incr *h);
 
+/* Continuous-batching request loop over an incremental handle (no
+ * counterpart in the paper; it serves Section 3.5's batch semantics to many
+ * clients).  Requests are linearised in ticket order: request r's inserts are
+ * applied, then its queries answered, after every request with a smaller
+ * ticket, so each answer is the same alone or in the mix.  A dispatcher
+ * thread admits requests as device slots free up (slots x slot_pairs pairs
+ * of device memory, 9 bytes per pair; larger requests are split into
+ * chunks, inserts first) and overlaps one request's copies with another's
+ * kernels on separate streams.
+ * cc_server_create: the server uses `h` exclusively until it is destroyed.
+ * cc_server_submit: inserts (2k uint32) and queries (2q uint32) are HOST
+ *   arrays, answers a HOST uint8[q] array; all three must stay valid until
+ *   cc_server_wait returns.  When all three are pinned (device-mapped) host
+ *   memory, the kernels read and write them in place (no staging copies, no
+ *   slot); otherwise the request is staged through the slots.
+ * cc_server_wait: blocks until the request's answers are in host memory;
+ *   *latency_ms_out (may be NULL) gets submit-to-completion time.
+ * cc_server_destroy: drains the queue, then frees the server (not h). */
+typedef struct cc_server cc_server;
+typedef struct cc_server_opt {
+    uint32_t slots;        /* device slots in flight (1..64; 4) */
+    uint32_t reserved;     /* must be 0 */
+    uint64_t slot_pairs;   /* pairs per slot (1..2^30; 2^22) */
+} cc_server_opt;
+void cc_server_default_opt(cc_server_opt *opt);
+cc_status cc_server_create(cc_incr *h, const cc_server_opt *opt, cc_server **out);
+cc_status cc_server_submit(cc_server *s, const uint32_t *inserts, uint64_t k, const uint32_t *queries, uint64_t q,
+                           uint8_t *answers, uint64_t *ticket_out);
+cc_status cc_server_wait(cc_server *s, uint64_t ticket, double *latency_ms_out);
+cc_status cc_server_destroy(cc_server *s);
+
 /* Synchronise `stream`, then read and clear the per-device sticky error
  * word (CC_DEVERR_* bits) into *bits_out (host; may be NULL).  Returns
  * CC_OK when the word was 0, else the matching status. */

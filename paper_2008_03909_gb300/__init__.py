@@ -60,6 +60,10 @@ class BatchOpt(ctypes.Structure):
                 ("vertex_mode", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
+class ServerOpt(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("slot_pairs", ctypes.c_uint64)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("lmax", ctypes.c_uint32), ("sample_info", ctypes.c_int32), ("rounds", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32), ("edges_finish", ctypes.c_uint64)]
@@ -106,6 +110,12 @@ _SIGS = {
     "cc_incr_labels": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "cc_incr_num_vertices": (ctypes.c_uint32, [ctypes.c_void_p]),
     "cc_incr_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "cc_server_default_opt": (None, [ctypes.POINTER(ServerOpt)]),
+    "cc_server_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServerOpt), ctypes.POINTER(ctypes.c_void_p)]),
+    "cc_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
+                                        ctypes.c_uint64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
+    "cc_server_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
+    "cc_server_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "cc_device_error": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32)]),
     "cc_set_iteration_cap": (None, [ctypes.c_uint64]),
     "cc_profile_enable": (None, [ctypes.c_int]),
@@ -371,6 +381,52 @@ class Incremental:
         if self._h:
             lib().cc_incr_destroy(self._h)
             self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request loop over an Incremental handle.  Host
+    tensors (pinned for overlap) are kept alive until wait()."""
+
+    def __init__(self, inc: "Incremental", slots: int = 4, slot_pairs: int = 1 << 22):
+        self._s = ctypes.c_void_p(0)
+        self._keep = {}
+        self.inc = inc
+        _check(lib().cc_server_create(inc._h, ctypes.byref(ServerOpt(slots, 0, slot_pairs)), ctypes.byref(self._s)),
+               "cc_server_create")
+
+    def submit(self, inserts: torch.Tensor | None, queries: torch.Tensor | None, answers: torch.Tensor | None = None):
+        for t, nm in ((inserts, "inserts"), (queries, "queries")):
+            if t is not None and (t.is_cuda or t.dtype != torch.int32 or not t.is_contiguous()):
+                raise TypeError(f"{nm} must be a contiguous host int32 tensor")
+        k = inserts.numel() // 2 if inserts is not None else 0
+        q = queries.numel() // 2 if queries is not None else 0
+        if answers is None:
+            answers = torch.empty(q, dtype=torch.uint8, pin_memory=True)
+        t = ctypes.c_uint64(0)
+        _check(lib().cc_server_submit(self._s, ctypes.c_void_p(inserts.data_ptr() if k else 0), k,
+                                      ctypes.c_void_p(queries.data_ptr() if q else 0), q,
+                                      ctypes.c_void_p(answers.data_ptr() if q else 0), ctypes.byref(t)),
+               "cc_server_submit")
+        self._keep[t.value] = (inserts, queries, answers)
+        return t.value
+
+    def wait(self, ticket: int):
+        """Returns (answers tensor, latency in ms)."""
+        lat = ctypes.c_double(0)
+        _check(lib().cc_server_wait(self._s, ticket, ctypes.byref(lat)), "cc_server_wait")
+        ins, qs, ans = self._keep.pop(ticket)
+        return ans, lat.value
+
+    def close(self):
+        if self._s:
+            lib().cc_server_destroy(self._s)
+            self._s = ctypes.c_void_p(0)
 
     def __del__(self):
         try:

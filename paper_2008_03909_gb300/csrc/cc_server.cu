@@ -1,0 +1,354 @@
+// cc_server.cu -- a continuous-batching request loop over the resident
+// union-find of an incremental handle (no counterpart in the paper, which
+// processes one batch at a time, Algorithm 3; it builds on the
+// batch-incremental semantics of Section 3.5: a request's inserts are
+// applied, then its queries answered).
+//
+// Requests (host arrays of insert pairs and query pairs, with a host array
+// for the answers) are linearised in the order of their tickets: request r's
+// queries see the inserts of every request up to and including r, so each
+// answer is the same whether r runs alone or among others.  A dispatcher
+// thread admits requests as device slots free up (each slot holds one chunk
+// of at most `slot_pairs` pairs and its answers, so device memory is bounded
+// by slots x slot_pairs x 17 bytes), and issues each piece of a request as
+// host->device copies (copy stream) -> insert and query kernels (compute
+// stream, ticket order) -> answers device->host (return stream).  Copies of
+// later requests overlap the kernels of earlier ones.  Requests whose host
+// buffers the device can address directly (pinned memory; over NVLink-C2C
+// on Grace-Blackwell) skip staging: their kernels read the pairs from host
+// memory and write the answers there.  A completion thread
+// waits on each request's last event in issue order and stamps its time.
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "cc_internal.h"
+
+using namespace ccg;
+
+namespace {
+
+double now_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// One piece of a request: up to slot_pairs inserts, then up to slot_pairs
+// queries (a request's inserts all come before its queries).
+struct Piece {
+    const uint32_t *ins;
+    uint64_t k;
+    const uint32_t *qs;
+    uint64_t q;
+    uint8_t *answers;
+};
+
+struct Request {
+    uint64_t ticket = 0;
+    std::vector<Piece> pieces;
+    double t_submit = 0, t_done = 0;
+    bool done = false;
+    bool direct = false;   // buffers reachable from the device: no staging
+    cc_status status = CC_OK;
+    cudaEvent_t finished = nullptr;
+};
+
+struct Slot {
+    uint32_t *d_ins = nullptr, *d_qs = nullptr;
+    uint8_t *d_ans = nullptr;
+    cudaEvent_t copied = nullptr, computed = nullptr, free = nullptr;
+    bool used = false;
+};
+
+}  // namespace
+
+struct cc_server {
+    cc_incr *h = nullptr;
+    int device = 0;
+    uint64_t cap = 0;
+    cudaStream_t s_in = nullptr, s_comp = nullptr, s_out = nullptr;
+    std::vector<Slot> slots;
+    size_t next_slot = 0;
+    std::mutex mu;
+    std::condition_variable cv_queue, cv_done;
+    std::deque<std::shared_ptr<Request>> queue;     // submitted, not yet issued
+    std::deque<std::shared_ptr<Request>> issued;    // issued, not yet complete
+    std::map<uint64_t, std::shared_ptr<Request>> live;
+    uint64_t next_ticket = 1;
+    bool stop = false, dispatcher_done = false;
+    cc_status fatal = CC_OK;
+    std::thread worker, completer;
+};
+
+namespace {
+
+// Device-visible address of a host pointer that the GPU can reach directly
+// (pinned / registered host memory, mapped into the device's address space
+// and, on Grace-Blackwell, reached over NVLink-C2C); nullptr otherwise.
+const void *device_view(const void *p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    if ((a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeManaged) && a.devicePointer) return a.devicePointer;
+    return nullptr;
+}
+
+cc_status issue(cc_server *s, Request &r) {
+    cudaError_t e = cudaSuccess;
+#define CC_SRV(x)                                   \
+    do {                                            \
+        if ((e = (x)) != cudaSuccess) return from_cuda(e); \
+    } while (0)
+    // Requests whose host buffers the device can read and write directly
+    // skip the staging copies: their kernels stream the pairs from host
+    // memory and write the answers back, in ticket order on the compute
+    // stream, holding no device slot.
+    if (r.direct) {
+        for (const Piece &p : r.pieces) {
+            if (p.k) {
+                cc_status st = cc_incr_insert_batch(s->h, static_cast<const uint32_t *>(device_view(p.ins)), p.k,
+                                                    s->s_comp);
+                if (st != CC_OK) return st;
+            }
+            if (p.q) {
+                cc_status st = cc_incr_query_batch(s->h, static_cast<const uint32_t *>(device_view(p.qs)), p.q,
+                                                   static_cast<uint8_t *>(const_cast<void *>(device_view(p.answers))),
+                                                   s->s_comp);
+                if (st != CC_OK) return st;
+            }
+        }
+        CC_SRV(cudaEventRecord(r.finished, s->s_comp));
+        return CC_OK;
+    }
+    for (const Piece &p : r.pieces) {
+        Slot &sl = s->slots[s->next_slot];
+        s->next_slot = (s->next_slot + 1) % s->slots.size();
+        // admission: the slot's previous piece must have left the device
+        if (sl.used) CC_SRV(cudaEventSynchronize(sl.free));
+        sl.used = true;
+        if (p.k) CC_SRV(cudaMemcpyAsync(sl.d_ins, p.ins, p.k * 8, cudaMemcpyHostToDevice, s->s_in));
+        if (p.q) CC_SRV(cudaMemcpyAsync(sl.d_qs, p.qs, p.q * 8, cudaMemcpyHostToDevice, s->s_in));
+        CC_SRV(cudaEventRecord(sl.copied, s->s_in));
+        CC_SRV(cudaStreamWaitEvent(s->s_comp, sl.copied, 0));
+        if (p.k) {
+            cc_status st = cc_incr_insert_batch(s->h, sl.d_ins, p.k, s->s_comp);
+            if (st != CC_OK) return st;
+        }
+        if (p.q) {
+            cc_status st = cc_incr_query_batch(s->h, sl.d_qs, p.q, sl.d_ans, s->s_comp);
+            if (st != CC_OK) return st;
+        }
+        CC_SRV(cudaEventRecord(sl.computed, s->s_comp));
+        CC_SRV(cudaStreamWaitEvent(s->s_out, sl.computed, 0));
+        if (p.q) CC_SRV(cudaMemcpyAsync(p.answers, sl.d_ans, p.q, cudaMemcpyDeviceToHost, s->s_out));
+        CC_SRV(cudaEventRecord(sl.free, s->s_out));
+    }
+    CC_SRV(cudaEventRecord(r.finished, s->s_out));
+#undef CC_SRV
+    return CC_OK;
+}
+
+void finish(cc_server *s, Request &r, cc_status st) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    r.status = st;
+    r.t_done = now_ms();
+    r.done = true;
+    s->cv_done.notify_all();
+}
+
+void dispatcher(cc_server *s) {
+    cudaSetDevice(s->device);
+    for (;;) {
+        std::shared_ptr<Request> r;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv_queue.wait(lk, [&] { return s->stop || !s->queue.empty(); });
+            if (s->queue.empty()) {
+                s->dispatcher_done = true;
+                s->cv_done.notify_all();
+                return;
+            }
+            r = s->queue.front();
+            s->queue.pop_front();
+        }
+        cc_status st = s->fatal == CC_OK ? issue(s, *r) : s->fatal;
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (st != CC_OK) {
+            s->fatal = st;
+            r->status = st;
+            r->t_done = now_ms();
+            r->done = true;
+        } else {
+            s->issued.push_back(r);
+        }
+        s->cv_done.notify_all();
+    }
+}
+
+// Waits for issued requests in issue order (their events complete in that
+// order on the return stream) and stamps their completion time.
+void completer(cc_server *s) {
+    cudaSetDevice(s->device);
+    for (;;) {
+        std::shared_ptr<Request> r;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv_done.wait(lk, [&] { return !s->issued.empty() || s->dispatcher_done; });
+            if (s->issued.empty()) return;
+            r = s->issued.front();
+            s->issued.pop_front();
+        }
+        cudaError_t e = cudaEventSynchronize(r->finished);
+        finish(s, *r, from_cuda(e));
+    }
+}
+
+void destroy_resources(cc_server *s) {
+    for (Slot &sl : s->slots) {
+        if (sl.d_ins) cudaFree(sl.d_ins);
+        if (sl.d_qs) cudaFree(sl.d_qs);
+        if (sl.d_ans) cudaFree(sl.d_ans);
+        if (sl.copied) cudaEventDestroy(sl.copied);
+        if (sl.computed) cudaEventDestroy(sl.computed);
+        if (sl.free) cudaEventDestroy(sl.free);
+    }
+    if (s->s_in) cudaStreamDestroy(s->s_in);
+    if (s->s_comp) cudaStreamDestroy(s->s_comp);
+    if (s->s_out) cudaStreamDestroy(s->s_out);
+}
+
+}  // namespace
+
+extern "C" {
+
+void cc_server_default_opt(cc_server_opt *o) {
+    if (!o) return;
+    o->slots = 4;
+    o->reserved = 0;
+    o->slot_pairs = 1ull << 22;
+}
+
+cc_status cc_server_create(cc_incr *h, const cc_server_opt *opt, cc_server **out) {
+    if (!h || !out) return CC_ERR_INVALID;
+    *out = nullptr;
+    cc_server_opt o;
+    cc_server_default_opt(&o);
+    if (opt) o = *opt;
+    if (o.slots < 1 || o.slots > 64 || o.slot_pairs < 1 || o.slot_pairs > (1ull << 30) || o.reserved)
+        return CC_ERR_INVALID;
+    const DeviceInfo *di = device_info();
+    if (!di) return CC_ERR_CUDA;
+    cc_server *s = new cc_server();
+    s->h = h;
+    s->device = di->device;
+    s->cap = o.slot_pairs;
+    s->slots.resize(o.slots);
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_in, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_comp, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_out, cudaStreamNonBlocking);
+    for (Slot &sl : s->slots) {
+        if (e == cudaSuccess) e = cudaMalloc(&sl.d_ins, o.slot_pairs * 8);
+        if (e == cudaSuccess) e = cudaMalloc(&sl.d_qs, o.slot_pairs * 8);
+        if (e == cudaSuccess) e = cudaMalloc(&sl.d_ans, o.slot_pairs);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.copied, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.computed, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.free, cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        destroy_resources(s);
+        delete s;
+        return from_cuda(e);
+    }
+    s->worker = std::thread(dispatcher, s);
+    s->completer = std::thread(completer, s);
+    *out = s;
+    return CC_OK;
+}
+
+cc_status cc_server_submit(cc_server *s, const uint32_t *inserts, uint64_t k, const uint32_t *queries, uint64_t q,
+                           uint8_t *answers, uint64_t *ticket_out) {
+    if (!s || !ticket_out) return CC_ERR_INVALID;
+    if ((k && !inserts) || (q && (!queries || !answers))) return CC_ERR_INVALID;
+    auto r = std::make_shared<Request>();
+    r->direct = (k == 0 || device_view(inserts)) && (q == 0 || (device_view(queries) && device_view(answers)));
+    if (r->direct) {
+        r->pieces.push_back(Piece{inserts, k, queries, q, answers});
+    } else {
+    // pieces: one per insert chunk, the last insert chunk sharing its piece
+    // with the first query chunk, then one per remaining query chunk
+    const uint64_t C = s->cap;
+    std::vector<Piece> ins_p, q_p;
+    for (uint64_t i = 0; i < k; i += C) ins_p.push_back(Piece{inserts + 2 * i, k - i < C ? k - i : C, nullptr, 0, nullptr});
+    for (uint64_t i = 0; i < q; i += C)
+        q_p.push_back(Piece{nullptr, 0, queries + 2 * i, q - i < C ? q - i : C, answers + i});
+    r->pieces = ins_p;
+    size_t first_q = 0;
+    if (!r->pieces.empty() && !q_p.empty()) {
+        Piece &last = r->pieces.back();
+        last.qs = q_p[0].qs;
+        last.q = q_p[0].q;
+        last.answers = q_p[0].answers;
+        first_q = 1;
+    }
+    for (size_t i = first_q; i < q_p.size(); ++i) r->pieces.push_back(q_p[i]);
+    }
+    if (cudaEventCreateWithFlags(&r->finished, cudaEventDisableTiming) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return CC_ERR_CUDA;
+    }
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stop) return CC_ERR_INVALID;
+        if (s->fatal != CC_OK) return s->fatal;
+        r->ticket = s->next_ticket++;
+        r->t_submit = now_ms();
+        s->live[r->ticket] = r;
+        s->queue.push_back(r);
+        *ticket_out = r->ticket;
+    }
+    s->cv_queue.notify_one();
+    return CC_OK;
+}
+
+cc_status cc_server_wait(cc_server *s, uint64_t ticket, double *latency_ms_out) {
+    if (!s) return CC_ERR_INVALID;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->live.find(ticket);
+    if (it == s->live.end()) return CC_ERR_INVALID;
+    std::shared_ptr<Request> r = it->second;
+    s->cv_done.wait(lk, [&] { return r->done; });
+    if (latency_ms_out) *latency_ms_out = r->t_done - r->t_submit;
+    s->live.erase(it);
+    cc_status st = r->status;
+    lk.unlock();
+    if (r->finished) cudaEventDestroy(r->finished);
+    r->finished = nullptr;
+    return st;
+}
+
+cc_status cc_server_destroy(cc_server *s) {
+    if (!s) return CC_OK;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_queue.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    if (s->completer.joinable()) s->completer.join();
+    cudaError_t e = cudaSuccess;
+    if (s->s_out) e = cudaStreamSynchronize(s->s_out);
+    if (s->s_comp && e == cudaSuccess) e = cudaStreamSynchronize(s->s_comp);
+    destroy_resources(s);
+    delete s;
+    return from_cuda(e);
+}
+
+}  // extern "C"
