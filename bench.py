@@ -59,6 +59,11 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--combos", action="store_true", help="also time every sampling x finish combination")
     p.add_argument("--batched-graphs", type=int, default=10000)
+    p.add_argument("--sel-train", type=int, default=300)
+    p.add_argument("--sel-test", type=int, default=100)
+    p.add_argument("--sel-scale-lo", type=int, default=12)
+    p.add_argument("--sel-scale-hi", type=int, default=18)
+    p.add_argument("--no-selector", action="store_true")
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     return p.parse_args()
@@ -298,6 +303,9 @@ def run_ours(args):
     if not args.no_batched:
         out["batched"] = bench_batched(args, cc, synth, dev)
 
+    if not args.no_selector:
+        out["selector"] = bench_selector(args, cc, synth, dev)
+
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(off, edg, args.cpu_seconds)
     if dist:
@@ -324,6 +332,58 @@ def bench_combos(args, cc, off, edg, labels, ref, m):
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / reps
             res[f"{s}+{f}"] = {"ms": round(ms, 3), "gedges_s": round(m / (ms * 1e-3) / 1e9, 2), "exact": same}
+    return res
+
+
+def bench_selector(args, cc, synth, dev):
+    """Learned selector: features and exhaustive timings of the 12 classes on
+    seeded graphs, train on the first part with the library's MLP kernels,
+    and score the held-out part by regret (t_pick - t_best) / t_best against
+    always k-out + UF-Rem-CAS and against the paper's decision tree."""
+    import torch
+    from paper_2008_03909_gb300 import selector
+    N = args.sel_train + args.sel_test
+    X = torch.empty(N, 16, dtype=torch.float32)
+    T = torch.empty(N, 12, dtype=torch.float32)
+    fam = []
+    t0 = time.time()
+    feat_ms = []
+    for i in range(N):
+        g = synth.selector_graph(i, seed=7, scale_lo=args.sel_scale_lo, scale_hi=args.sel_scale_hi, device=dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        X[i] = cc.cc_features(g.offsets, g.edges, seed=1).cpu()
+        e1.record()
+        e1.synchronize()
+        feat_ms.append(e0.elapsed_time(e1))
+        T[i] = selector.time_classes(g.offsets, g.edges, reps=2)
+        fam.append(i % 4)
+        del g
+    collect_s = time.time() - t0
+    sel = selector.Selector(device=dev, seed=1)
+    t1 = time.time()
+    hist = sel.fit(X[: args.sel_train].to(dev), T[: args.sel_train].to(dev), epochs=800, lr=3e-3)
+    train_s = time.time() - t1
+    Xt, Tt = X[args.sel_train:], T[args.sel_train:]
+    pick = sel.predict(Xt.to(dev)).cpu()
+    tree = torch.tensor([selector.paper_decision_tree(x) for x in Xt], dtype=torch.int32)
+    dflt = torch.full((args.sel_test,), selector.DEFAULT, dtype=torch.int32)
+
+    def score(ch):
+        r = selector.regret(Tt, ch)
+        return {"mean_regret": round(float(r.mean()), 4), "median_regret": round(float(r.median()), 4),
+                "p90_regret": round(float(r.quantile(0.9)), 4),
+                "total_ms": round(float(Tt.gather(1, ch.long()[:, None]).sum()), 3)}
+
+    best_ms = float(Tt.min(dim=1).values.sum())
+    res = {"train_graphs": args.sel_train, "heldout_graphs": args.sel_test,
+           "scales": [args.sel_scale_lo, args.sel_scale_hi],
+           "classes": [f"{s}+{f}" for s, f in selector.CLASSES],
+           "mlp": score(pick), "always_kout_uf_rem_cas": score(dflt), "paper_decision_tree": score(tree),
+           "oracle_best_total_ms": round(best_ms, 3), "train_loss": [round(hist[0], 4), round(hist[-1], 4)],
+           "collect_s": round(collect_s, 1), "train_s": round(train_s, 2),
+           "features_ms_median": round(float(torch.tensor(feat_ms).median()), 4)}
+    res["mlp_vs_default_time"] = round(res["always_kout_uf_rem_cas"]["total_ms"] / res["mlp"]["total_ms"], 3)
     return res
 
 

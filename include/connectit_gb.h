@@ -259,6 +259,52 @@ cc_status cc_server_submit(cc_server *s, const uint32_t *inserts, uint64_t k, co
 cc_status cc_server_wait(cc_server *s, uint64_t ticket, double *latency_ms_out);
 cc_status cc_server_destroy(cc_server *s);
 
+/* Learned variant selector (no counterpart in the paper, whose Section 4.7
+ * offers a hand-made decision tree): an FP32 MLP 16 -> 64 -> 64 -> 12 with
+ * ReLU, trained on the GPU by these kernels.  It only picks which
+ * combination to run; labels never depend on it.
+ * Parameter block (DEVICE float[CC_MLP_NPARAM]): mu[16], sigma[16] (input
+ * standardisation), W1[16][64], b1[64], W2[64][64], b2[64], W3[64][12],
+ * b3[12]; W[i][j] maps input i to output j.  X: DEVICE float[B][16].
+ * cc_mlp_init: Glorot-uniform weights from counter-based draws of `seed`,
+ *   zero biases, mu = 0, sigma = 1.
+ * cc_mlp_set_norm: mu, sigma <- mean, standard deviation of X's columns.
+ * cc_mlp_forward: logits float[B][12]; acts (may be NULL) float[B][128]
+ *   gets both hidden layers for cc_mlp_backward.
+ * cc_mlp_soft_targets: targets[B][12] from measured times[B][12]:
+ *   q_c proportional to exp(-(t_c / min_c t_c - 1) / tau).
+ * cc_mlp_backward: grads float[CC_MLP_NPARAM] <- gradient of the mean
+ *   cross-entropy between softmax(logits) and the targets (zero for mu,
+ *   sigma); *loss (DEVICE float, may be NULL) <- that mean.  Per-sample
+ *   gradients are summed in a fixed order (deterministic).
+ * cc_mlp_adam: one Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the
+ *   trained parameters; m, v: DEVICE float[CC_MLP_NPARAM], zero at step 1.
+ * cc_mlp_predict: class_out DEVICE int32[B] <- argmax of the logits. */
+#define CC_MLP_IN 16
+#define CC_MLP_HID 64
+#define CC_MLP_OUT 12
+#define CC_MLP_NPARAM (2 * CC_MLP_IN + CC_MLP_IN * CC_MLP_HID + CC_MLP_HID + CC_MLP_HID * CC_MLP_HID + \
+                       CC_MLP_HID + CC_MLP_HID * CC_MLP_OUT + CC_MLP_OUT)
+/* Selector features of a graph (same conventions as cc_static; n >= 1):
+ * feat_out (DEVICE float[16]) <- 0 log2(n+1), 1 log2(m+1), 2 m/n,
+ * 3 log2(max degree + 1), 4 degree variance / mean^2, 5-7 fractions of
+ * vertices of degree 0, 1, 2, 8 fraction of degree 3..16, 9 fraction of
+ * degree > 64, 10 share of edges at vertices of degree > 64, 11 size of
+ * the largest k-out (k = 2, `seed`) sampled cluster / n, 12 sampled
+ * clusters / n, 13 edges left for the finish after k-out / m, 14 levels of
+ * a BFS from the highest-degree vertex capped at 64, divided by 64, 15
+ * vertices that BFS reached / n.  Synchronises the stream. */
+cc_status cc_features(const void *offsets, int offsets_u64, const uint32_t *edges, uint32_t n, uint64_t m,
+                      uint64_t seed, float *feat_out, void *stream);
+cc_status cc_mlp_init(float *params, uint64_t seed, void *stream);
+cc_status cc_mlp_set_norm(float *params, const float *X, uint32_t B, void *stream);
+cc_status cc_mlp_forward(const float *params, const float *X, uint32_t B, float *logits, float *acts, void *stream);
+cc_status cc_mlp_soft_targets(const float *times, uint32_t B, float tau, float *targets, void *stream);
+cc_status cc_mlp_backward(const float *params, const float *X, const float *acts, const float *logits,
+                          const float *targets, uint32_t B, float *grads, float *loss, void *stream);
+cc_status cc_mlp_adam(float *params, const float *grads, float *m, float *v, uint32_t step, float lr, void *stream);
+cc_status cc_mlp_predict(const float *params, const float *X, uint32_t B, int32_t *class_out, void *stream);
+
 /* Synchronise `stream`, then read and clear the per-device sticky error
  * word (CC_DEVERR_* bits) into *bits_out (host; may be NULL).  Returns
  * CC_OK when the word was 0, else the matching status. */

@@ -116,6 +116,21 @@ _SIGS = {
                                         ctypes.c_uint64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
     "cc_server_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
     "cc_server_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "cc_features": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64,
+                                   ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]),
+    "cc_mlp_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]),
+    "cc_mlp_set_norm": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]),
+    "cc_mlp_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_void_p]),
+    "cc_mlp_soft_targets": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_float, ctypes.c_void_p,
+                                           ctypes.c_void_p]),
+    "cc_mlp_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
+    "cc_mlp_adam": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_uint32, ctypes.c_float, ctypes.c_void_p]),
+    "cc_mlp_predict": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p,
+                                      ctypes.c_void_p]),
     "cc_device_error": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32)]),
     "cc_set_iteration_cap": (None, [ctypes.c_uint64]),
     "cc_profile_enable": (None, [ctypes.c_int]),
@@ -337,6 +352,55 @@ def cc_batched_autotune(gv, offsets, edges, labels_out=None, stream=None):
     _check(lib().cc_batched_autotune(*a, ctypes.c_void_p(labels_out.data_ptr()), ctypes.byref(best),
                                      ctypes.byref(ms), _stream(stream)), "cc_batched_autotune")
     return labels_out, best, ms.value
+
+
+def cc_features(offsets, edges, seed: int = 1, out=None, stream=None) -> torch.Tensor:
+    """The selector's 16 graph features (float32 CUDA tensor)."""
+    Ip, u64, Ap, n, m = _graph_args(offsets, edges)
+    if out is None:
+        out = torch.empty(16, dtype=torch.float32, device=offsets.device)
+    _check(lib().cc_features(Ip, u64, Ap, n, m, seed, ctypes.c_void_p(out.data_ptr()), _stream(stream)),
+           "cc_features")
+    return out
+
+
+MLP_IN, MLP_HID, MLP_OUT = 16, 64, 12
+MLP_NPARAM = 2 * MLP_IN + MLP_IN * MLP_HID + MLP_HID + MLP_HID * MLP_HID + MLP_HID + MLP_HID * MLP_OUT + MLP_OUT
+
+
+def _p(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def mlp_init(params, seed=1, stream=None):
+    _check(lib().cc_mlp_init(_p(params), seed, _stream(stream)), "cc_mlp_init")
+
+
+def mlp_set_norm(params, X, stream=None):
+    _check(lib().cc_mlp_set_norm(_p(params), _p(X), X.shape[0], _stream(stream)), "cc_mlp_set_norm")
+
+
+def mlp_forward(params, X, logits, acts=None, stream=None):
+    _check(lib().cc_mlp_forward(_p(params), _p(X), X.shape[0], _p(logits), _p(acts), _stream(stream)),
+           "cc_mlp_forward")
+
+
+def mlp_soft_targets(times, tau, targets, stream=None):
+    _check(lib().cc_mlp_soft_targets(_p(times), times.shape[0], tau, _p(targets), _stream(stream)),
+           "cc_mlp_soft_targets")
+
+
+def mlp_backward(params, X, acts, logits, targets, grads, loss=None, stream=None):
+    _check(lib().cc_mlp_backward(_p(params), _p(X), _p(acts), _p(logits), _p(targets), X.shape[0], _p(grads),
+                                 _p(loss), _stream(stream)), "cc_mlp_backward")
+
+
+def mlp_adam(params, grads, m, v, step, lr, stream=None):
+    _check(lib().cc_mlp_adam(_p(params), _p(grads), _p(m), _p(v), step, lr, _stream(stream)), "cc_mlp_adam")
+
+
+def mlp_predict(params, X, out, stream=None):
+    _check(lib().cc_mlp_predict(_p(params), _p(X), X.shape[0], _p(out), _stream(stream)), "cc_mlp_predict")
 
 
 class Incremental:

@@ -717,6 +717,82 @@ __global__ void __launch_bounds__(256, 8) k_apply_cluster_min(uint32_t *P, uint3
         P[i] = cmin[P[i]];
 }
 
+// ---------------------------------------------------------------- selector features
+struct FeatStats {
+    unsigned long long sum_deg, cnt[5], edges_gt64, maxkey;   // maxkey = deg << 32 | ~v
+    double sum_deg2;
+    unsigned long long roots, lmax_count, edges_nonlmax;
+};
+
+// Degree statistics in one pass over the offsets.
+template <typename OffT>
+__global__ void __launch_bounds__(256, 8) k_degree_stats(const OffT *I, uint32_t n, uint64_t m, FeatStats *st, Dev d) {
+    unsigned long long sd = 0, c[5] = {0, 0, 0, 0, 0}, e64 = 0, mk = 0;
+    double sd2 = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t b, e;
+        vertex_range(I, (uint32_t)i, m, b, e, d);
+        const uint64_t deg = e - b;
+        sd += deg;
+        sd2 += (double)deg * (double)deg;
+        c[0] += deg == 0;
+        c[1] += deg == 1;
+        c[2] += deg == 2;
+        c[3] += deg >= 3 && deg <= 16;
+        c[4] += deg > 64;
+        if (deg > 64) e64 += deg;
+        const unsigned long long key = ((deg < 0xFFFFFFFFull ? deg : 0xFFFFFFFFull) << 32) | (uint32_t)~(uint32_t)i;
+        mk = key > mk ? key : mk;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sd += __shfl_xor_sync(0xFFFFFFFFu, sd, o);
+        sd2 += __shfl_xor_sync(0xFFFFFFFFu, sd2, o);
+        e64 += __shfl_xor_sync(0xFFFFFFFFu, e64, o);
+        for (int j = 0; j < 5; ++j) c[j] += __shfl_xor_sync(0xFFFFFFFFu, c[j], o);
+        unsigned long long y = __shfl_xor_sync(0xFFFFFFFFu, mk, o);
+        mk = y > mk ? y : mk;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&st->sum_deg, sd);
+        atomicAdd(&st->sum_deg2, sd2);
+        atomicAdd(&st->edges_gt64, e64);
+        for (int j = 0; j < 5; ++j) atomicAdd(&st->cnt[j], c[j]);
+        atomicMax(&st->maxkey, mk);
+    }
+}
+
+// On flat sampled labels: roots (= sampled components), the size of L_max's
+// cluster, and the edges out of vertices outside it (left for the finish).
+template <typename OffT>
+__global__ void __launch_bounds__(256, 8) k_label_stats(const OffT *I, uint32_t n, uint64_t m, const uint32_t *P,
+                                                         const uint32_t *lmax_p, FeatStats *st, Dev d) {
+    const uint32_t lmax = *lmax_p;
+    unsigned long long r = 0, c = 0, e = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t l = P[i];
+        r += l == i;
+        if (l == lmax) {
+            ++c;
+        } else {
+            uint64_t b, t;
+            vertex_range(I, (uint32_t)i, m, b, t, d);
+            e += t - b;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        r += __shfl_xor_sync(0xFFFFFFFFu, r, o);
+        c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+        e += __shfl_xor_sync(0xFFFFFFFFu, e, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&st->roots, r);
+        atomicAdd(&st->lmax_count, c);
+        atomicAdd(&st->edges_nonlmax, e);
+    }
+}
+
 // ================================================================ host side
 struct Graph {
     const void *I;
@@ -1293,6 +1369,126 @@ cc_status run_static(const Graph &g, const cc_sample_opt &so, const cc_finish_op
     return CC_OK;
 }
 
+// Capped BFS (push only, at most `cap` levels) from src: levels run and
+// vertices reached.  Uses the BFS sampling's kernels and scratch.
+template <typename OffT>
+cc_status bfs_capped(const Graph &g, uint32_t src, uint32_t cap, uint32_t *P, Work &w, const DeviceInfo *di,
+                     const Dev &d, cudaStream_t s, uint32_t *levels, uint64_t *reached) {
+    const OffT *I = static_cast<const OffT *>(g.I);
+    const uint32_t n = g.n;
+    const uint64_t words = (n + 31) / 32;
+    Ctl *ctl = w.ctl();
+    uint32_t *vis = w.sc.at<uint32_t>(w.o_vis);
+    uint32_t *q[2] = {w.sc.at<uint32_t>(w.o_q0), w.sc.at<uint32_t>(w.o_q1)};
+    ChunkRef *chunks = w.sc.at<ChunkRef>(w.o_chunks);
+    const unsigned gv = grid_for(di, n, TPB);
+    CC_TRY(cudaMemsetAsync(vis, 0, words * 4, s));
+    CC_TRY(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+    k_set_u32<<<1, 1, 0, s>>>(q[0], src);
+    k_set_u32<<<1, 1, 0, s>>>(&ctl->nfront[0], 1);
+    k_set_u32<<<1, 1, 0, s>>>(&ctl->minv, src);
+    k_list_to_bitmap<<<1, 32, 0, s>>>(q[0], &ctl->nfront[0], vis);
+    CC_LAUNCH();
+    uint64_t tot = 1;
+    uint32_t lv = 0;
+    int cur = 0;
+    for (; lv < cap; ++lv) {
+        const int nx = cur ^ 1;
+        CC_TRY(cudaMemsetAsync(&ctl->nfront[nx], 0, 4, s));
+        CC_TRY(cudaMemsetAsync(&ctl->nchunks, 0, 4, s));
+        BFSEdge f{P, vis, q[nx], &ctl->nfront[nx], &ctl->minv, src, NONE};
+        {
+            CC_PROF("k_list_bin", s);
+            k_list_bin<OffT, BFSEdge><<<gv, TPB, 0, s>>>(I, g.A, n, g.m, q[cur], &ctl->nfront[cur], f, chunks,
+                                                         &ctl->nchunks, w.chunk_cap, d);
+        }
+        {
+            CC_PROF("k_chunks", s);
+            k_chunks<OffT, BFSEdge><<<grid_for(di, (uint64_t)1 << 40, TPB), TPB, 0, s>>>(
+                I, g.A, n, g.m, chunks, &ctl->nchunks, w.chunk_cap, f, d);
+        }
+        CC_LAUNCH();
+        uint32_t nf = 0;
+        CC_TRY(cudaMemcpyAsync(&nf, &ctl->nfront[nx], 4, cudaMemcpyDeviceToHost, s));
+        CC_TRY(cudaStreamSynchronize(s));
+        cur = nx;
+        if (nf == 0) break;
+        tot += nf;
+    }
+    *levels = lv;
+    *reached = tot;
+    return CC_OK;
+}
+
+template <typename OffT>
+cc_status run_features(const Graph &g, uint64_t seed, float *feat_out, cudaStream_t s) {
+    const DeviceInfo *di = device_info();
+    if (!di) return CC_ERR_CUDA;
+    const Dev d = make_dev(di, g.n);
+    const uint32_t n = g.n;
+    const unsigned gv = grid_for(di, n, TPB);
+    Work w;
+    plan(w, g, CC_SAMPLE_KOUT, 0, CC_FINISH_UF_REM_CAS, false);
+    const uint64_t words = (n + 31) / 32;
+    w.o_vis = w.sc.reserve(words * 4);
+    w.o_q0 = w.sc.reserve((size_t)n * 4);
+    w.o_q1 = w.sc.reserve((size_t)n * 4);
+    const size_t o_lab = w.sc.reserve((size_t)n * 4), o_st = w.sc.reserve(sizeof(FeatStats));
+    cc_status st = w.sc.alloc(s);
+    if (st != CC_OK) return st;
+    uint32_t *P = w.sc.at<uint32_t>(o_lab);
+    FeatStats *fs = w.sc.at<FeatStats>(o_st);
+    CC_TRY(cudaMemsetAsync(fs, 0, sizeof(FeatStats), s));
+    CC_TRY(cudaMemsetAsync(w.ctl(), 0, sizeof(Ctl), s));
+    {
+        CC_PROF("k_degree_stats", s);
+        k_degree_stats<OffT><<<gv, TPB, 0, s>>>(static_cast<const OffT *>(g.I), n, g.m, fs, d);
+    }
+    CC_LAUNCH();
+    // k-out sample (k = 2) and its frequent cluster
+    cc_sample_opt so;
+    cc_finish_opt fo;
+    cc_default_opts(&so, &fo);
+    so.seed = seed;
+    int32_t info = 0;
+    if ((st = sample_phase<OffT>(g, so, fo, P, w, di, d, s, &info, w.sc.at<uint32_t>(w.o_counts))) != CC_OK) return st;
+    if ((st = identify_phase(P, n, 0, seed, &w.ctl()->lmax, w, di, d, s, true, true)) != CC_OK) return st;
+    {
+        CC_PROF("k_label_stats", s);
+        k_label_stats<OffT><<<gv, TPB, 0, s>>>(static_cast<const OffT *>(g.I), n, g.m, P, &w.ctl()->lmax, fs, d);
+    }
+    CC_LAUNCH();
+    FeatStats h;
+    CC_TRY(cudaMemcpyAsync(&h, fs, sizeof(h), cudaMemcpyDeviceToHost, s));
+    CC_TRY(cudaStreamSynchronize(s));
+    // capped BFS from the highest-degree vertex (ties: smallest id)
+    const uint32_t src = ~(uint32_t)(h.maxkey & 0xFFFFFFFFull);
+    uint32_t levels = 0;
+    uint64_t reached = 0;
+    if ((st = bfs_capped<OffT>(g, src, 64, P, w, di, d, s, &levels, &reached)) != CC_OK) return st;
+    const double nn = (double)n, mm = (double)g.m > 0 ? (double)g.m : 1.0;
+    const double mean = (double)h.sum_deg / nn;
+    const double var = h.sum_deg2 / nn - mean * mean;
+    float f[CC_MLP_IN];
+    f[0] = (float)std::log2(nn + 1.0);
+    f[1] = (float)std::log2((double)g.m + 1.0);
+    f[2] = (float)mean;
+    f[3] = (float)std::log2((double)(h.maxkey >> 32) + 1.0);
+    f[4] = (float)(mean > 0 ? var / (mean * mean) : 0.0);
+    for (int j = 0; j < 3; ++j) f[5 + j] = (float)(h.cnt[j] / nn);
+    f[8] = (float)(h.cnt[3] / nn);
+    f[9] = (float)(h.cnt[4] / nn);
+    f[10] = (float)(h.edges_gt64 / mm);
+    f[11] = (float)(h.lmax_count / nn);
+    f[12] = (float)(h.roots / nn);
+    f[13] = (float)(h.edges_nonlmax / mm);
+    f[14] = (float)(levels / 64.0);
+    f[15] = (float)(reached / nn);
+    CC_TRY(cudaMemcpyAsync(feat_out, f, sizeof(f), cudaMemcpyHostToDevice, s));
+    CC_TRY(cudaStreamSynchronize(s));
+    return CC_OK;
+}
+
 }  // namespace
 
 // ================================================================ C ABI
@@ -1438,3 +1634,13 @@ cc_status cc_finish(const void *offsets, int offsets_u64, const uint32_t *edges,
 }
 
 }  // extern "C"
+
+extern "C" cc_status cc_features(const void *offsets, int offsets_u64, const uint32_t *edges, uint32_t n, uint64_t m,
+                                 uint64_t seed, float *feat_out, void *stream) {
+    cc_status st = check_graph(offsets, offsets_u64, edges, n, m);
+    if (st != CC_OK) return st;
+    if (n == 0 || !feat_out || !aligned(feat_out, 4)) return CC_ERR_INVALID;
+    Graph g{offsets, offsets_u64 != 0, edges, n, m};
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    return offsets_u64 ? run_features<uint64_t>(g, seed, feat_out, s) : run_features<uint32_t>(g, seed, feat_out, s);
+}

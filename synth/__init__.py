@@ -318,3 +318,52 @@ def batch_config3(count: int, seed: int = 1, lo: int = 6, hi: int = 16):
             h = max(1, n // w)
             graphs.append(grid2d(w, h, 0.5 * float(u[i]), seed=seed * 100003 + i))
     return graphs
+
+
+def cliques_fast(sizes, device="cpu") -> CSR:
+    """Disjoint cliques (vectorised): clique i occupies ids [sum(sizes[:i]), ...)."""
+    sizes = [int(s) for s in sizes]
+    base = 0
+    us, vs = [], []
+    by_size = {}
+    for s in sizes:
+        by_size.setdefault(s, []).append(base)
+        base += s
+    for s, starts in by_size.items():
+        if s < 2:
+            continue
+        iu = torch.triu_indices(s, s, 1, device=device)
+        st = torch.tensor(starts, dtype=torch.int64, device=device)[:, None]
+        us.append((st + iu[0][None, :]).reshape(-1))
+        vs.append((st + iu[1][None, :]).reshape(-1))
+    if not us:
+        z = torch.zeros(0, dtype=torch.int64, device=device)
+        return from_pairs(base, z, z, name="cliques")
+    return from_pairs(base, torch.cat(us), torch.cat(vs), name="cliques")
+
+
+def selector_graph(i: int, seed: int = 1, scale_lo: int = 14, scale_hi: int = 22, device="cpu") -> CSR:
+    """Graph i of the selector's training / held-out families (seeded):
+    i % 4 == 0 RMAT with a in [0.45, 0.65], b = c = (1 - a - 0.05) / 2 and
+    edge factor 4, 8 or 16; 1 a grid with drop probability in [0, 0.5];
+    2 G(n, M) with average degree in [0.5, 8]; 3 disjoint cliques of 4-64
+    vertices.  Scales (log2 n) uniform in [scale_lo, scale_hi]."""
+    u = hash3(seed, 700 + i % 4, torch.tensor([i, i + 1_000_003, i + 2_000_006], dtype=torch.int64))
+    r = (u.to(torch.float64) / 2**32).tolist()
+    scale = scale_lo + min(scale_hi - scale_lo, int(r[0] * (scale_hi - scale_lo + 1)))
+    gseed = seed * 1_000_003 + i
+    fam = i % 4
+    if fam == 0:
+        a = 0.45 + 0.2 * r[1]
+        bc = (1.0 - a - 0.05) / 2
+        ef = (4, 8, 16)[int(r[2] * 3) % 3]
+        return rmat(scale, ef, a=a, b=bc, c=bc, seed=gseed, device=device)
+    n = 1 << scale
+    if fam == 1:
+        w = max(1, int(math.isqrt(n)))
+        return grid2d(w, max(1, n // w), 0.5 * r[1], seed=gseed, device=device)
+    if fam == 2:
+        return erdos_renyi(n, 0.5 + 7.5 * r[1], seed=gseed, device=device)
+    cnt = max(1, n // 34)
+    sz = (4 + (hash3(gseed, 710, torch.arange(cnt, dtype=torch.int64)) % 61)).tolist()
+    return cliques_fast(sz, device=device)

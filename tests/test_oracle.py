@@ -398,3 +398,50 @@ def test_incremental_matches_recompute():
         want = scipy_labels(n, us, vs)
         assert np.array_equal(ans, (want[qs[:, 0]] == want[qs[:, 1]]).astype(np.uint8))
         assert np.array_equal(inc.labels(), want)
+
+
+# ---------------------------------------------------------------- selector network
+def _mlp_case(seed, B=7):
+    from oracle import mlp
+    rng = np.random.default_rng(seed)
+    p = rng.normal(0, 0.3, mlp.NPARAM)
+    d = mlp.unpack(p)
+    d["mu"][:] = rng.normal(0, 1, mlp.IN)
+    d["sigma"][:] = rng.uniform(0.5, 2.0, mlp.IN)
+    p = mlp.pack(d)
+    X = rng.normal(0, 1, (B, mlp.IN))
+    Q = mlp.soft_targets(rng.uniform(1, 3, (B, mlp.OUT)), 0.3)
+    return p, X, Q
+
+
+def test_mlp_gradient_matches_finite_differences():
+    from oracle import mlp
+    p, X, Q = _mlp_case(1)
+    g, _ = mlp.backward(p, X, Q)
+    rng = np.random.default_rng(2)
+    idx = rng.choice(np.arange(2 * mlp.IN, mlp.NPARAM), 60, replace=False)
+    h = 1e-6
+    for j in idx:
+        e = np.zeros_like(p)
+        e[j] = h
+        num = (mlp.loss(p + e, X, Q) - mlp.loss(p - e, X, Q)) / (2 * h)
+        assert abs(num - g[j]) <= 1e-6 + 1e-5 * abs(num), (j, num, g[j])
+    assert np.all(g[:2 * mlp.IN] == 0)
+
+
+def test_mlp_closed_forms():
+    from oracle import mlp
+    p, X, Q = _mlp_case(3)
+    d = mlp.unpack(p)
+    d["W3"][:] = 0
+    d["b3"][:] = 0
+    uniform = np.full_like(Q, 1.0 / mlp.OUT)
+    assert abs(mlp.loss(mlp.pack(d), X, uniform) - np.log(mlp.OUT)) < 1e-12   # zero logits
+    T = np.random.default_rng(4).uniform(1, 2, (5, mlp.OUT))
+    S = mlp.soft_targets(T, 0.1)
+    assert np.allclose(S.sum(axis=1), 1) and np.all(S.argmax(axis=1) == T.argmin(axis=1))
+    # first Adam step: bias-corrected moments give p - lr * g / (|g| + eps)
+    g = np.random.default_rng(5).normal(0, 1, mlp.NPARAM)
+    p2, m2, v2 = mlp.adam(p, g, np.zeros(mlp.NPARAM), np.zeros(mlp.NPARAM), 1, 0.01)
+    want = p - 0.01 * g / (np.abs(g) + 1e-8)
+    assert np.allclose(p2[2 * mlp.IN:], want[2 * mlp.IN:]) and np.array_equal(p2[:2 * mlp.IN], p[:2 * mlp.IN])
