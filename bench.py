@@ -69,6 +69,25 @@ def parse():
     return p.parse_args()
 
 
+def kernel_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture
+    (profiles/traffic.json), or None when the kernels' source has changed
+    since the counters were taken."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            tj = json.load(f)
+        ent = tj["kernels"].get(kernel)
+        src = os.path.join(ROOT, tj["source"])
+        with open(src, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+        if ent is None or sha != tj["source_sha256"]:
+            return None
+        return int(ent["bytes_per_launch"])
+    except Exception:
+        return None
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -149,8 +168,11 @@ def algorithmic_bytes(kernel, n, m, m_finish, n_nz, k, off_bytes):
     ob = off_bytes
     table = {
         "k_iota": 4 * n,                                            # write P
-        # offsets, first edge of each non-isolated vertex, write P
-        "k_kout_hook_first": ob * (n + 1) + 4 * n_nz + 4 * n,
+        # offsets, first edge and (k = 2) random pick of each non-isolated
+        # vertex, write P and the stashed pick
+        "k_kout_hook_first": ob * (n + 1) + 8 * n_nz + 8 * n,
+        # stashed pick, own parent, picked vertex's parent
+        "k_kout_apply_pick": 8 * n + 4 * n_nz,
         # offsets, (k-1) picked edges, own parent and picked parent per pick
         "k_kout_rest": ob * (n + 1) + n_nz * (k - 1) * (4 + 4 + 4),
         "k_compress_mid": 8 * n,                                    # read + write P
@@ -248,8 +270,27 @@ def run_ours(args):
             per_launch_ms = kernels[dom]["ms_avg"]
             ach = ab / (per_launch_ms * 1e-3) / 1e9
             roof = {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
-                    "frac": round(ach / peak, 4), "traffic": None, "peak_kind": peak_kind,
+                    "frac": round(ach / peak, 4), "traffic": kernel_traffic(dom), "peak_kind": peak_kind,
                     "algorithmic_bytes": ab, "ms_avg": round(per_launch_ms, 5)}
+
+    # MapEdges / GatherEdges (Table 8): this GPU's floors for reading the
+    # graph and for one indirect read per edge
+    probes = {}
+    xs = torch.arange(n, dtype=torch.int32, device=dev)
+    pout = torch.empty(n, dtype=torch.int32, device=dev)
+    for name, fn in (("map_edges", lambda: cc.cc_map_edges(off, edg, pout)),
+                     ("gather_edges", lambda: cc.cc_gather_edges(off, edg, xs, pout))):
+        fn()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record()
+        for _ in range(3):
+            fn()
+        p1.record()
+        torch.cuda.synchronize()
+        pms = p0.elapsed_time(p1) / 3
+        probes[name] = {"ms": round(pms, 4), "gedges_s": round(m / (pms * 1e-3) / 1e9, 2),
+                        "csr_gbs": round((off_bytes * (n + 1) + 4 * m) / (pms * 1e-3) / 1e9, 1)}
+    del xs, pout
 
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "Gedges/s", "n_gpus": world, "steps": args.steps,
@@ -261,7 +302,7 @@ def run_ours(args):
                    "freq_samples": args.freq_samples, "l2": "inputs exceed L2 (no flush)",
                    "parallelism": f"replicas x{world}"},
         "hbm_roof_frac": round(hbm_frac, 4), "hbm_roof_peak_gbs": peak,
-        "roofline": roof, "kernels": kernels, "gpu_launches": launches,
+        "roofline": roof, "kernels": kernels, "gpu_launches": launches, "edge_primitives": probes,
         "check": {"invariants_ok": ok, "components": ncomp, "lmax": st["lmax"], "edges_finish": st["edges_finish"],
                   "n_nonisolated": n_nz},
         "gen_s": round(gen_s, 2),

@@ -170,6 +170,17 @@ cc_status cc_finish(const void *offsets, int offsets_u64, const uint32_t *edges,
 #define CC_NOALLOC_MAX_LABELS (1u << 22)
 cc_status cc_identify_frequent_noalloc(const uint32_t *labels, uint32_t n, uint32_t *lmax_out, void *stream);
 
+/* MapEdges and GatherEdges (Section 4, Table 8): per-vertex reductions over
+ * the incident edges, the paper's floors for reading a graph and for one
+ * indirect read per edge.  out (DEVICE uint32[n]): MapEdges writes the
+ * number of edges it read (the degree); GatherEdges writes the sum, mod
+ * 2^32, of x[w] over the neighbours w (x: DEVICE uint32[n]).  Edge ids >= n
+ * are skipped and flagged. */
+cc_status cc_map_edges(const void *offsets, int offsets_u64, const uint32_t *edges, uint32_t n, uint64_t m,
+                       uint32_t *out, void *stream);
+cc_status cc_gather_edges(const void *offsets, int offsets_u64, const uint32_t *edges, uint32_t n, uint64_t m,
+                          const uint32_t *x, uint32_t *out, void *stream);
+
 /* Batched static connectivity of many independent graphs in one persistent
  * launch (no counterpart in the paper, which labels one graph per call).
  * Each graph is labelled as Algorithm 1 with no sampling would label it:

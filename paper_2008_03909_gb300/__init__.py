@@ -116,6 +116,10 @@ _SIGS = {
                                         ctypes.c_uint64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
     "cc_server_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
     "cc_server_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "cc_map_edges": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64,
+                                    ctypes.c_void_p, ctypes.c_void_p]),
+    "cc_gather_edges": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint32,
+                                       ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "cc_features": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64,
                                    ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]),
     "cc_mlp_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]),
@@ -352,6 +356,26 @@ def cc_batched_autotune(gv, offsets, edges, labels_out=None, stream=None):
     _check(lib().cc_batched_autotune(*a, ctypes.c_void_p(labels_out.data_ptr()), ctypes.byref(best),
                                      ctypes.byref(ms), _stream(stream)), "cc_batched_autotune")
     return labels_out, best, ms.value
+
+
+def cc_map_edges(offsets, edges, out=None, stream=None) -> torch.Tensor:
+    """MapEdges: edges read per vertex (int32 view of uint32)."""
+    Ip, u64, Ap, n, m = _graph_args(offsets, edges)
+    if out is None:
+        out = torch.empty(n, dtype=torch.int32, device=offsets.device)
+    _check(lib().cc_map_edges(Ip, u64, Ap, n, m, ctypes.c_void_p(out.data_ptr()), _stream(stream)), "cc_map_edges")
+    return out
+
+
+def cc_gather_edges(offsets, edges, x, out=None, stream=None) -> torch.Tensor:
+    """GatherEdges: per vertex, the sum mod 2^32 of x over its neighbours."""
+    Ip, u64, Ap, n, m = _graph_args(offsets, edges)
+    _dev(x, (torch.int32,), "x")
+    if out is None:
+        out = torch.empty(n, dtype=torch.int32, device=offsets.device)
+    _check(lib().cc_gather_edges(Ip, u64, Ap, n, m, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                 _stream(stream)), "cc_gather_edges")
+    return out
 
 
 def cc_features(offsets, edges, seed: int = 1, out=None, stream=None) -> torch.Tensor:

@@ -176,7 +176,8 @@ void launch_kout(unsigned grid, cudaStream_t s, const OffT *I, const uint32_t *A
 template <typename OffT>
 __global__ void __launch_bounds__(256, 8) k_kout_hook_first(const OffT *I, const uint32_t *A, uint32_t n,
                                                             uint64_t m, uint32_t *P, uint32_t *defer,
-                                                            uint32_t *ndefer, Dev d) {
+                                                            uint32_t *ndefer, uint32_t *pick1, uint64_t seed,
+                                                            Dev d) {
     const int lane = threadIdx.x & 31;
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -203,13 +204,20 @@ __global__ void __launch_bounds__(256, 8) k_kout_hook_first(const OffT *I, const
             beg[j] = o[j];
             end[j] = lane < 31 ? nxt : first;
         }
-        uint32_t w[4];
+        uint32_t w[4], r[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const uint64_t v = base + 32 * j + lane;
             uint64_t b = 0, e = 0;
             if (v < n) clamp_range(beg[j], end[j], m, b, e, d);
             w[j] = e > b ? ld_stream(A + b) : NONE;
+            // with k = 2 the random pick (slot 1) is read here too and kept
+            // for the second round, so that round reads no offsets or edges
+            r[j] = NONE;
+            if (pick1 && e > b) {
+                const uint64_t off = ((draw64(seed ^ TAG_KOUT, v * 2 + 1) >> 32) * (e - b)) >> 32;
+                r[j] = ld_stream(A + b + off);
+            }
         }
         // the next step's offsets load while this step's first edges are read
         if (base + nw * 128 < n) load(base + nw * 128);
@@ -220,11 +228,28 @@ __global__ void __launch_bounds__(256, 8) k_kout_hook_first(const OffT *I, const
             if (w[j] != NONE && w[j] >= n) { atomicOr(d.err, ERR_BAD_EDGE); w[j] = NONE; }
             if (v < n) P[v] = (w[j] != NONE && w[j] < v) ? w[j] : (uint32_t)v;
             nd += (w[j] != NONE && w[j] > v);
+            if (pick1 && v < n) {
+                if (r[j] != NONE && r[j] >= n) { atomicOr(d.err, ERR_BAD_EDGE); r[j] = NONE; }
+                pick1[v] = r[j] == (uint32_t)v ? NONE : r[j];
+            }
         }
         uint32_t slot = warp_append_full(ndefer, nd);
 #pragma unroll
         for (int j = 0; j < 4; ++j)
             if (w[j] != NONE && w[j] > base + 32 * j + lane) defer[slot++] = (uint32_t)(base + 32 * j + lane);
+    }
+}
+
+// Second round for k = 2: Union(v, pick1[v]) from the stash written in the
+// first pass (coalesced reads of the stash and of P[v]).
+template <class E>
+__global__ void __launch_bounds__(256, 8) k_kout_apply_pick(const uint32_t *pick1, uint32_t n, uint32_t *P, Dev d) {
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
+         v += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t w = pick1[v];
+        uint32_t u1[1] = {(uint32_t)v}, w1[1] = {w};
+        bool ok[1] = {w != NONE};
+        unite_pairs<E, 1>(P, u1, w1, ok, d);
     }
 }
 
@@ -805,7 +830,7 @@ struct Graph {
 // Scratch layout of one call.
 struct Work {
     Scratch sc;
-    size_t o_defer = 0;
+    size_t o_defer = 0, o_pick = 0;
     size_t o_ctl = 0, o_chunks = 0, o_counts = 0, o_prev = 0, o_light = 0, o_vis = 0, o_q0 = 0, o_q1 = 0,
            o_bm0 = 0, o_bm1 = 0, o_cand = 0;
     bool has_counts = false, has_sv = false, has_bfs = false, has_ldd = false;
@@ -818,7 +843,10 @@ void plan(Work &w, const Graph &g, int sample_kind, uint32_t freq_samples, int f
     w.o_ctl = w.sc.reserve(sizeof(Ctl));
     w.chunk_cap = chunk_capacity(n, g.m);
     w.o_chunks = w.sc.reserve(w.chunk_cap * sizeof(ChunkRef));
-    if (sample_kind == CC_SAMPLE_KOUT) w.o_defer = w.sc.reserve(n * 4);
+    if (sample_kind == CC_SAMPLE_KOUT) {
+        w.o_defer = w.sc.reserve(n * 4);
+        w.o_pick = w.sc.reserve(n * 4);
+    }
     if (sample_kind != CC_SAMPLE_NONE && freq_samples == 0) {
         w.has_counts = true;
         w.o_counts = w.sc.reserve(n * 4);
@@ -1142,9 +1170,10 @@ cc_status sample_phase(const Graph &g, const cc_sample_opt &so, const cc_finish_
         uint32_t *defer = w.sc.at<uint32_t>(w.o_defer);
         Ctl *ctl = w.ctl();
         CC_TRY(cudaMemsetAsync(&ctl->ndefer, 0, 4, s));
+        uint32_t *pick1 = so.k == 2 ? w.sc.at<uint32_t>(w.o_pick) : nullptr;
         {
             CC_PROF("k_kout_hook_first", s);
-            k_kout_hook_first<OffT><<<gv, TPB, 0, s>>>(I, g.A, g.n, g.m, P, defer, &ctl->ndefer, d);
+            k_kout_hook_first<OffT><<<gv, TPB, 0, s>>>(I, g.A, g.n, g.m, P, defer, &ctl->ndefer, pick1, so.seed, d);
         }
         {
             CC_PROF("k_kout_defer", s);
@@ -1156,7 +1185,8 @@ cc_status sample_phase(const Graph &g, const cc_sample_opt &so, const cc_finish_
                 k_shortcut<false><<<gv, TPB, 0, s>>>(P, nullptr, g.n, nullptr, d);
             }
             CC_PROF("k_kout_rest", s);
-            launch_kout<OffT, E>(gv, s, I, g.A, g.n, g.m, so.k, so.seed, P, d, 1u, so.k);
+            if (pick1) k_kout_apply_pick<E><<<gv, TPB, 0, s>>>(pick1, g.n, P, d);
+            else launch_kout<OffT, E>(gv, s, I, g.A, g.n, g.m, so.k, so.seed, P, d, 1u, so.k);
         }
         if (count_into) {
             CC_TRY(cudaMemsetAsync(count_into, 0, (size_t)g.n * 4, s));

@@ -246,3 +246,19 @@ def test_unaligned_label_slices():
         wl, _ = oracle.identify_frequent(oracle.kout_sample(*g.numpy(), 2, 1))
         assert int(lm.item()) == wl
     assert cc.device_error() == 0
+
+
+@pytest.mark.parametrize("u64", [True, False])
+def test_map_and_gather_edges_bit_exact(u64):
+    """Table 8's primitives against their definitions (numpy reductions)."""
+    for g in (synth.rmat(16, 8, seed=2), synth.star(70000, centre=3), synth.empty(9)):
+        off, edg = on_gpu(g, u64)
+        o, e = g.numpy()
+        deg = np.diff(o).astype(np.uint32)
+        assert np.array_equal(cc.cc_map_edges(off, edg).cpu().numpy().view(np.uint32), deg)
+        x = np.random.default_rng(1).integers(0, 2**32, size=g.n, dtype=np.uint64).astype(np.uint32)
+        got = cc.cc_gather_edges(off, edg, torch.from_numpy(x.view(np.int32)).cuda()).cpu().numpy().view(np.uint32)
+        want = np.zeros(g.n, np.uint64)
+        src = np.repeat(np.arange(g.n), np.diff(o))
+        np.add.at(want, src, x[e.astype(np.int64)].astype(np.uint64))
+        assert np.array_equal(got, (want % 2**32).astype(np.uint32))
