@@ -69,6 +69,21 @@ def parse():
     return p.parse_args()
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The slowest rank's value (timing is reported for the whole job)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 def kernel_traffic(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu capture
     (profiles/traffic.json), or None when the kernels' source has changed
@@ -247,13 +262,10 @@ def run_ours(args):
     prof = cc.profile_read()
     cc.profile_enable(False)
     launches = cc.launch_count() - launches0
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, dev)
     if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
-    value = world * m / (ms * 1e-3) / 1e9
+    value = job_rate(m, world, ms) / 1e9
     peak, peak_kind = peaks()
     off_bytes = 8 if off.dtype == torch.int64 else 4
     b_csr = off_bytes * (n + 1) + 4 * m
@@ -323,11 +335,7 @@ def run_ours(args):
         t1 = time.perf_counter()
         for _ in range(k2):
             cc.cc_static_host(h_off, h_edg, so, fo, h_lab)
-        e2e_s = (time.perf_counter() - t1) / k2
-        if dist:
-            t = torch.tensor([e2e_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks((time.perf_counter() - t1) / k2, dist, dev)
         same = bool(torch.equal(h_lab, lab.cpu()))
         out["e2e"] = {"value": round(world * m / e2e_s / 1e9, 3), "unit": "Gedges/s",
                       "h2d_bytes_per_step": b_csr, "d2h_bytes_per_step": 4 * n, "ms_per_step": round(e2e_s * 1e3, 3),
@@ -581,7 +589,7 @@ def cpu_baseline(off, edg, seconds):
     n = offs.shape[0] - 1
     # calibrate on a small prefix, then run a prefix sized for `seconds`
     target_e = 20_000_000
-    u_end = int(np.searchsorted(offs, target_e))
+    u_end = min(n, int(np.searchsorted(offs, target_e)))
     e_end = int(offs[u_end])
     edges = edg[:e_end].cpu().numpy().view(np.uint32)
     P = np.arange(n, dtype=np.uint32)
@@ -591,7 +599,7 @@ def cpu_baseline(off, edg, seconds):
     rate = cnt / max(dt, 1e-9)
     want_e = min(int(offs[-1]), int(rate * seconds))
     if want_e > e_end:
-        u_end = int(np.searchsorted(offs, want_e))
+        u_end = min(n, int(np.searchsorted(offs, want_e)))
         e_end = int(offs[u_end])
         edges = edg[:e_end].cpu().numpy().view(np.uint32)
         P = np.arange(n, dtype=np.uint32)
@@ -630,13 +638,13 @@ def run_reference(args):
     n = g.n
     per_step = max(1.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
     target = 5_000_000
-    u_end = int(np.searchsorted(offs, target))
+    u_end = min(n, int(np.searchsorted(offs, target)))
     edges = g.edges[: int(offs[u_end])].cpu().numpy().view(np.uint32)
     t0 = time.perf_counter()
     _, cnt = _prefix(oracle, offs, edges, u_end, np.arange(n, dtype=np.uint32))
     rate = cnt / max(time.perf_counter() - t0, 1e-9)
     want = min(int(offs[-1]), int(rate * per_step))
-    u_end = int(np.searchsorted(offs, want))
+    u_end = min(n, int(np.searchsorted(offs, want)))
     e_end = int(offs[u_end])
     edges = g.edges[:e_end].cpu().numpy().view(np.uint32)
     for _ in range(args.warmup):
