@@ -79,6 +79,10 @@ def lib():
             L.oracle_incr_query.argtypes = [c.c_uint32, u32p, u32p, c.c_uint64, u8p]
             L.oracle_incr_labels.restype = None
             L.oracle_incr_labels.argtypes = [c.c_uint32, u32p, u32p]
+            L.oracle_spanning_forest.restype = c.c_uint64
+            L.oracle_spanning_forest.argtypes = [c.c_uint32, u64p, u32p, u32p]
+            L.oracle_check_forest.restype = c.c_int
+            L.oracle_check_forest.argtypes = [c.c_uint32, u64p, u32p, u32p, c.c_uint64, u32p]
             _lib = L
     return _lib
 
@@ -233,3 +237,27 @@ class Incremental:
         lib().oracle_incr_labels(self.n, self.P.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
                                  lab.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
         return lab
+
+
+def spanning_forest(offsets, edges):
+    """Spanning forest by sequential union-find: uint32[count, 2] pairs."""
+    n, (I, Ip), (A, Ap) = _graph(_as_np(offsets), _as_np(edges))
+    out = np.empty(2 * max(n - 1, 1), np.uint32)
+    cnt = lib().oracle_spanning_forest(n, Ip, Ap, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
+    return out[: 2 * cnt].reshape(-1, 2)
+
+
+FOREST_CHECK = {0: "ok", 1: "endpoint out of range", 2: "not an edge of G", 3: "closes a cycle",
+                4: "joins two components of G", 5: "does not span a component"}
+
+
+def check_forest(offsets, edges, pairs, labels=None) -> int:
+    """0 if `pairs` (uint32[count, 2]) is a spanning forest of G, else the
+    code of the first failed property (FOREST_CHECK).  `labels` are G's
+    canonical labels (computed by O1 when not given)."""
+    n, (I, Ip), (A, Ap) = _graph(_as_np(offsets), _as_np(edges))
+    if labels is None:
+        labels, _ = cc_uf(I, A)
+    L, Lp = _u32(_as_np(labels))
+    pr, pp = _u32(_as_np(pairs).reshape(-1))
+    return int(lib().oracle_check_forest(n, Ip, Ap, pp, pr.size // 2, Lp))

@@ -31,6 +31,12 @@
  *   oracle_connectivity   Algorithm 1 composed from the above
  *   oracle_incr_*         batch-incremental setting, Section 3.5 and
  *                         Appendix B.4 (inserts, then queries, per batch)
+ *   oracle_spanning_forest   spanning forest (Section 3.5 "Spanning Forest"
+ *                         and its appendix): the edges whose union joined
+ *                         two trees in a sequential union-find (O1)
+ *   oracle_check_forest   validity of any claimed spanning forest: every
+ *                         pair is an edge of G, the pairs are acyclic, and
+ *                         they connect exactly the components of G
  *
  * Random draws: counter-based, the ctr-th output of a SplitMix64 sequence
  * (Steele, Lea, Flood, "Fast splittable pseudorandom number generators",
@@ -415,4 +421,73 @@ void oracle_incr_query(uint32_t n, uint32_t *P, const uint32_t *pairs, uint64_t 
 }
 void oracle_incr_labels(uint32_t n, uint32_t *P, uint32_t *label) {
     for (uint32_t v = 0; v < n; v++) label[v] = uf_find(P, v);
+}
+
+/* ---- spanning forest -------------------------------------------------- */
+/* A spanning forest of G: one tree per component, n - #components edges.
+ * Sequential union-find over every edge; an edge is kept iff its union
+ * joined two different trees.  Returns the number of pairs written to
+ * out[2*i], out[2*i+1] (room for 2*(n-1) words). */
+uint64_t oracle_spanning_forest(uint32_t n, const uint64_t *I, const uint32_t *A, uint32_t *out) {
+    uint32_t *P = (uint32_t *)malloc((size_t)(n ? n : 1) * sizeof(uint32_t));
+    uint64_t cnt = 0;
+    for (uint32_t v = 0; v < n; ++v) P[v] = v;
+    for (uint32_t u = 0; u < n; ++u)
+        for (uint64_t e = I[u]; e < I[u + 1]; ++e)
+            if (uf_union(P, u, A[e])) {
+                out[2 * cnt] = u;
+                out[2 * cnt + 1] = A[e];
+                ++cnt;
+            }
+    free(P);
+    return cnt;
+}
+
+/* is (u, v) an edge of G?  adjacency lists sorted: binary search, else scan */
+static int has_edge(const uint64_t *I, const uint32_t *A, uint32_t u, uint32_t v, int sorted) {
+    uint64_t lo = I[u], hi = I[u + 1];
+    if (!sorted) {
+        for (uint64_t e = lo; e < hi; ++e)
+            if (A[e] == v) return 1;
+        return 0;
+    }
+    while (lo < hi) {
+        uint64_t mid = lo + (hi - lo) / 2;
+        if (A[mid] < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo < I[u + 1] && A[lo] == v;
+}
+
+/* Checks a claimed spanning forest F (count pairs) of G against the
+ * canonical labels `label` of G.  Returns 0 if F is a spanning forest, else
+ * the first failed property: 1 a pair with an endpoint >= n, 2 a pair that
+ * is not an edge of G, 3 a pair that closes a cycle in F, 4 a pair joining
+ * two different components of G, 5 F's components differ from G's (too few
+ * pairs). */
+int oracle_check_forest(uint32_t n, const uint64_t *I, const uint32_t *A, const uint32_t *pairs, uint64_t count,
+                        const uint32_t *label) {
+    int sorted = 1;
+    for (uint32_t u = 0; u < n && sorted; ++u)
+        for (uint64_t e = I[u] + 1; e < I[u + 1]; ++e)
+            if (A[e - 1] > A[e]) { sorted = 0; break; }
+    uint32_t *P = (uint32_t *)malloc((size_t)(n ? n : 1) * sizeof(uint32_t));
+    for (uint32_t v = 0; v < n; ++v) P[v] = v;
+    int bad = 0;
+    for (uint64_t i = 0; i < count && !bad; ++i) {
+        uint32_t u = pairs[2 * i], v = pairs[2 * i + 1];
+        if (u >= n || v >= n) bad = 1;
+        else if (!has_edge(I, A, u, v, sorted)) bad = 2;
+        else if (label[u] != label[v]) bad = 4;
+        else if (!uf_union(P, u, v)) bad = 3;
+    }
+    if (!bad) {
+        /* acyclic pairs inside G's components: F spans them iff it has
+         * exactly n - #components pairs */
+        uint64_t comps = 0;
+        for (uint32_t v = 0; v < n; ++v) comps += label[v] == v;
+        if (count != (uint64_t)n - comps) bad = 5;
+    }
+    free(P);
+    return bad;
 }

@@ -445,3 +445,99 @@ def test_mlp_closed_forms():
     p2, m2, v2 = mlp.adam(p, g, np.zeros(mlp.NPARAM), np.zeros(mlp.NPARAM), 1, 0.01)
     want = p - 0.01 * g / (np.abs(g) + 1e-8)
     assert np.allclose(p2[2 * mlp.IN:], want[2 * mlp.IN:]) and np.array_equal(p2[:2 * mlp.IN], p[:2 * mlp.IN])
+
+
+# ---------------------------------------------------------------- spanning forest
+def forest_is_valid_bruteforce(n, pairs, forest):
+    """Independent of the oracle's union-find: every forest pair is an edge,
+    the forest has no cycle (DFS over an adjacency dict), and its
+    transitive-closure components equal those of the graph."""
+    edges = {frozenset(p) for p in pairs}
+    if any(frozenset((int(u), int(v))) not in edges or u == v for u, v in forest):
+        return False
+    adj = {v: [] for v in range(n)}
+    for i, (u, v) in enumerate(forest):
+        adj[int(u)].append((int(v), i))
+        adj[int(v)].append((int(u), i))
+    seen = [False] * n
+    for s in range(n):
+        if seen[s]:
+            continue
+        stack = [(s, -1)]
+        seen[s] = True
+        while stack:
+            x, via = stack.pop()
+            for y, i in adj[x]:
+                if i == via:
+                    continue
+                if seen[y]:
+                    return False          # a second path to y: a cycle
+                seen[y] = True
+                stack.append((y, i))
+    return np.array_equal(closure_labels(n, [tuple(map(int, p)) for p in forest]), closure_labels(n, pairs))
+
+
+def test_spanning_forest_bruteforce_all_graphs_n5():
+    n = 5
+    allpairs = list(itertools.combinations(range(n), 2))
+    for mask in range(1 << len(allpairs)):
+        pairs = [allpairs[i] for i in range(len(allpairs)) if mask >> i & 1]
+        g = synth.from_edge_list(n, pairs)
+        off, edg = g.numpy()
+        F = oracle.spanning_forest(off, edg)
+        assert forest_is_valid_bruteforce(n, pairs, F), (pairs, F)
+        assert oracle.check_forest(off, edg, F) == 0
+
+
+def test_spanning_forest_closed_forms():
+    # a path, a star and a random tree are their own spanning trees
+    rng = np.random.default_rng(3)
+    parent = [int(rng.integers(0, v)) for v in range(1, 500)]
+    tree = synth.from_edge_list(500, [(v, p) for v, p in zip(range(1, 500), parent)])
+    for g in (synth.path(300), synth.star(200, centre=17), tree):
+        off, edg = g.numpy()
+        F = oracle.spanning_forest(off, edg)
+        src, dst = csr_pairs(g)
+        want = {frozenset((int(a), int(b))) for a, b in zip(src, dst)}
+        assert {frozenset(map(int, p)) for p in F} == want
+    # a cycle keeps n - 1 of its n edges; disjoint cliques sum(s - 1); an
+    # empty graph none
+    cyc = synth.from_edge_list(64, [(i, (i + 1) % 64) for i in range(64)])
+    assert oracle.spanning_forest(*cyc.numpy()).shape == (63, 2)
+    sizes = [4, 9, 1, 30, 2]
+    assert oracle.spanning_forest(*synth.cliques(sizes).numpy()).shape == (sum(s - 1 for s in sizes), 2)
+    assert oracle.spanning_forest(*synth.empty(10).numpy()).shape == (0, 2)
+
+
+def test_check_forest_rejects_planted_mistakes():
+    g = synth.grid2d(30, 20, 0.3, seed=4)
+    off, edg = g.numpy()
+    lab, _ = oracle.cc_uf(off, edg)
+    F = oracle.spanning_forest(off, edg)
+    assert oracle.check_forest(off, edg, F, lab) == 0
+    # a pair that is not an edge (two far-apart grid vertices)
+    bad = F.copy()
+    bad[0] = (0, 599)
+    assert oracle.check_forest(off, edg, bad, lab) in (2,)
+    # a repeated pair closes a cycle
+    assert oracle.check_forest(off, edg, np.vstack([F, F[:1]]), lab) == 3
+    # a dropped pair leaves a component unspanned
+    assert oracle.check_forest(off, edg, F[1:], lab) == 5
+    # an endpoint out of range
+    bad = F.copy()
+    bad[3, 1] = g.n
+    assert oracle.check_forest(off, edg, bad, lab) == 1
+    # wrong labels: a forest pair across two claimed components
+    lab2 = lab.copy()
+    u = int(F[0, 0])
+    lab2[lab2 == lab[u]] = np.arange(g.n, dtype=np.uint32)[lab2 == lab[u]]
+    assert oracle.check_forest(off, edg, F, lab2) == 4
+
+
+def test_spanning_forest_workload_shapes():
+    for g in (synth.rmat(12, 8, seed=9), synth.grid2d(60, 40, 0.45, seed=1), synth.erdos_renyi(6000, 1.2, seed=2)):
+        off, edg = g.numpy()
+        lab, links = oracle.cc_uf(off, edg)
+        F = oracle.spanning_forest(off, edg)
+        assert len(F) == links == g.n - int((lab == np.arange(g.n)).sum())
+        assert oracle.check_forest(off, edg, F, lab) == 0
