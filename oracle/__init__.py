@@ -22,6 +22,7 @@ _lib = None
 
 NONE = 0xFFFFFFFF
 SAMPLE = {"none": 0, "kout": 1, "bfs": 2, "ldd": 3}
+KOUT_RULE = {"hybrid": 0, "afforest": 1, "pure": 2}
 FINISH = {"uf_rem_cas": 0, "uf_async": 1, "sv": 2, "lt_prf": 3}
 
 
@@ -55,9 +56,9 @@ def lib():
             L.oracle_identify_frequent.restype = c.c_uint32
             L.oracle_identify_frequent.argtypes = [c.c_uint32, u32p, c.c_uint32, c.c_uint64, u64p]
             L.oracle_kout_pick.restype = c.c_uint32
-            L.oracle_kout_pick.argtypes = [u64p, u32p, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint64]
+            L.oracle_kout_pick.argtypes = [u64p, u32p, c.c_uint32, c.c_uint32, c.c_uint32, c.c_uint64, c.c_int]
             L.oracle_kout_sample.restype = None
-            L.oracle_kout_sample.argtypes = [c.c_uint32, u64p, u32p, c.c_uint32, c.c_uint64, u32p]
+            L.oracle_kout_sample.argtypes = [c.c_uint32, u64p, u32p, c.c_uint32, c.c_uint64, c.c_int, u32p]
             L.oracle_bfs_sample.restype = c.c_int
             L.oracle_bfs_sample.argtypes = [c.c_uint32, u64p, u32p, c.c_uint32, c.c_uint64, u32p]
             L.oracle_ldd_schedule.restype = c.c_uint64
@@ -71,7 +72,7 @@ def lib():
             L.oracle_finish_lt_prf.restype = c.c_int
             L.oracle_finish_lt_prf.argtypes = [c.c_uint32, u64p, u32p, u32p, c.c_uint32]
             L.oracle_connectivity.restype = c.c_int
-            L.oracle_connectivity.argtypes = [c.c_uint32, u64p, u32p, c.c_int, c.c_uint32, c.c_uint32,
+            L.oracle_connectivity.argtypes = [c.c_uint32, u64p, u32p, c.c_int, c.c_uint32, c.c_int, c.c_uint32,
                                               c.c_double, c.c_uint64, c.c_uint32, c.c_int, u32p, u64p]
             L.oracle_incr_insert.restype = None
             L.oracle_incr_insert.argtypes = [c.c_uint32, u32p, u32p, c.c_uint64]
@@ -152,15 +153,16 @@ def identify_frequent(labels, samples: int = 0, seed: int = 0):
     return int(lm), int(cnt.value)
 
 
-def kout_pick(offsets, edges, v: int, k: int, j: int, seed: int) -> int:
+def kout_pick(offsets, edges, v: int, k: int, j: int, seed: int, rule: str = "hybrid") -> int:
+    """Pick j of vertex v under the selection rule (NONE: no pick)."""
     n, (I, Ip), (A, Ap) = _graph(_as_np(offsets), _as_np(edges))
-    return int(lib().oracle_kout_pick(Ip, Ap, v, k, j, seed))
+    return int(lib().oracle_kout_pick(Ip, Ap, v, k, j, seed, KOUT_RULE[rule]))
 
 
-def kout_sample(offsets, edges, k: int = 2, seed: int = 1):
+def kout_sample(offsets, edges, k: int = 2, seed: int = 1, rule: str = "hybrid"):
     n, (I, Ip), (A, Ap) = _graph(_as_np(offsets), _as_np(edges))
     lab = np.empty(n, np.uint32)
-    lib().oracle_kout_sample(n, Ip, Ap, k, seed, lab.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
+    lib().oracle_kout_sample(n, Ip, Ap, k, seed, KOUT_RULE[rule], lab.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
     return lab
 
 
@@ -200,12 +202,12 @@ def finish(offsets, edges, labels, lmax: int, kind: str = "uf_rem_cas"):
 
 
 def connectivity(offsets, edges, sample: str = "none", finish: str = "uf_rem_cas", k: int = 2,
-                 tries: int = 3, beta: float = 0.2, seed: int = 1, freq_samples: int = 0):
+                 tries: int = 3, beta: float = 0.2, seed: int = 1, freq_samples: int = 0, kout_rule: str = "hybrid"):
     """Algorithm 1: labels and stats dict (lmax, applied, rounds, sample_info)."""
     n, (I, Ip), (A, Ap) = _graph(_as_np(offsets), _as_np(edges))
     lab = np.empty(n, np.uint32)
     st = np.zeros(4, np.uint64)
-    rc = lib().oracle_connectivity(n, Ip, Ap, SAMPLE[sample], k, tries, beta, seed, freq_samples,
+    rc = lib().oracle_connectivity(n, Ip, Ap, SAMPLE[sample], k, KOUT_RULE[kout_rule], tries, beta, seed, freq_samples,
                                    FINISH[finish], lab.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
                                    st.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
     assert rc == 0

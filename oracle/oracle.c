@@ -154,14 +154,17 @@ uint32_t oracle_identify_frequent(uint32_t n, const uint32_t *label, uint32_t sa
     return best;
 }
 
-/* ---- k-out sampling (Section 3.2, Algorithm 4) ------------------------ */
-/* Neighbour pick j of vertex v (deg > 0): j = 0 is the first edge A[I[v]];
- * j >= 1 is A[I[v] + r], r = floor(hi32(out(seed ^ TAG_KOUT, v*k + j)) * deg
- * / 2^32), a uniform pick with replacement. */
+/* ---- k-out sampling (Section 3.2, Algorithm 4; variants, Appendix C.4) - */
+/* Neighbour pick j (0 <= j < k) of vertex v (deg > 0) under the selection
+ * rule: 0 hybrid (the first edge, then k - 1 uniform picks), 1 afforest
+ * (the first k edges; pick j exists only if j < deg), 2 pure (k uniform
+ * picks).  A uniform pick is A[I[v] + r], r = floor(hi32(out(seed ^
+ * TAG_KOUT, v*k + j)) * deg / 2^32), with replacement.  NONE: no pick. */
 uint32_t oracle_kout_pick(const uint64_t *I, const uint32_t *A, uint32_t v, uint32_t k,
-                          uint32_t j, uint64_t seed) {
+                          uint32_t j, uint64_t seed, int rule) {
     uint64_t deg = I[v + 1] - I[v];
-    if (j == 0) return A[I[v]];
+    if (rule == 1) return j < deg ? A[I[v] + j] : NONE;
+    if (rule == 0 && j == 0) return A[I[v]];
     uint64_t h = oracle_draw(seed ^ TAG_KOUT, (uint64_t)v * k + j) >> 32;
     return A[I[v] + ((h * deg) >> 32)];
 }
@@ -169,11 +172,14 @@ uint32_t oracle_kout_pick(const uint64_t *I, const uint32_t *A, uint32_t v, uint
 /* Sampled labels: union-find over the picked edges, then full compression,
  * so label[v] = min id of v's component in the sampled subgraph. */
 void oracle_kout_sample(uint32_t n, const uint64_t *I, const uint32_t *A, uint32_t k,
-                        uint64_t seed, uint32_t *label) {
+                        uint64_t seed, int rule, uint32_t *label) {
     for (uint32_t i = 0; i < n; i++) label[i] = i;
     for (uint32_t v = 0; v < n; v++) {
         if (I[v + 1] == I[v]) continue;
-        for (uint32_t j = 0; j < k; j++) uf_union(label, v, oracle_kout_pick(I, A, v, k, j, seed));
+        for (uint32_t j = 0; j < k; j++) {
+            uint32_t w = oracle_kout_pick(I, A, v, k, j, seed, rule);
+            if (w != NONE) uf_union(label, v, w);
+        }
     }
     for (uint32_t v = 0; v < n; v++) label[v] = uf_find(label, v);
 }
@@ -376,20 +382,21 @@ int oracle_finish_lt_prf(uint32_t n, const uint64_t *I, const uint32_t *A, uint3
 }
 
 /* ---- Algorithm 1 ------------------------------------------------------ */
-/* sample: 0 none, 1 k-out, 2 BFS, 3 LDD; finish: 0/1 union-find (all
+/* sample: 0 none, 1 k-out (kout_rule: 0 hybrid, 1 afforest, 2 pure), 2 BFS,
+ * 3 LDD; finish: 0/1 union-find (all
  * union-find variants reach the same sequential result), 2 SV, 3 LT-PRF.
  * With no sampling there is no frequent component to skip.
  * stats (optional, 4 entries): L_max, edges applied by a union-find finish
  * (0 otherwise), rounds of an SV/LT finish (0 otherwise), sampling result
  * (BFS try index or LDD rounds). */
 int oracle_connectivity(uint32_t n, const uint64_t *I, const uint32_t *A, int sample, uint32_t k,
-                        uint32_t tries, double beta, uint64_t seed, uint32_t freq_samples,
+                        int kout_rule, uint32_t tries, double beta, uint64_t seed, uint32_t freq_samples,
                         int finish, uint32_t *label, uint64_t *stats) {
     uint64_t st[4] = {NONE, 0, 0, 0};
     for (uint32_t i = 0; i < n; i++) label[i] = i;
     switch (sample) {
         case 0: break;
-        case 1: oracle_kout_sample(n, I, A, k, seed, label); break;
+        case 1: oracle_kout_sample(n, I, A, k, seed, kout_rule, label); break;
         case 2: st[3] = (uint64_t)(int64_t)oracle_bfs_sample(n, I, A, tries, seed, label); break;
         case 3: st[3] = (uint64_t)oracle_ldd_sample(n, I, A, beta, label); break;
         default: return -1;

@@ -208,7 +208,7 @@ def test_identify_frequent_sampled_positions():
 
 
 # ---------------------------------------------------------------- sampling
-def kout_edges_py(g, k, seed):
+def kout_edges_py(g, k, seed, rule="hybrid"):
     off, edg = g.numpy()
     us, vs = [], []
     for v in range(g.n):
@@ -216,7 +216,11 @@ def kout_edges_py(g, k, seed):
         if d == 0:
             continue
         for j in range(k):
-            if j == 0:
+            if rule == "afforest":
+                if j >= d:
+                    continue
+                w = edg[off[v] + j]
+            elif j == 0 and rule == "hybrid":
                 w = edg[off[v]]
             else:
                 h = splitmix_out(seed ^ 0x6B6F7574, v * k + j) >> 32
@@ -227,13 +231,48 @@ def kout_edges_py(g, k, seed):
 
 
 @pytest.mark.parametrize("k", [1, 2, 3])
-def test_kout_sample_is_cc_of_picked_edges(k):
+@pytest.mark.parametrize("rule", ["hybrid", "afforest", "pure"])
+def test_kout_sample_is_cc_of_picked_edges(k, rule):
     for g in (synth.rmat(10, 8, seed=2), synth.grid2d(30, 30, 0.3, seed=1), synth.erdos_renyi(3000, 2.0)):
         off, edg = g.numpy()
-        us, vs = kout_edges_py(g, k, seed=77)
+        us, vs = kout_edges_py(g, k, seed=77, rule=rule)
         want = scipy_labels(g.n, us, vs)
-        got = oracle.kout_sample(off, edg, k=k, seed=77)
+        got = oracle.kout_sample(off, edg, k=k, seed=77, rule=rule)
         assert np.array_equal(got, want)
+
+
+def test_kout_rules_closed_forms():
+    g = synth.rmat(11, 8, seed=4)
+    off, edg = g.numpy()
+    maxdeg = int(np.diff(off).max())
+    # afforest with k >= the maximum degree samples every edge: exact labels
+    assert np.array_equal(oracle.kout_sample(off, edg, k=maxdeg, rule="afforest"), oracle.cc_uf(off, edg)[0])
+    # hybrid and afforest coincide at k = 1 (both take the first edge)
+    assert np.array_equal(oracle.kout_sample(off, edg, k=1, rule="afforest"),
+                          oracle.kout_sample(off, edg, k=1, seed=5, rule="hybrid"))
+    # afforest pick j is the j-th neighbour, none past the degree
+    v = int(np.argmax(np.diff(off) == 3))
+    assert [oracle.kout_pick(off, edg, v, 5, j, 1, "afforest") for j in range(5)] == \
+        [int(x) for x in edg[off[v]:off[v] + 3]] + [oracle.NONE] * 2
+    # every rule is exact on a perfect matching (each vertex has one edge)
+    mt = synth.from_edge_list(40, [(2 * i, 2 * i + 1) for i in range(20)])
+    for rule in ("hybrid", "afforest", "pure"):
+        lab = oracle.kout_sample(*mt.numpy(), k=1, seed=3, rule=rule)
+        assert np.array_equal(lab, np.repeat(np.arange(0, 40, 2), 2))
+
+
+def test_kout_pure_picks_are_uniform():
+    """Pure sampling draws every slot uniformly: positions of the picks in
+    the adjacency lists of K_50 (degree 49) pass a chi-square test."""
+    from scipy.stats import chisquare
+    g = synth.cliques([50])
+    off, edg = g.numpy()
+    counts = np.zeros(49)
+    for v in range(50):
+        for j in range(40):
+            w = oracle.kout_pick(off, edg, v, 40, j, 11, "pure")
+            counts[int(np.flatnonzero(edg[off[v]:off[v + 1]] == w)[0])] += 1
+    assert chisquare(counts).pvalue > 1e-3
 
 
 def test_kout_on_matching_is_exact():
