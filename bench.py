@@ -56,8 +56,12 @@ def parse():
     p.add_argument("--incr-qfrac", type=float, default=0.5)
     p.add_argument("--no-incr", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-forest", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--combos", action="store_true", help="also time every sampling x finish combination")
+    p.add_argument("--matrix", action="store_true",
+                   help="time every sampling x finish combination on the 16384x16384 grid (edge drop 0.3) "
+                        "and on Erdos-Renyi n=2^25, average degree 1.2")
     p.add_argument("--batched-graphs", type=int, default=10000)
     p.add_argument("--sel-train", type=int, default=300)
     p.add_argument("--sel-test", type=int, default=100)
@@ -235,13 +239,7 @@ def run_ours(args):
 
     # one checked run: stats + invariants that hold at any size
     lab, st = cc.cc_static(off, edg, so, fo, labels, stats=True)
-    src = torch.repeat_interleave(torch.arange(n, device=dev, dtype=torch.int32), (off[1:] - off[:-1]))
-    ok = bool((lab[src.long()] == lab[edg.long()]).all().item()) if m else True
-    del src
-    ar = torch.arange(n, device=dev, dtype=torch.int32)
-    ok = ok and bool((lab <= ar).all().item()) and bool((lab[lab.long()] == lab).all().item())
-    ncomp = int((lab == ar).sum().item())
-    del ar
+    ok, ncomp = check_labels(off, edg, lab)
     torch.cuda.empty_cache()
 
     for _ in range(args.warmup):
@@ -304,6 +302,25 @@ def run_ours(args):
                         "csr_gbs": round((off_bytes * (n + 1) + 4 * m) / (pms * 1e-3) / 1e9, 1)}
     del xs, pout
 
+    # spanning forest with the same sampling and finish (the edges that
+    # hooked roots are recorded as they are linked)
+    forest = None
+    if not args.no_forest:
+        fbuf = torch.empty(2 * n, dtype=torch.int32, device=dev)
+        pairs, _ = cc.cc_spanning_forest(off, edg, so, fo, forest_out=fbuf)
+        fcount = pairs.shape[0]
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record()
+        for _ in range(3):
+            cc.cc_spanning_forest(off, edg, so, fo, forest_out=fbuf)
+        f1.record()
+        torch.cuda.synchronize()
+        fms = f0.elapsed_time(f1) / 3
+        forest = {"ms": round(fms, 4), "gedges_s": round(m / (fms * 1e-3) / 1e9, 2), "edges": fcount,
+                  "size_ok": fcount == n - ncomp, "overhead_vs_cc": round(fms / ms - 1.0, 4),
+                  "note": "synchronous call (returns the count), timed on the host thread's stream"}
+        del fbuf, pairs
+
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "Gedges/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
@@ -315,6 +332,7 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}"},
         "hbm_roof_frac": round(hbm_frac, 4), "hbm_roof_peak_gbs": peak,
         "roofline": roof, "kernels": kernels, "gpu_launches": launches, "edge_primitives": probes,
+        "spanning_forest": forest,
         "check": {"invariants_ok": ok, "components": ncomp, "lmax": st["lmax"], "edges_finish": st["edges_finish"],
                   "n_nonisolated": n_nz},
         "gen_s": round(gen_s, 2),
@@ -349,6 +367,9 @@ def run_ours(args):
     if args.combos:
         out["combos"] = bench_combos(args, cc, off, edg, labels, lab, m)
 
+    if args.matrix:
+        out["matrix"] = bench_matrix(args, cc, synth, dev)
+
     if not args.no_batched:
         out["batched"] = bench_batched(args, cc, synth, dev)
 
@@ -381,6 +402,62 @@ def bench_combos(args, cc, off, edg, labels, ref, m):
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / reps
             res[f"{s}+{f}"] = {"ms": round(ms, 3), "gedges_s": round(m / (ms * 1e-3) / 1e9, 2), "exact": same}
+    return res
+
+
+def check_labels(off, edg, lab):
+    """Properties of a min-id labelling that hold at any size: both ends of
+    every edge share a label, label[v] <= v, labels are fixed points.
+    Returns (ok, number of components)."""
+    import torch
+    n = lab.numel()
+    dev = lab.device
+    src = torch.repeat_interleave(torch.arange(n, device=dev, dtype=torch.int32), off[1:] - off[:-1])
+    ok = bool((lab[src.long()] == lab[edg.long()]).all().item()) if edg.numel() else True
+    del src
+    ar = torch.arange(n, device=dev, dtype=torch.int32)
+    ok = ok and bool((lab <= ar).all().item()) and bool((lab[lab.long()] == lab).all().item())
+    return ok, int((lab == ar).sum().item())
+
+
+def bench_matrix(args, cc, synth, dev):
+    """Every sampling x finish combination on the high-diameter grid and on
+    the near-percolation Erdos-Renyi graph: ms per call (one untimed call,
+    then the mean of `reps`), Gedges/s, and whether the labels equal the
+    no-sampling union-find labels (which are checked by the invariants)."""
+    import torch
+    res = {}
+    for name, make in (("grid16384x16384_p0.3", lambda: synth.grid2d(16384, 16384, 0.3, seed=1, device=dev)),
+                       ("er_n2^25_d1.2", lambda: synth.erdos_renyi(1 << 25, 1.2, seed=1, device=dev))):
+        t0 = time.time()
+        g = make()
+        gen_s = time.time() - t0
+        torch.cuda.empty_cache()
+        off, edg, n, m = g.offsets, g.edges, g.n, g.m
+        labels = torch.empty(n, dtype=torch.int32, device=dev)
+        base = cc.cc_static(off, edg, cc.sample_opt("none"), cc.finish_opt("uf_rem_cas"), labels).clone()
+        ok, ncomp = check_labels(off, edg, base)
+        rows = {}
+        for s in ("none", "kout", "bfs", "ldd"):
+            for f in ("uf_rem_cas", "uf_async", "sv", "lt_prf"):
+                so = cc.sample_opt(s)
+                fo = cc.finish_opt(f, "naive" if f != "uf_async" else "split")
+                cc.cc_static(off, edg, so, fo, labels)
+                same = bool(torch.equal(labels, base))
+                reps = 2
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(reps):
+                    cc.cc_static(off, edg, so, fo, labels)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / reps
+                rows[f"{s}+{f}"] = {"ms": round(ms, 3), "gedges_s": round(m / (ms * 1e-3) / 1e9, 2), "exact": same}
+        best = min(rows, key=lambda k: rows[k]["ms"])
+        res[name] = {"n": n, "m": m, "offsets": "u64", "components": ncomp, "invariants_ok": ok,
+                     "gen_s": round(gen_s, 1), "best": best, "combos": rows}
+        del g, off, edg, labels, base
+        torch.cuda.empty_cache()
     return res
 
 

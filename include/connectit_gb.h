@@ -67,29 +67,46 @@ enum { CC_SAMPLE_NONE = 0, CC_SAMPLE_KOUT = 1, CC_SAMPLE_BFS = 2, CC_SAMPLE_LDD 
 /* Finish methods (Section 3.3): UF-Rem-CAS (Algorithm 14), UF-Async
  * (Algorithm 10), Shiloach-Vishkin (Algorithm 15), Liu-Tarjan PRF
  * (ParentConnect + RootUpdate + FullShortcut, Appendix D). */
-enum { CC_FINISH_UF_REM_CAS = 0, CC_FINISH_UF_ASYNC = 1, CC_FINISH_SV = 2, CC_FINISH_LT_PRF = 3 };
+enum { CC_FINISH_UF_REM_CAS = 0, CC_FINISH_UF_ASYNC = 1, CC_FINISH_SV = 2, CC_FINISH_LT_PRF = 3,
+       CC_FINISH_UF_HOOKS = 4, CC_FINISH_UF_EARLY = 5, CC_FINISH_LIU_TARJAN = 6, CC_FINISH_STERGIOU = 7,
+       CC_FINISH_LABEL_PROP = 8 };
+/* Liu-Tarjan rules (CC_FINISH_LIU_TARJAN, field lt_rules; Section 3.3 and
+ * the appendix's list of sixteen variants): connect = CONNECT, PARENT or
+ * EXTENDED, plus ROOTUP (RootUpdate), FULL (FullShortcut instead of one
+ * Shortcut step) and ALTER.  Valid: CONNECT with ALTER (CUSA, CRSA, CUFA,
+ * CRFA); PARENT with anything (PUSA, PRSA, PUS, PRS, PUFA, PRFA, PUF, PRF);
+ * EXTENDED without ROOTUP (EUSA, EUS, EUFA, EUF).  CC_FINISH_LT_PRF is the
+ * root-based PRF with its own kernels. */
+enum { CC_LT_CONNECT = 0, CC_LT_PARENT = 1, CC_LT_EXTENDED = 2, CC_LT_ROOTUP = 4, CC_LT_FULL = 8,
+       CC_LT_ALTER = 16 };
 /* Find options (Algorithm 8): no compaction, atomic path splitting, atomic
- * path halving.  For UF-Rem-CAS this is the Compress option of Algorithm 14. */
-enum { CC_FIND_NAIVE = 0, CC_FIND_SPLIT = 1, CC_FIND_HALVE = 2 };
-/* Splice options of Rem's algorithm (Algorithm 9). */
-enum { CC_SPLICE_SPLIT_ONE = 0, CC_SPLICE_HALVE_ONE = 1 };
+ * path halving, full compression of the find path.  For UF-Rem-CAS this is
+ * the Compress option of Algorithm 14, which excludes FindCompress. */
+enum { CC_FIND_NAIVE = 0, CC_FIND_SPLIT = 1, CC_FIND_HALVE = 2, CC_FIND_COMPRESS = 3 };
+/* Splice options of Rem's algorithm (Algorithm 9).  SpliceAtomic is correct
+ * phase-concurrently (every call here separates unions from finds) and is
+ * not root-based, so cc_spanning_forest rejects it. */
+enum { CC_SPLICE_SPLIT_ONE = 0, CC_SPLICE_HALVE_ONE = 1, CC_SPLICE_ATOMIC = 2 };
+/* k-out selection rules (Appendix C.4): hybrid, the first edge and k - 1
+ * uniform picks; afforest, the first k edges; pure, k uniform picks. */
+enum { CC_KOUT_HYBRID = 0, CC_KOUT_AFFOREST = 1, CC_KOUT_PURE = 2 };
 
 typedef struct cc_sample_opt {
     int32_t kind;          /* CC_SAMPLE_* */
-    uint32_t k;            /* k-out: edges per vertex, the first plus k-1 uniform picks (>= 1; 2) */
+    uint32_t k;            /* k-out: edges per vertex (1..64; 2) */
     uint32_t bfs_tries;    /* BFS: number of tries c (>= 1; 3) */
     float ldd_beta;        /* LDD: beta in (0, 64] (0.2) */
     uint64_t seed;         /* seed of every random draw (k-out picks, BFS sources, freq sample) */
     uint32_t freq_samples; /* IdentifyFrequent: 0 counts all n labels; S in [1, 4096] counts S
                               seeded sample positions (an estimate; changes work, not labels) */
-    uint32_t reserved;     /* must be 0 */
+    uint32_t kout_rule;    /* k-out: CC_KOUT_* (CC_KOUT_HYBRID) */
 } cc_sample_opt;
 
 typedef struct cc_finish_opt {
     int32_t kind;          /* CC_FINISH_* */
     int32_t find;          /* CC_FIND_* (union-find finishes) */
     int32_t splice;        /* CC_SPLICE_* (UF-Rem-CAS) */
-    int32_t reserved;      /* must be 0 */
+    int32_t lt_rules;      /* CC_LT_* bits (CC_FINISH_LIU_TARJAN); 0 for every other kind */
 } cc_finish_opt;
 
 /* Counters of one cc_static_ex call. */
@@ -119,6 +136,30 @@ cc_status cc_static(const void *offsets, int offsets_u64, const uint32_t *edges,
 cc_status cc_static_ex(const void *offsets, int offsets_u64, const uint32_t *edges, uint32_t n,
                        uint64_t m, const cc_sample_opt *sample, const cc_finish_opt *finish,
                        uint32_t *labels_out, cc_stats *stats, void *stream);
+
+/* Spanning forest (Section 3.5 "Spanning Forest" and the spanning-forest
+ * algorithm of its appendix): the same sampling / IdentifyFrequent / finish
+ * pipeline, where the sampling emits its tree edges (k-out: each edge that
+ * hooked a root; BFS: the tree edge at each child; LDD: the searches' tree
+ * edges) and the root-based finish stores each edge that hooked a root; the
+ * non-empty slots are then filtered into forest_out.
+ * forest_out: device uint32[2*n] (room for n pairs), receives *count_out
+ *   pairs (u, v), each an edge of G, in no particular order; the pairs form
+ *   a forest whose trees span exactly the components of G, so
+ *   *count_out = n - #components.  Which spanning forest is returned depends
+ *   on thread timing; its size and the components it spans do not.
+ * count_out: host uint64, written before the call returns (it synchronises
+ *   the stream).
+ * labels_out: optional device uint32[n], the canonical labels (NULL: not
+ *   returned; scratch is used instead).
+ * Finishes: the root-based union-find finishes (UF-Rem-CAS without
+ * SpliceAtomic, UF-Async, UF-Hooks, UF-Early).  SV and LT-PRF return
+ * CC_ERR_UNSUPPORTED (their writeMin hooks do not identify the winning edge
+ * without another pass), as does SpliceAtomic (not root-based).  Returns
+ * the device error status. */
+cc_status cc_spanning_forest(const void *offsets, int offsets_u64, const uint32_t *edges, uint32_t n,
+                             uint64_t m, const cc_sample_opt *sample, const cc_finish_opt *finish,
+                             uint32_t *forest_out, uint64_t *count_out, uint32_t *labels_out, void *stream);
 
 /* cc_static on HOST buffers (offsets, edges, labels_out in host memory,
  * ideally pinned): copies the graph to library-allocated device memory,

@@ -23,7 +23,10 @@ _lib = None
 NONE = 0xFFFFFFFF
 SAMPLE = {"none": 0, "kout": 1, "bfs": 2, "ldd": 3}
 KOUT_RULE = {"hybrid": 0, "afforest": 1, "pure": 2}
-FINISH = {"uf_rem_cas": 0, "uf_async": 1, "sv": 2, "lt_prf": 3}
+# every union-find option of Algorithm 7's meta-algorithm (Union = Async,
+# Hooks, Early or Rem-CAS, any find / splice) reaches the same sequential
+# union-find result, so they share the oracle's one union-find finish
+FINISH = {"uf_rem_cas": 0, "uf_async": 1, "sv": 2, "lt_prf": 3, "uf_hooks": 0, "uf_early": 0}
 
 
 def build(force: bool = False) -> str:
@@ -82,6 +85,12 @@ def lib():
             L.oracle_incr_labels.argtypes = [c.c_uint32, u32p, u32p]
             L.oracle_spanning_forest.restype = c.c_uint64
             L.oracle_spanning_forest.argtypes = [c.c_uint32, u64p, u32p, u32p]
+            fp = ctypes.POINTER(ctypes.c_float)
+            dp = ctypes.POINTER(ctypes.c_double)
+            L.oracle_msf_kruskal.restype = c.c_uint64
+            L.oracle_msf_kruskal.argtypes = [c.c_uint32, u64p, u32p, fp, u32p, dp]
+            L.oracle_amsf.restype = c.c_uint64
+            L.oracle_amsf.argtypes = [c.c_uint32, u64p, u32p, fp, c.c_double, u32p, dp]
             L.oracle_check_forest.restype = c.c_int
             L.oracle_check_forest.argtypes = [c.c_uint32, u64p, u32p, u32p, c.c_uint64, u32p]
             _lib = L
@@ -190,7 +199,7 @@ def finish(offsets, edges, labels, lmax: int, kind: str = "uf_rem_cas"):
     lab = np.array(_as_np(labels), dtype=np.uint32, copy=True)
     lp = lab.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
     L = lib()
-    if kind in ("uf_rem_cas", "uf_async"):
+    if kind in ("uf_rem_cas", "uf_async", "uf_hooks", "uf_early"):
         st = L.oracle_finish_uf(n, Ip, Ap, lp, lmax)
     elif kind == "sv":
         st = L.oracle_finish_sv(n, Ip, Ap, lp, lmax)
@@ -263,3 +272,23 @@ def check_forest(offsets, edges, pairs, labels=None) -> int:
     L, Lp = _u32(_as_np(labels))
     pr, pp = _u32(_as_np(pairs).reshape(-1))
     return int(lib().oracle_check_forest(n, Ip, Ap, pp, pr.size // 2, Lp))
+
+
+def _forest_call(fn, offsets, edges, weights, *extra):
+    n, (I, Ip), (A, Ap) = _graph(_as_np(offsets), _as_np(edges))
+    W = np.ascontiguousarray(np.asarray(_as_np(weights), dtype=np.float32))
+    out = np.empty(2 * max(n - 1, 1), np.uint32)
+    wt = ctypes.c_double(0.0)
+    cnt = fn(n, Ip, Ap, W.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), *extra,
+             out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), ctypes.byref(wt))
+    return out[: 2 * cnt].reshape(-1, 2), wt.value
+
+
+def msf_kruskal(offsets, edges, weights):
+    """Exact minimum spanning forest: (pairs uint32[count, 2], total weight)."""
+    return _forest_call(lib().oracle_msf_kruskal, offsets, edges, weights)
+
+
+def amsf(offsets, edges, weights, eps: float):
+    """Approximate MSF by weight buckets of ratio 1 + eps: (pairs, weight)."""
+    return _forest_call(lib().oracle_amsf, offsets, edges, weights, ctypes.c_double(eps))

@@ -37,6 +37,12 @@
  *   oracle_check_forest   validity of any claimed spanning forest: every
  *                         pair is an edge of G, the pairs are acyclic, and
  *                         they connect exactly the components of G
+ *   oracle_msf_kruskal    exact minimum spanning forest (plain definition,
+ *                         by Kruskal's algorithm)
+ *   oracle_amsf           approximate minimum spanning forest, Section 5.1:
+ *                         weight buckets [Wmin(1+eps)^i, Wmin(1+eps)^(i+1)),
+ *                         smallest first, a spanning forest of each bucket
+ *                         over the labelling of the buckets before it
  *
  * Random draws: counter-based, the ctr-th output of a SplitMix64 sequence
  * (Steele, Lea, Flood, "Fast splittable pseudorandom number generators",
@@ -497,4 +503,114 @@ int oracle_check_forest(uint32_t n, const uint64_t *I, const uint32_t *A, const 
     }
     free(P);
     return bad;
+}
+
+/* ---- minimum spanning forests ---------------------------------------- */
+/* Undirected edges (u < v) of a symmetric weighted CSR, as indices into A. */
+static uint64_t upper_edges(uint32_t n, const uint64_t *I, const uint32_t *A, uint64_t *idx, uint32_t *src) {
+    uint64_t k = 0;
+    for (uint32_t u = 0; u < n; ++u)
+        for (uint64_t e = I[u]; e < I[u + 1]; ++e)
+            if (A[e] > u) { idx[k] = e; src[k] = u; ++k; }
+    return k;
+}
+
+static const float *g_w;   /* weights seen by the comparator */
+static int by_weight(const void *a, const void *b) {
+    const uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    if (g_w[x] < g_w[y]) return -1;
+    if (g_w[x] > g_w[y]) return 1;
+    return x < y ? -1 : (x > y);
+}
+
+/* Exact MSF: Kruskal over the undirected edges sorted by weight (ties by
+ * CSR position).  Writes the forest pairs, returns their number, and the
+ * total weight (summed in double) in *weight. */
+uint64_t oracle_msf_kruskal(uint32_t n, const uint64_t *I, const uint32_t *A, const float *W, uint32_t *out,
+                            double *weight) {
+    uint64_t m = I[n];
+    uint64_t *idx = (uint64_t *)malloc((m ? m : 1) * sizeof(uint64_t));
+    uint32_t *src = (uint32_t *)malloc((m ? m : 1) * sizeof(uint32_t));
+    uint32_t *owner = (uint32_t *)malloc((m ? m : 1) * sizeof(uint32_t));
+    uint64_t k = upper_edges(n, I, A, idx, src);
+    for (uint64_t i = 0; i < k; ++i) owner[idx[i]] = src[i];
+    g_w = W;
+    qsort(idx, k, sizeof(uint64_t), by_weight);
+    uint32_t *P = (uint32_t *)malloc((size_t)(n ? n : 1) * sizeof(uint32_t));
+    for (uint32_t v = 0; v < n; ++v) P[v] = v;
+    uint64_t cnt = 0;
+    double total = 0.0;
+    for (uint64_t i = 0; i < k; ++i) {
+        uint64_t e = idx[i];
+        uint32_t u = owner[e], v = A[e];
+        if (uf_union(P, u, v)) {
+            out[2 * cnt] = u;
+            out[2 * cnt + 1] = v;
+            ++cnt;
+            total += W[e];
+        }
+    }
+    free(P);
+    free(owner);
+    free(src);
+    free(idx);
+    *weight = total;
+    return cnt;
+}
+
+/* Bucket of weight w: floor(log(w / Wmin) / log(1 + eps)), clamped at 0. */
+static uint64_t weight_bucket(float w, float wmin, double eps) {
+    double b = floor(log((double)w / (double)wmin) / log1p(eps));
+    return b < 0.0 ? 0u : (uint64_t)b;
+}
+
+/* Approximate MSF (the folklore bucketed algorithm of Section 5.1): buckets
+ * in increasing weight order; within a bucket every edge whose endpoints
+ * are not yet connected joins the forest (a spanning forest of the bucket's
+ * edges over the labelling so far).  Sequential, no skipping.  Empty
+ * buckets do nothing, so the edges are visited sorted by (bucket, CSR
+ * position): the bucket order, and vertex order inside a bucket. */
+static const uint64_t *g_bucket;
+static int by_bucket(const void *a, const void *b) {
+    const uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    if (g_bucket[x] != g_bucket[y]) return g_bucket[x] < g_bucket[y] ? -1 : 1;
+    return x < y ? -1 : (x > y);
+}
+
+uint64_t oracle_amsf(uint32_t n, const uint64_t *I, const uint32_t *A, const float *W, double eps, uint32_t *out,
+                     double *weight) {
+    uint64_t m = I[n];
+    float wmin = 0.0f;
+    for (uint64_t e = 0; e < m; ++e)
+        if (e == 0 || W[e] < wmin) wmin = W[e];
+    uint64_t *bucket = (uint64_t *)malloc((m ? m : 1) * sizeof(uint64_t));
+    uint32_t *owner = (uint32_t *)malloc((m ? m : 1) * sizeof(uint32_t));
+    uint64_t *order = (uint64_t *)malloc((m ? m : 1) * sizeof(uint64_t));
+    for (uint32_t u = 0; u < n; ++u)
+        for (uint64_t e = I[u]; e < I[u + 1]; ++e) owner[e] = u;
+    for (uint64_t e = 0; e < m; ++e) {
+        bucket[e] = weight_bucket(W[e], wmin, eps);
+        order[e] = e;
+    }
+    g_bucket = bucket;
+    qsort(order, m, sizeof(uint64_t), by_bucket);
+    uint32_t *P = (uint32_t *)malloc((size_t)(n ? n : 1) * sizeof(uint32_t));
+    for (uint32_t v = 0; v < n; ++v) P[v] = v;
+    uint64_t cnt = 0;
+    double total = 0.0;
+    for (uint64_t i = 0; i < m; ++i) {
+        uint64_t e = order[i];
+        if (uf_union(P, owner[e], A[e])) {
+            out[2 * cnt] = owner[e];
+            out[2 * cnt + 1] = A[e];
+            ++cnt;
+            total += W[e];
+        }
+    }
+    free(P);
+    free(order);
+    free(owner);
+    free(bucket);
+    *weight = total;
+    return cnt;
 }

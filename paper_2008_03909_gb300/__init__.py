@@ -25,9 +25,17 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libconnectit_gb.so")
 
 SAMPLE = {"none": 0, "kout": 1, "bfs": 2, "ldd": 3}
-FINISH = {"uf_rem_cas": 0, "uf_async": 1, "sv": 2, "lt_prf": 3}
-FIND = {"naive": 0, "split": 1, "halve": 2}
-SPLICE = {"split_one": 0, "halve_one": 1}
+FINISH = {"uf_rem_cas": 0, "uf_async": 1, "sv": 2, "lt_prf": 3, "uf_hooks": 4, "uf_early": 5, "liu_tarjan": 6,
+          "stergiou": 7, "label_prop": 8}
+# the sixteen Liu-Tarjan variants: connect (C/P/E), update (U/R), shortcut
+# (S one step / F full), A = alter
+LT_VARIANTS = {name: {"C": 0, "P": 1, "E": 2}[name[0]] | (4 if name[1] == "R" else 0) |
+               (8 if name[2] == "F" else 0) | (16 if name.endswith("A") else 0)
+               for name in ("CUSA", "CRSA", "PUSA", "PRSA", "PUS", "PRS", "EUSA", "EUS",
+                            "CUFA", "CRFA", "PUFA", "PRFA", "PUF", "PRF", "EUFA", "EUF")}
+FIND = {"naive": 0, "split": 1, "halve": 2, "compress": 3}
+SPLICE = {"split_one": 0, "halve_one": 1, "atomic": 2}
+KOUT_RULE = {"hybrid": 0, "afforest": 1, "pure": 2}
 NONE = 0xFFFFFFFF
 
 STATUS = {0: "CC_OK", 1: "CC_ERR_INVALID", 2: "CC_ERR_OOM", 3: "CC_ERR_CUDA", 4: "CC_ERR_NONCONVERGED",
@@ -43,12 +51,12 @@ class CCError(RuntimeError):
 class SampleOpt(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("k", ctypes.c_uint32), ("bfs_tries", ctypes.c_uint32),
                 ("ldd_beta", ctypes.c_float), ("seed", ctypes.c_uint64), ("freq_samples", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("kout_rule", ctypes.c_uint32)]
 
 
 class FinishOpt(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("find", ctypes.c_int32), ("splice", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("lt_rules", ctypes.c_int32)]
 
 
 class KernelTime(ctypes.Structure):
@@ -80,6 +88,10 @@ _SIGS = {
     "cc_static_ex": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint32,
                                     ctypes.c_uint64, ctypes.POINTER(SampleOpt), ctypes.POINTER(FinishOpt),
                                     ctypes.c_void_p, ctypes.POINTER(Stats), ctypes.c_void_p]),
+    "cc_spanning_forest": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint32,
+                                          ctypes.c_uint64, ctypes.POINTER(SampleOpt), ctypes.POINTER(FinishOpt),
+                                          ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64), ctypes.c_void_p,
+                                          ctypes.c_void_p]),
     "cc_static_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint32,
                                       ctypes.c_uint64, ctypes.POINTER(SampleOpt), ctypes.POINTER(FinishOpt),
                                       ctypes.c_void_p, ctypes.c_void_p]),
@@ -187,13 +199,17 @@ def _dev(t: torch.Tensor, dtypes, what: str) -> torch.Tensor:
     return t
 
 
-def sample_opt(kind="kout", k=2, bfs_tries=3, ldd_beta=0.2, seed=1, freq_samples=0) -> SampleOpt:
-    return SampleOpt(SAMPLE[kind] if isinstance(kind, str) else kind, k, bfs_tries, ldd_beta, seed, freq_samples, 0)
+def sample_opt(kind="kout", k=2, bfs_tries=3, ldd_beta=0.2, seed=1, freq_samples=0, kout_rule="hybrid") -> SampleOpt:
+    return SampleOpt(SAMPLE[kind] if isinstance(kind, str) else kind, k, bfs_tries, ldd_beta, seed, freq_samples,
+                     KOUT_RULE[kout_rule] if isinstance(kout_rule, str) else kout_rule)
 
 
-def finish_opt(kind="uf_rem_cas", find="naive", splice="split_one") -> FinishOpt:
+def finish_opt(kind="uf_rem_cas", find="naive", splice="split_one", lt_rules=0) -> FinishOpt:
+    """kind may also name a Liu-Tarjan variant ("PRS", "CUFA", ...)."""
+    if isinstance(kind, str) and kind in LT_VARIANTS:
+        kind, lt_rules = "liu_tarjan", LT_VARIANTS[kind]
     return FinishOpt(FINISH[kind] if isinstance(kind, str) else kind, FIND[find] if isinstance(find, str) else find,
-                     SPLICE[splice] if isinstance(splice, str) else splice, 0)
+                     SPLICE[splice] if isinstance(splice, str) else splice, lt_rules)
 
 
 def _graph_args(offsets: torch.Tensor, edges: torch.Tensor):
@@ -225,6 +241,29 @@ def cc_static(offsets, edges, sample: SampleOpt | None = None, finish: FinishOpt
     _check(L.cc_static(Ip, u64, Ap, n, m, ctypes.byref(so), ctypes.byref(fo), ctypes.c_void_p(labels_out.data_ptr()),
                        _stream(stream)), "cc_static")
     return labels_out
+
+
+def cc_spanning_forest(offsets, edges, sample: SampleOpt | None = None, finish: FinishOpt | None = None,
+                       forest_out: torch.Tensor | None = None, labels_out: torch.Tensor | None = None,
+                       stream=None):
+    """Spanning forest: (pairs int32[count, 2] view of forest_out, labels or
+    None).  forest_out: int32[2 * n] on the device (allocated if None)."""
+    Ip, u64, Ap, n, m = _graph_args(offsets, edges)
+    if forest_out is None:
+        forest_out = torch.empty(2 * max(n, 1), dtype=torch.int32, device=offsets.device)
+    _dev(forest_out, (torch.int32,), "forest_out")
+    if forest_out.numel() < 2 * n:
+        raise ValueError("forest_out needs room for 2 * n values")
+    if labels_out is not None:
+        _dev(labels_out, (torch.int32,), "labels_out")
+    so = sample if sample is not None else sample_opt()
+    fo = finish if finish is not None else finish_opt()
+    cnt = ctypes.c_uint64(0)
+    _check(lib().cc_spanning_forest(Ip, u64, Ap, n, m, ctypes.byref(so), ctypes.byref(fo),
+                                    ctypes.c_void_p(forest_out.data_ptr()), ctypes.byref(cnt),
+                                    ctypes.c_void_p(labels_out.data_ptr() if labels_out is not None else 0),
+                                    _stream(stream)), "cc_spanning_forest")
+    return forest_out[: 2 * cnt.value].view(-1, 2), labels_out
 
 
 def cc_static_host(offsets: torch.Tensor, edges: torch.Tensor, sample=None, finish=None,

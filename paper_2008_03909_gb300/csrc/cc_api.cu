@@ -78,15 +78,25 @@ cc_status check_sample(const cc_sample_opt &s) {
     if (s.kind == CC_SAMPLE_BFS && (s.bfs_tries < 1 || s.bfs_tries > 1024)) return CC_ERR_INVALID;
     if (s.kind == CC_SAMPLE_LDD && !(s.ldd_beta > 0.0f && s.ldd_beta <= 64.0f)) return CC_ERR_INVALID;
     if (s.freq_samples > 4096) return CC_ERR_INVALID;
-    if (s.reserved != 0) return CC_ERR_INVALID;
+    if (s.kout_rule > CC_KOUT_PURE) return CC_ERR_INVALID;
     return CC_OK;
 }
 
 cc_status check_finish(const cc_finish_opt &f) {
-    if (f.kind < CC_FINISH_UF_REM_CAS || f.kind > CC_FINISH_LT_PRF) return CC_ERR_INVALID;
-    if (f.find < CC_FIND_NAIVE || f.find > CC_FIND_HALVE) return CC_ERR_INVALID;
-    if (f.splice < CC_SPLICE_SPLIT_ONE || f.splice > CC_SPLICE_HALVE_ONE) return CC_ERR_INVALID;
-    if (f.reserved != 0) return CC_ERR_INVALID;
+    if (f.kind < CC_FINISH_UF_REM_CAS || f.kind > CC_FINISH_LABEL_PROP) return CC_ERR_INVALID;
+    if (f.find < CC_FIND_NAIVE || f.find > CC_FIND_COMPRESS) return CC_ERR_INVALID;
+    if (f.splice < CC_SPLICE_SPLIT_ONE || f.splice > CC_SPLICE_ATOMIC) return CC_ERR_INVALID;
+    // Rem's Compress option is FindNaive / Split / Halve (FindCompress with
+    // SpliceAtomic is incorrect: the counter-example in the appendix on
+    // Rem's algorithm)
+    if (f.kind == CC_FINISH_UF_REM_CAS && f.find == CC_FIND_COMPRESS) return CC_ERR_INVALID;
+    if (f.kind != CC_FINISH_LIU_TARJAN) return f.lt_rules == 0 ? CC_OK : CC_ERR_INVALID;
+    // the sixteen Liu-Tarjan variants
+    const int conn = f.lt_rules & 3;
+    if (f.lt_rules & ~31) return CC_ERR_INVALID;
+    if (conn == 3) return CC_ERR_INVALID;
+    if (conn == CC_LT_CONNECT && !(f.lt_rules & CC_LT_ALTER)) return CC_ERR_INVALID;   // Connect needs Alter
+    if (conn == CC_LT_EXTENDED && (f.lt_rules & CC_LT_ROOTUP)) return CC_ERR_INVALID;
     return CC_OK;
 }
 
@@ -151,13 +161,13 @@ void cc_default_opts(cc_sample_opt *sample, cc_finish_opt *finish) {
         sample->ldd_beta = 0.2f;
         sample->seed = 1;
         sample->freq_samples = 0;
-        sample->reserved = 0;
+        sample->kout_rule = CC_KOUT_HYBRID;
     }
     if (finish) {
         finish->kind = CC_FINISH_UF_REM_CAS;
         finish->find = CC_FIND_NAIVE;
         finish->splice = CC_SPLICE_SPLIT_ONE;
-        finish->reserved = 0;
+        finish->lt_rules = 0;
     }
 }
 

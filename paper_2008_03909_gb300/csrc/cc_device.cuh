@@ -15,8 +15,8 @@ constexpr uint32_t ERR_BAD_OFFSETS = 2u;
 constexpr uint32_t ERR_NONCONVERGED = 4u;
 constexpr uint64_t OP_TIME_LIMIT_NS = 4000000000ull;  // one find/union may run 4 s at most
 
-enum { FIND_NAIVE = 0, FIND_SPLIT = 1, FIND_HALVE = 2 };
-enum { SPLICE_SPLIT_ONE = 0, SPLICE_HALVE_ONE = 1 };
+enum { FIND_NAIVE = 0, FIND_SPLIT = 1, FIND_HALVE = 2, FIND_COMPRESS = 3 };
+enum { SPLICE_SPLIT_ONE = 0, SPLICE_HALVE_ONE = 1, SPLICE_ATOMIC = 2 };
 
 // Degree binning: vertices of degree <= LIGHT_MAX are handled by one thread;
 // the edges of heavier vertices are cut into chunks of <= CHUNK edges, each
@@ -26,8 +26,10 @@ constexpr uint32_t CHUNK = 2048;
 
 // Per-launch context passed by value.
 struct Dev {
-    uint32_t *err;   // per-device sticky error word (CC_DEVERR_* bits)
-    uint64_t cap;    // iteration cap of one device loop
+    uint32_t *err;             // per-device sticky error word (CC_DEVERR_* bits)
+    uint64_t cap;              // iteration cap of one device loop
+    uint2 *forest = nullptr;   // spanning forest: edges[r] = the edge that hooked root r
+    uint32_t *hooks = nullptr; // UF-Hooks: the hooks array H (NONE = free)
 };
 
 // ---------------------------------------------------------------- loads
@@ -71,6 +73,63 @@ struct Guard {
     }
 };
 
+// ---------------------------------------------------------------- grid barrier
+__device__ __forceinline__ uint32_t ld_acq(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_rel(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_rel64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Barrier over every block of a cooperative launch (all blocks are
+// co-resident).  A block reads the generation, then arrives; the last
+// arrival resets the count and publishes the next generation with a
+// release store.  The wait is bounded by OP_TIME_LIMIT_NS: a block that
+// gives up records ERR_NONCONVERGED and sets `abort`, and from then on
+// every block's grid_sync returns false, so all blocks leave the kernel.
+struct GridBar {
+    uint32_t count;
+    uint32_t gen;
+    uint32_t abort;
+    uint32_t pad;
+};
+
+__device__ __forceinline__ bool grid_sync(GridBar *b, const Dev &d) {
+    __shared__ uint32_t ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t g = ld_acq(&b->gen);
+        __threadfence();
+        bool ok = true;
+        if (atomicAdd(&b->count, 1u) + 1 == gridDim.x) {
+            atomicExch(&b->count, 0u);
+            st_rel(&b->gen, g + 1);
+        } else {
+            const uint64_t t0 = gtimer();
+            while (ld_acq(&b->gen) == g) {
+                if (ld_rel(&b->abort)) { ok = false; break; }
+                if (gtimer() - t0 > OP_TIME_LIMIT_NS) {
+                    atomicOr(d.err, ERR_NONCONVERGED);
+                    atomicExch(&b->abort, 1u);
+                    ok = false;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        ok_s = ok && ld_rel(&b->abort) == 0;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
 // ---------------------------------------------------------------- draws
 // Counter-based draws: the ctr-th output of a SplitMix64 sequence started at
 // state s (Steele, Lea, Flood, OOPSLA 2014), mix64(s + (ctr+1) * gamma).
@@ -84,10 +143,28 @@ constexpr uint64_t TAG_KOUT = 0x6B6F7574ull;
 constexpr uint64_t TAG_FREQ = 0x66726571ull;
 constexpr uint64_t TAG_BFS = 0x62667373ull;
 
+// k-out selection rules (Appendix C.4): hybrid takes the first edge and
+// k - 1 uniform picks, afforest the first k edges, pure k uniform picks.
+enum { KOUT_HYBRID = 0, KOUT_AFFOREST = 1, KOUT_PURE = 2 };
+constexpr uint64_t NO_PICK = ~0ull;
+
+// Position of pick j (0 <= j < k) of vertex v in its adjacency list of
+// length deg > 0, or NO_PICK (afforest past the degree).  A uniform pick is
+// floor(hi32(out(seed ^ TAG_KOUT, v*k + j)) * deg / 2^32), with replacement.
+__device__ __forceinline__ uint64_t kout_offset(uint32_t rule, uint64_t seed, uint64_t v, uint32_t k, uint32_t j,
+                                                uint64_t deg) {
+    if (rule == KOUT_AFFOREST) return j < deg ? j : NO_PICK;
+    if (rule == KOUT_HYBRID && j == 0) return 0;
+    return ((draw64(seed ^ TAG_KOUT, v * k + j) >> 32) * deg) >> 32;
+}
+
 // ---------------------------------------------------------------- finds
 // Root of x given px = P[x] (Algorithm 8): FindNaive follows parents;
 // FindAtomicSplit points each visited node at its grandparent and moves to
-// the parent; FindAtomicHalve does the same and moves to the grandparent.
+// the parent; FindAtomicHalve does the same and moves to the grandparent;
+// FindCompress finds the root r, then walks the path again pointing every
+// node whose parent is above r straight at r (plain stores: the nodes are
+// non-roots, which never become roots again, and r is an ancestor of each).
 template <int FIND>
 __device__ __forceinline__ uint32_t find_from(uint32_t *P, uint32_t x, uint32_t px, const Dev &d) {
     Guard g;
@@ -110,7 +187,7 @@ __device__ __forceinline__ uint32_t find_from(uint32_t *P, uint32_t x, uint32_t 
             if (!g.step(d)) break;
         }
         return v;
-    } else {
+    } else if (FIND == FIND_HALVE) {
         uint32_t v = px;
         if (v == x) return x;
         uint32_t w = ld_rel(P + v);
@@ -123,13 +200,32 @@ __device__ __forceinline__ uint32_t find_from(uint32_t *P, uint32_t x, uint32_t 
             if (!g.step(d)) break;
         }
         return v;
+    } else {
+        if (px == x) return x;
+        uint32_t r = px, pr = ld_rel(P + r);
+        while (pr != r) {
+            r = pr;
+            pr = ld_rel(P + r);
+            if (!g.step(d)) return r;
+        }
+        uint32_t j = px;
+        while (j > r) {
+            P[x] = r;
+            x = j;
+            j = ld_rel(P + x);
+            if (!g.step(d)) break;
+        }
+        return r;
     }
 }
 
 // ---------------------------------------------------------------- unions
-// Both engines keep P[x] <= x: a root is only ever linked under a smaller
+// Every engine keeps P[x] <= x: a root is only ever linked under a smaller
 // id, so every root is the minimum of its tree and the final roots are the
-// canonical labels.  pu = P[u] and pv = P[v] are passed in already loaded
+// canonical labels.  All but UF-Rem-CAS with SpliceAtomic are root-based in
+// the sense of the spanning-forest appendix: a link hooks a root exactly
+// once, so when d.forest is set the hooking edge (u, v) is stored at the
+// hooked root's slot.  pu = P[u] and pv = P[v] are passed in already loaded
 // (callers batch those loads); pu == pv means nothing to do.
 
 // UF-Async (Algorithm 10; the CAS is on the larger root's own slot): find
@@ -146,7 +242,10 @@ struct UnionAsync {
         while (ru != rv) {
             if (ru < rv) { uint32_t t = ru; ru = rv; rv = t; }
             uint32_t old = atomicCAS(P + ru, ru, rv);
-            if (old == ru) return true;
+            if (old == ru) {
+                if (d.forest) d.forest[ru] = make_uint2(u, v);
+                return true;
+            }
             ru = find_from<FIND>(P, ru, old, d);
             rv = find_from<FIND>(P, rv, ld_rel(P + rv), d);
             if (!g.step(d)) return false;
@@ -155,12 +254,88 @@ struct UnionAsync {
     }
 };
 
+// UF-Hooks (Algorithm 11; the CAS is read as on H[p_u]): as UF-Async, but
+// the larger root is claimed by a CAS on the hooks array, and the winner
+// then writes P[p_u] with a plain store (nobody else writes a claimed
+// root's slot).  A thread that loses the claim continues from the parent
+// the winner is writing (the hooks entry), instead of polling P[p_u].
+template <int FIND>
+struct UnionHooks {
+    static constexpr int find_kind = FIND;
+    __device__ static __forceinline__ bool unite(uint32_t *P, uint32_t u, uint32_t v, uint32_t pu,
+                                                 uint32_t pv, const Dev &d) {
+        uint32_t ru = find_from<FIND>(P, u, pu, d);
+        uint32_t rv = find_from<FIND>(P, v, pv, d);
+        Guard g;
+        while (ru != rv) {
+            if (ru < rv) { uint32_t t = ru; ru = rv; rv = t; }
+            uint32_t pr = ld_rel(P + ru);
+            if (pr == ru) {
+                const uint32_t h = atomicCAS(d.hooks + ru, NONE, rv);
+                if (h == NONE) {
+                    st_rel(P + ru, rv);
+                    if (d.forest) d.forest[ru] = make_uint2(u, v);
+                    return true;
+                }
+                // claimed by another union whose store may not be visible
+                // yet: continue from the parent it is about to write
+                pr = h;
+            }
+            ru = find_from<FIND>(P, pr, ld_rel(P + pr), d);
+            rv = find_from<FIND>(P, rv, ld_rel(P + rv), d);
+            if (!g.step(d)) return false;
+        }
+        return false;
+    }
+};
+
+// UF-Early (Algorithm 12; the CAS is read as on P[p_u]): walk both sides
+// together; whenever the larger side is a root, try to hook it under the
+// other side's current vertex (smaller, so in another tree); otherwise one
+// path-halving step on the larger side.  Then the optional find from both
+// endpoints compresses their paths.
+template <int FIND>
+struct UnionEarly {
+    static constexpr int find_kind = FIND;
+    __device__ static __forceinline__ bool unite(uint32_t *P, uint32_t u, uint32_t v, uint32_t pu,
+                                                 uint32_t pv, const Dev &d) {
+        uint32_t ru = pu, rv = pv;
+        bool linked = false;
+        Guard g;
+        while (ru != rv) {
+            if (!g.step(d)) return false;
+            if (ru < rv) { uint32_t t = ru; ru = rv; rv = t; }
+            const uint32_t z = ld_rel(P + ru);
+            if (z == ru) {
+                if (atomicCAS(P + ru, ru, rv) == ru) {
+                    if (d.forest) d.forest[ru] = make_uint2(u, v);
+                    linked = true;
+                    break;
+                }
+                continue;   // linked by another thread: no longer a root
+            }
+            const uint32_t w = ld_rel(P + z);
+            if (w != z) atomicCAS(P + ru, z, w);
+            ru = w;
+        }
+        if (FIND != FIND_NAIVE) {
+            find_from<FIND>(P, u, ld_rel(P + u), d);
+            find_from<FIND>(P, v, ld_rel(P + v), d);
+        }
+        return linked;
+    }
+};
+
 // UF-Rem-CAS (Algorithm 14): walk r_u, r_v upward comparing parents; when
 // the side with the larger parent is a root, CAS it under the other side's
 // parent; otherwise take one splice step there (SplitAtomicOne: compact one
 // link and move to the parent; HalveAtomicOne: compact and move to the
-// grandparent, Algorithm 9).  After a successful link the optional Compress
-// (FindAtomicSplit / FindAtomicHalve) runs from both endpoints.
+// grandparent; SpliceAtomic: swing r_u's parent to r_v's smaller parent and
+// move to r_u's old parent, Algorithm 9).  After a successful link the
+// optional Compress (FindAtomicSplit / FindAtomicHalve) runs from both
+// endpoints.  SpliceAtomic moves non-roots between trees, so it is correct
+// only phase-concurrently (unions and finds separated, as every caller
+// here does) and is not root-based.
 template <int SPLICE, int FIND>
 struct UnionRem {
     static constexpr int find_kind = FIND;
@@ -176,6 +351,7 @@ struct UnionRem {
             if (ru == pru) {
                 uint32_t old = atomicCAS(P + ru, ru, prv);
                 if (old == ru) {
+                    if (d.forest) d.forest[ru] = make_uint2(u, v);
                     if (FIND != FIND_NAIVE) {
                         find_from<FIND>(P, u, ld_rel(P + u), d);
                         find_from<FIND>(P, v, ld_rel(P + v), d);
@@ -188,6 +364,10 @@ struct UnionRem {
                 if (pru != w) atomicCAS(P + ru, pru, w);
                 ru = pru;
                 pru = w;
+            } else if (SPLICE == SPLICE_ATOMIC) {
+                atomicCAS(P + ru, pru, prv);
+                ru = pru;
+                pru = ld_rel(P + ru);
             } else {
                 uint32_t w = ld_rel(P + pru);
                 if (pru != w) {
@@ -203,6 +383,51 @@ struct UnionRem {
         return false;
     }
 };
+
+// Calls fn(Engine{}) with the union-find engine the finish options name
+// (kind, find, splice); the min-label finishes (SV, Liu-Tarjan, Stergiou,
+// label propagation) use UF-Rem-CAS for their k-out sampling.  Options are
+// validated before this is reached.
+template <class Fn>
+__host__ auto with_uf_engine(int kind, int find, int splice, Fn &&fn) {
+    switch (kind) {
+        case 1:   // UF-Async
+            switch (find) {
+                case FIND_NAIVE: return fn(UnionAsync<FIND_NAIVE>{});
+                case FIND_SPLIT: return fn(UnionAsync<FIND_SPLIT>{});
+                case FIND_HALVE: return fn(UnionAsync<FIND_HALVE>{});
+                default: return fn(UnionAsync<FIND_COMPRESS>{});
+            }
+        case 4:   // UF-Hooks
+            switch (find) {
+                case FIND_NAIVE: return fn(UnionHooks<FIND_NAIVE>{});
+                case FIND_SPLIT: return fn(UnionHooks<FIND_SPLIT>{});
+                case FIND_HALVE: return fn(UnionHooks<FIND_HALVE>{});
+                default: return fn(UnionHooks<FIND_COMPRESS>{});
+            }
+        case 5:   // UF-Early
+            switch (find) {
+                case FIND_NAIVE: return fn(UnionEarly<FIND_NAIVE>{});
+                case FIND_SPLIT: return fn(UnionEarly<FIND_SPLIT>{});
+                case FIND_HALVE: return fn(UnionEarly<FIND_HALVE>{});
+                default: return fn(UnionEarly<FIND_COMPRESS>{});
+            }
+        default:
+            break;
+    }
+    if (kind != 0) { find = FIND_NAIVE; splice = SPLICE_SPLIT_ONE; }   // k-out under the min-label finishes
+    switch (splice * 3 + find) {
+        case 0: return fn(UnionRem<SPLICE_SPLIT_ONE, FIND_NAIVE>{});
+        case 1: return fn(UnionRem<SPLICE_SPLIT_ONE, FIND_SPLIT>{});
+        case 2: return fn(UnionRem<SPLICE_SPLIT_ONE, FIND_HALVE>{});
+        case 3: return fn(UnionRem<SPLICE_HALVE_ONE, FIND_NAIVE>{});
+        case 4: return fn(UnionRem<SPLICE_HALVE_ONE, FIND_SPLIT>{});
+        case 5: return fn(UnionRem<SPLICE_HALVE_ONE, FIND_HALVE>{});
+        case 6: return fn(UnionRem<SPLICE_ATOMIC, FIND_NAIVE>{});
+        case 7: return fn(UnionRem<SPLICE_ATOMIC, FIND_SPLIT>{});
+        default: return fn(UnionRem<SPLICE_ATOMIC, FIND_HALVE>{});
+    }
+}
 
 // ---------------------------------------------------------------- CSR ranges
 __device__ __forceinline__ void clamp_range(uint64_t s, uint64_t t, uint64_t m, uint64_t &b, uint64_t &e,
@@ -296,9 +521,13 @@ __device__ __forceinline__ uint32_t append_one(uint32_t *counter) {
 // and are run over a vertex's edges in groups of four for memory-level
 // parallelism.  Bad edge ids (>= n) are dropped and flagged here.
 
+// One thread applies f to the edges [b, e) of vertex u (e - b <= LIGHT_MAX),
+// four independent loads at a time.  (Aligned 16-byte group loads were
+// tried here and lost: a group straddles the range ends of low-degree
+// vertices, doubling the functor calls on grids and sparse graphs.)
 template <class F>
-__device__ __forceinline__ void light_edges(uint32_t u, uint64_t b, uint64_t e, const uint32_t *A,
-                                            uint32_t n, F &f, const Dev &d) {
+__device__ __forceinline__ void light_edges(uint32_t u, uint64_t b, uint64_t e, const uint32_t *A, uint32_t n,
+                                            F &f, const Dev &d) {
     for (uint64_t x = b; x < e; x += 4) {
         uint32_t v[4];
         bool ok[4];

@@ -14,6 +14,7 @@ struct cc_incr {
     uint32_t n;
     uint32_t *P;
     cc_finish_opt fo;
+    uint32_t *hooks;   // UF-Hooks: the resident hooks array (all free after the base graph)
 };
 
 namespace {
@@ -81,24 +82,6 @@ __global__ void __launch_bounds__(256, 8) k_incr_labels(const uint32_t *P, uint3
     }
 }
 
-template <class Fn>
-cc_status with_uf_engine(const cc_finish_opt &f, Fn &&fn) {
-    if (f.kind == CC_FINISH_UF_ASYNC) {
-        switch (f.find) {
-            case CC_FIND_NAIVE: return fn(UnionAsync<FIND_NAIVE>{});
-            case CC_FIND_SPLIT: return fn(UnionAsync<FIND_SPLIT>{});
-            default: return fn(UnionAsync<FIND_HALVE>{});
-        }
-    }
-    switch (f.splice * 3 + f.find) {
-        case 0: return fn(UnionRem<SPLICE_SPLIT_ONE, FIND_NAIVE>{});
-        case 1: return fn(UnionRem<SPLICE_SPLIT_ONE, FIND_SPLIT>{});
-        case 2: return fn(UnionRem<SPLICE_SPLIT_ONE, FIND_HALVE>{});
-        case 3: return fn(UnionRem<SPLICE_HALVE_ONE, FIND_NAIVE>{});
-        case 4: return fn(UnionRem<SPLICE_HALVE_ONE, FIND_SPLIT>{});
-        default: return fn(UnionRem<SPLICE_HALVE_ONE, FIND_HALVE>{});
-    }
-}
 
 }  // namespace
 
@@ -121,14 +104,22 @@ cc_status cc_incr_create(const void *offsets, int offsets_u64, const uint32_t *e
     cc_status st = check_sample(so);
     if (st == CC_OK) st = check_finish(fo);
     if (st != CC_OK) return st;
-    if (fo.kind != CC_FINISH_UF_REM_CAS && fo.kind != CC_FINISH_UF_ASYNC) return CC_ERR_UNSUPPORTED;
+    if (fo.kind != CC_FINISH_UF_REM_CAS && fo.kind != CC_FINISH_UF_ASYNC && fo.kind != CC_FINISH_UF_HOOKS &&
+        fo.kind != CC_FINISH_UF_EARLY)
+        return CC_ERR_UNSUPPORTED;
     const DeviceInfo *di = device_info();
     if (!di) return CC_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cc_incr *h = new cc_incr{di->device, n, nullptr, fo};
+    cc_incr *h = new cc_incr{di->device, n, nullptr, fo, nullptr};
     if (n > 0) {
         cudaError_t e = cudaMalloc(&h->P, (size_t)n * 4);
+        if (e == cudaSuccess && fo.kind == CC_FINISH_UF_HOOKS) {
+            e = cudaMalloc(&h->hooks, (size_t)n * 4);
+            if (e == cudaSuccess) e = cudaMemsetAsync(h->hooks, 0xFF, (size_t)n * 4, s);
+        }
         if (e != cudaSuccess) {
+            if (h->P) cudaFree(h->P);
+            if (h->hooks) cudaFree(h->hooks);
             delete h;
             return from_cuda(e);
         }
@@ -143,6 +134,7 @@ cc_status cc_incr_create(const void *offsets, int offsets_u64, const uint32_t *e
         }
         if (st != CC_OK) {
             cudaFree(h->P);
+            if (h->hooks) cudaFree(h->hooks);
             delete h;
             return st;
         }
@@ -159,9 +151,10 @@ cc_status cc_incr_insert_batch(cc_incr *h, const uint32_t *pairs, uint64_t k, vo
     const DeviceInfo *di = device_info();
     if (!di) return CC_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const Dev d = make_dev(di, h->n);
+    Dev d = make_dev(di, h->n);
+    d.hooks = h->hooks;
     const unsigned grid = grid_for(di, (k + 3) / 4, TPB);
-    return with_uf_engine(h->fo, [&](auto eng) -> cc_status {
+    return with_uf_engine(h->fo.kind, h->fo.find, h->fo.splice, [&](auto eng) -> cc_status {
         using E = decltype(eng);
         {
             CC_PROF("k_incr_insert", s);
@@ -183,6 +176,7 @@ cc_status cc_incr_query_batch(cc_incr *h, const uint32_t *pairs, uint64_t q, uin
     switch (h->fo.find) {
         case CC_FIND_SPLIT: { CC_PROF("k_incr_query", s); k_incr_query<FIND_SPLIT><<<grid, TPB, 0, s>>>(h->P, h->n, pairs, q, answers_out, d); } break;
         case CC_FIND_HALVE: { CC_PROF("k_incr_query", s); k_incr_query<FIND_HALVE><<<grid, TPB, 0, s>>>(h->P, h->n, pairs, q, answers_out, d); } break;
+        case CC_FIND_COMPRESS: { CC_PROF("k_incr_query", s); k_incr_query<FIND_COMPRESS><<<grid, TPB, 0, s>>>(h->P, h->n, pairs, q, answers_out, d); } break;
         default: { CC_PROF("k_incr_query", s); k_incr_query<FIND_NAIVE><<<grid, TPB, 0, s>>>(h->P, h->n, pairs, q, answers_out, d); } break;
     }
     return from_cuda(cudaGetLastError());
@@ -208,6 +202,10 @@ cc_status cc_incr_destroy(cc_incr *h) {
     if (!h) return CC_OK;
     cudaError_t e = cudaSuccess;
     if (h->P) e = cudaFree(h->P);
+    if (h->hooks) {
+        const cudaError_t e2 = cudaFree(h->hooks);
+        if (e == cudaSuccess) e = e2;
+    }
     delete h;
     return from_cuda(e);
 }

@@ -108,6 +108,27 @@ class LaunchScope {
 #define CC_CAT(a, b) CC_CAT2(a, b)
 #define CC_PROF(name, stream) ::ccg::LaunchScope CC_CAT(cc_prof_, __LINE__)(name, stream)
 
+// The min-label finishes that need not be monotone (cc_minlabel.cu): the
+// Liu-Tarjan framework's variants, Stergiou's algorithm, label propagation.
+// They run on the candidate lists the binning pass built (candidates: the
+// vertices with edges whose sampled label is not the frequent one).
+struct MinLabelIn {
+    const void *I;
+    bool offsets_u64;
+    const uint32_t *A;
+    uint32_t n;
+    uint64_t m;
+    uint32_t *P;                            // sampled labels in, canonical labels out
+    const uint32_t *lmax_p;                 // device: the frequent sampled label, or null
+    const uint32_t *light, *nlight;         // device: candidates of degree <= LIGHT_MAX
+    const ChunkRef *chunks;                 // device: CHUNK-edge pieces of the heavier candidates
+    const uint32_t *nchunks;
+    uint64_t chunk_cap;
+    const unsigned long long *cand_edges;   // device: edges out of the candidates
+};
+cc_status minlabel_finish(const MinLabelIn &in, const cc_finish_opt &fo, const DeviceInfo *di, const Dev &d,
+                          cudaStream_t s, uint32_t *rounds_out);
+
 // Validation shared by the entry points (host side, synchronous).
 inline bool aligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 cc_status check_graph(const void *offsets, int offsets_u64, const uint32_t *edges, uint32_t n, uint64_t m);

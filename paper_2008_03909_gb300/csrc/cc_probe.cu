@@ -13,6 +13,19 @@ namespace {
 
 constexpr unsigned TPB = 256;
 
+// Per-vertex reduction of the light path: MODE 0 counts the edges read,
+// MODE 1 sums x at the neighbours.
+template <int MODE>
+struct ProbeEdge {
+    const uint32_t *x;
+    uint32_t acc;
+    __device__ __forceinline__ void apply4(uint32_t, const uint32_t (&v)[4], const bool (&ok)[4]) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (ok[j]) acc += MODE == 0 ? 1u : x[v[j]];
+    }
+};
+
 // MODE 0: MapEdges, out[v] = #edges read; MODE 1: GatherEdges,
 // out[v] = sum of x[w] over neighbours w (mod 2^32).  Vertices of degree
 // <= LIGHT_MAX are reduced by one thread; heavier ones are zeroed here and
@@ -35,13 +48,9 @@ __global__ void __launch_bounds__(256, 8) k_probe_bin(const OffT *I, const uint3
             write_chunks(chunks, cap, slot, nc, (uint32_t)v, d);
             out[v] = 0;
         } else if (v < n) {
-            uint32_t acc = 0;
-            for (uint64_t i = b; i < e; ++i) {
-                const uint32_t w = ld_stream(A + i);
-                if (w >= n) { atomicOr(d.err, ERR_BAD_EDGE); continue; }
-                acc += MODE == 0 ? 1u : x[w];
-            }
-            out[v] = acc;
+            ProbeEdge<MODE> f{x, 0u};
+            light_edges((uint32_t)v, b, e, A, n, f, d);
+            out[v] = f.acc;
         }
     }
 }

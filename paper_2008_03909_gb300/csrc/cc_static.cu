@@ -122,8 +122,8 @@ constexpr int KOUT_MINB = 8;
 
 template <typename OffT, class E, int NB>
 __global__ void __launch_bounds__(256, KOUT_MINB)
-k_kout(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, uint32_t k, uint64_t seed, uint32_t *P,
-       Dev d, uint32_t jb, uint32_t je) {
+k_kout(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, uint32_t k, uint32_t rule, uint64_t seed,
+       uint32_t *P, Dev d, uint32_t jb, uint32_t je) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     // software pipeline: the next vertex's offsets are in flight while the
@@ -147,9 +147,8 @@ k_kout(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, uint32_t k, uin
             for (int q = 0; q < NB; ++q) {
                 const uint32_t pick = j0 + q;
                 u[q] = (uint32_t)v;
-                ok[q] = pick < je;
-                uint64_t off = 0;
-                if (ok[q] && pick > 0) off = ((draw64(seed ^ TAG_KOUT, v * k + pick) >> 32) * deg) >> 32;
+                const uint64_t off = pick < je ? kout_offset(rule, seed, v, k, pick, deg) : NO_PICK;
+                ok[q] = off != NO_PICK;
                 w[q] = ok[q] ? ld_stream(A + b + off) : u[q];
                 if (ok[q] && w[q] >= n) { atomicOr(d.err, ERR_BAD_EDGE); ok[q] = false; }
                 if (ok[q] && w[q] == u[q]) ok[q] = false;
@@ -162,9 +161,9 @@ k_kout(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, uint32_t k, uin
 // picks per thread step: one when a round has a single pick (k = 2), else four
 template <typename OffT, class E>
 void launch_kout(unsigned grid, cudaStream_t s, const OffT *I, const uint32_t *A, uint32_t n, uint64_t m,
-                 uint32_t k, uint64_t seed, uint32_t *P, Dev d, uint32_t jb, uint32_t je) {
-    if (je - jb == 1) k_kout<OffT, E, 1><<<grid, 256, 0, s>>>(I, A, n, m, k, seed, P, d, jb, je);
-    else k_kout<OffT, E, 4><<<grid, 256, 0, s>>>(I, A, n, m, k, seed, P, d, jb, je);
+                 uint32_t k, uint32_t rule, uint64_t seed, uint32_t *P, Dev d, uint32_t jb, uint32_t je) {
+    if (je - jb == 1) k_kout<OffT, E, 1><<<grid, 256, 0, s>>>(I, A, n, m, k, rule, seed, P, d, jb, je);
+    else k_kout<OffT, E, 4><<<grid, 256, 0, s>>>(I, A, n, m, k, rule, seed, P, d, jb, je);
 }
 
 // First edges, part one (replaces the identity initialisation): each
@@ -172,12 +171,12 @@ void launch_kout(unsigned grid, cudaStream_t s, const OffT *I, const uint32_t *A
 // with a plain store: in this pass only v's thread writes P[v], so v is
 // still a root and the link keeps P[x] <= x.  Otherwise P[v] = v, and a
 // vertex with w0 > v (all its neighbours larger) is queued for a real Union
-// in part two.  Four vertices per lane, vector loads and stores.
+// in part two as the pair (v, w0), so part two reads no offsets or edges.
 template <typename OffT>
 __global__ void __launch_bounds__(256, 8) k_kout_hook_first(const OffT *I, const uint32_t *A, uint32_t n,
-                                                            uint64_t m, uint32_t *P, uint32_t *defer,
-                                                            uint32_t *ndefer, uint32_t *pick1, uint64_t seed,
-                                                            Dev d) {
+                                                            uint64_t m, uint32_t *P, uint2 *defer,
+                                                            uint32_t *ndefer, uint32_t *pick1, uint32_t k,
+                                                            uint32_t rule, uint64_t seed, Dev d) {
     const int lane = threadIdx.x & 31;
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -210,13 +209,14 @@ __global__ void __launch_bounds__(256, 8) k_kout_hook_first(const OffT *I, const
             const uint64_t v = base + 32 * j + lane;
             uint64_t b = 0, e = 0;
             if (v < n) clamp_range(beg[j], end[j], m, b, e, d);
-            w[j] = e > b ? ld_stream(A + b) : NONE;
-            // with k = 2 the random pick (slot 1) is read here too and kept
-            // for the second round, so that round reads no offsets or edges
+            // pick 0 (the first edge, or a uniform pick under the pure rule)
+            w[j] = e > b ? ld_stream(A + b + kout_offset(rule, seed, v, k, 0, e - b)) : NONE;
+            // with k = 2 pick 1 is read here too and kept for the second
+            // round, so that round reads no offsets or edges
             r[j] = NONE;
             if (pick1 && e > b) {
-                const uint64_t off = ((draw64(seed ^ TAG_KOUT, v * 2 + 1) >> 32) * (e - b)) >> 32;
-                r[j] = ld_stream(A + b + off);
+                const uint64_t off = kout_offset(rule, seed, v, 2, 1, e - b);
+                if (off != NO_PICK) r[j] = ld_stream(A + b + off);
             }
         }
         // the next step's offsets load while this step's first edges are read
@@ -227,6 +227,7 @@ __global__ void __launch_bounds__(256, 8) k_kout_hook_first(const OffT *I, const
             const uint64_t v = base + 32 * j + lane;
             if (w[j] != NONE && w[j] >= n) { atomicOr(d.err, ERR_BAD_EDGE); w[j] = NONE; }
             if (v < n) P[v] = (w[j] != NONE && w[j] < v) ? w[j] : (uint32_t)v;
+            if (d.forest && v < n && w[j] != NONE && w[j] < v) d.forest[v] = make_uint2((uint32_t)v, w[j]);
             nd += (w[j] != NONE && w[j] > v);
             if (pick1 && v < n) {
                 if (r[j] != NONE && r[j] >= n) { atomicOr(d.err, ERR_BAD_EDGE); r[j] = NONE; }
@@ -236,7 +237,22 @@ __global__ void __launch_bounds__(256, 8) k_kout_hook_first(const OffT *I, const
         uint32_t slot = warp_append_full(ndefer, nd);
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-            if (w[j] != NONE && w[j] > base + 32 * j + lane) defer[slot++] = (uint32_t)(base + 32 * j + lane);
+            if (w[j] != NONE && w[j] > base + 32 * j + lane)
+                defer[slot++] = make_uint2((uint32_t)(base + 32 * j + lane), w[j]);
+    }
+}
+
+// First edges, part two: Union(v, w0) for the queued (v, w0) pairs.
+template <class E>
+__global__ void __launch_bounds__(256, KOUT_MINB)
+k_kout_defer(uint32_t n, uint32_t *P, const uint2 *defer, const uint32_t *ndefer, Dev d) {
+    const uint32_t total = *ndefer;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint2 q = defer[i];
+        uint32_t u1[1] = {q.x}, w1[1] = {q.y};
+        bool ok[1] = {q.y < n && q.y != q.x};
+        unite_pairs<E, 1>(P, u1, w1, ok, d);
     }
 }
 
@@ -249,24 +265,6 @@ __global__ void __launch_bounds__(256, 8) k_kout_apply_pick(const uint32_t *pick
         const uint32_t w = pick1[v];
         uint32_t u1[1] = {(uint32_t)v}, w1[1] = {w};
         bool ok[1] = {w != NONE};
-        unite_pairs<E, 1>(P, u1, w1, ok, d);
-    }
-}
-
-// First edges, part two: Union(v, w0) for the queued vertices.
-template <typename OffT, class E>
-__global__ void __launch_bounds__(256, KOUT_MINB)
-k_kout_defer(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, uint32_t *P, const uint32_t *defer,
-             const uint32_t *ndefer, Dev d) {
-    const uint32_t total = *ndefer;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t v = defer[i];
-        uint64_t b, e;
-        vertex_range(I, v, m, b, e, d);
-        if (e == b) continue;
-        uint32_t u1[1] = {v}, w1[1] = {ld_stream(A + b)};
-        bool ok[1] = {w1[0] < n && w1[0] != v};
         unite_pairs<E, 1>(P, u1, w1, ok, d);
     }
 }
@@ -560,7 +558,8 @@ struct BFSEdge {
     uint32_t *minv;
     uint32_t src;
     uint32_t my_min;
-    __device__ __forceinline__ void apply4(uint32_t, const uint32_t (&v)[4], const bool (&ok)[4]) {
+    uint2 *forest;   // spanning forest: the tree edge (u, w) at the child w
+    __device__ __forceinline__ void apply4(uint32_t u, const uint32_t (&v)[4], const bool (&ok)[4]) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             if (!ok[j]) continue;
@@ -569,6 +568,7 @@ struct BFSEdge {
             if (ld_rel(word) & bit) continue;
             if (atomicOr(word, bit) & bit) continue;
             P[w] = src;
+            if (forest) forest[w] = make_uint2(u, w);
             next[append_one(nnext)] = w;
             my_min = w < my_min ? w : my_min;
         }
@@ -597,6 +597,7 @@ __global__ void __launch_bounds__(256, 8) k_bfs_pull(const OffT *I, const uint32
             if (y >= n) { atomicOr(d.err, ERR_BAD_EDGE); continue; }
             if (front_bm[y >> 5] & (1u << (y & 31))) {
                 P[w] = src;
+                if (d.forest) d.forest[w] = make_uint2(y, w);
                 atomicOr(next_bm + (w >> 5), bit);
                 atomicOr(vis + (w >> 5), bit);
                 ++cnt;
@@ -668,12 +669,134 @@ __global__ void __launch_bounds__(256, 8) k_bfs_relabel(uint32_t *P, const uint3
         if (vis[i >> 5] & (1u << (i & 31))) P[i] = mn;
 }
 
+// Top-down levels in one persistent launch.  A high-diameter graph (a road
+// network, a grid) needs tens of thousands of levels whose frontiers are
+// small; one launch sequence and one host round trip per level would
+// dominate.  Here every block of a cooperative launch runs level after level
+// with a grid barrier between them, and the launch returns to the host once
+// the frontier is empty, its edges exceed `mf_max`, or the direction rule
+// asks for bottom-up (frontier edges > unexplored / 14).
+// Frontier counts and edge sums rotate over three slots: level L reads slot
+// L % 3, appends into slot (L + 1) % 3, and clears slot (L + 2) % 3, which no
+// block reads after the barrier that ended level L - 1.
+struct BfsLoop {
+    GridBar bar;
+    uint32_t cnt[3];
+    uint32_t levels;
+    unsigned long long mfc[3];
+    unsigned long long reached;    // vertices claimed by the levels run
+    unsigned long long explored;   // frontier edges of the levels run
+};
+
+template <typename OffT>
+struct BFSPushEdge {
+    const OffT *I;
+    uint64_t m;
+    uint32_t *P;
+    uint32_t *vis;
+    uint32_t *next;
+    uint32_t *nnext;
+    uint32_t src;
+    uint32_t my_min;
+    unsigned long long my_edges;
+    Dev d;
+    __device__ __forceinline__ void apply4(uint32_t u, const uint32_t (&v)[4], const bool (&ok)[4]) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (!ok[j]) continue;
+            const uint32_t w = v[j], bit = 1u << (w & 31);
+            uint32_t *word = vis + (w >> 5);
+            if (ld_rel(word) & bit) continue;
+            if (atomicOr(word, bit) & bit) continue;
+            P[w] = src;
+            if (d.forest) d.forest[w] = make_uint2(u, w);
+            next[append_one(nnext)] = w;
+            my_min = w < my_min ? w : my_min;
+            uint64_t b, e;
+            vertex_range(I, w, m, b, e, d);
+            my_edges += e - b;
+        }
+    }
+};
+
+constexpr unsigned BFS_LOOP_TPB = 512;
+constexpr uint64_t BFS_LOOP_MF_MAX = 1ull << 24;   // frontier edges beyond which a level runs as its own launches
+constexpr uint32_t BFS_LOOP_LEVELS = 1u << 16;      // levels per launch at most (a launch stays well under a second)
+
+template <typename OffT>
+__global__ void __launch_bounds__(BFS_LOOP_TPB, 2) k_bfs_push_levels(const OffT *I, const uint32_t *A, uint32_t n,
+                                                                  uint64_t m, uint32_t *P, uint32_t *vis,
+                                                                  uint32_t *q0, uint32_t *q1, uint32_t src,
+                                                                  BfsLoop *L, uint32_t *cnt_out0,
+                                                                  uint32_t *cnt_out1, uint32_t *minv,
+                                                                  uint64_t unexplored0, uint64_t mf_max,
+                                                                  uint32_t max_levels, Dev d) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    uint32_t my_min = NONE;
+    uint64_t explored = 0, reached = 0;
+    uint32_t lv = 0, nf = 0;
+    for (;; ++lv) {
+        nf = ld_rel(&L->cnt[lv % 3]);
+        const uint64_t mf = ld_rel64(&L->mfc[lv % 3]);
+        if (lv > 0) reached += nf;
+        const uint64_t unexplored = unexplored0 > explored ? unexplored0 - explored : 0;
+        if (nf == 0 || lv == max_levels || mf > mf_max || mf > unexplored / 14) break;
+        uint32_t *cur = (lv & 1) ? q1 : q0;
+        uint32_t *nx = (lv & 1) ? q0 : q1;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            L->cnt[(lv + 2) % 3] = 0;
+            L->mfc[(lv + 2) % 3] = 0;
+        }
+        BFSPushEdge<OffT> f{I, m, P, vis, nx, &L->cnt[(lv + 1) % 3], src, NONE, 0ull, d};
+        for (uint64_t base = warp * 32; base < nf; base += nwarps * 32) {
+            const bool act = base + lane < nf;
+            const uint32_t u = act ? cur[base + lane] : 0;
+            uint64_t b = 0, e = 0;
+            if (act) vertex_range(I, u, m, b, e, d);
+            const bool heavy = e - b > LIGHT_MAX;
+            if (act && !heavy) light_edges(u, b, e, A, n, f, d);
+            // heavier vertices: the whole warp walks their edges
+            uint32_t hm = __ballot_sync(0xFFFFFFFFu, heavy);
+            while (hm) {
+                const int l = __ffs(hm) - 1;
+                hm &= hm - 1;
+                const uint32_t hu = __shfl_sync(0xFFFFFFFFu, u, l);
+                const uint64_t hb = __shfl_sync(0xFFFFFFFFu, b, l), he = __shfl_sync(0xFFFFFFFFu, e, l);
+                warp_chunk_edges(hu, hb, he, A, n, f, d);
+            }
+        }
+        unsigned long long me = f.my_edges;
+        for (int o = 16; o > 0; o >>= 1) me += __shfl_xor_sync(0xFFFFFFFFu, me, o);
+        if (lane == 0 && me) atomicAdd(&L->mfc[(lv + 1) % 3], me);
+        my_min = f.my_min < my_min ? f.my_min : my_min;
+        explored += mf;
+        if (!grid_sync(&L->bar, d)) break;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint32_t t = __shfl_xor_sync(0xFFFFFFFFu, my_min, o);
+        my_min = t < my_min ? t : my_min;
+    }
+    if (lane == 0 && my_min != NONE && my_min < ld_rel(minv)) atomicMin(minv, my_min);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        L->levels = lv;
+        L->reached = reached;
+        L->explored = explored;
+        *((lv & 1) ? cnt_out1 : cnt_out0) = nf;
+    }
+}
+
 // ---------------------------------------------------------------- LDD sampling
 // Round r of the clustering (Algorithm 6): every uncovered id in [s0, s1)
 // becomes a centre; then the frontier claims uncovered neighbours, the
 // smallest claiming centre id winning (candidates first, commit after).
+// stamp (spanning forest only, else null): the search step at which a
+// vertex joined its cluster; a centre woken before step t has stamp t - 1,
+// a vertex claimed in step t has stamp t.
 __global__ void __launch_bounds__(256, 8) k_ldd_wake(uint32_t s0, uint32_t s1, uint32_t *P, uint32_t *vis, uint32_t *front,
-                           uint32_t *nfront, uint32_t *last_round, uint32_t round) {
+                           uint32_t *nfront, uint32_t *last_round, uint32_t round, uint32_t *stamp,
+                           uint32_t step) {
     bool any = false;
     for (uint64_t i = s0 + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < s1;
          i += (uint64_t)gridDim.x * blockDim.x) {
@@ -681,6 +804,7 @@ __global__ void __launch_bounds__(256, 8) k_ldd_wake(uint32_t s0, uint32_t s1, u
         if (vis[v >> 5] & bit) continue;
         atomicOr(vis + (v >> 5), bit);
         P[v] = v;
+        if (stamp) stamp[v] = step - 1;
         front[append_one(nfront)] = v;
         any = true;
     }
@@ -708,16 +832,47 @@ struct LDDEdge {
 };
 
 __global__ void __launch_bounds__(256, 8) k_ldd_commit(uint32_t *P, uint32_t *vis, uint32_t *cand, const uint32_t *next,
-                             const uint32_t *nnext, uint32_t *last_round, uint32_t round) {
+                             const uint32_t *nnext, uint32_t *last_round, uint32_t round, uint32_t *stamp,
+                             uint32_t step) {
     const uint32_t total = *nnext;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
          i += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t w = next[i];
         P[w] = cand[w];
+        if (stamp) stamp[w] = step;
         cand[w] = NONE;
         atomicOr(vis + (w >> 5), 1u << (w & 31));
     }
     if (blockIdx.x == 0 && threadIdx.x == 0 && total) atomicMax(last_round, round + 1);
+}
+
+// Spanning-forest edges of the LDD clusters (the searches' tree edges,
+// assigned to the child): a non-centre w was claimed in step t by a
+// frontier vertex of its own cluster that joined in step t - 1, so such a
+// neighbour exists; any one of them is a valid parent, because following
+// parents strictly lowers the step and ends at the cluster's only
+// vertex without one, its centre.  Runs before the clusters are relabelled
+// (P[w] is still w's centre; centres are the w with P[w] = w).
+template <typename OffT>
+__global__ void __launch_bounds__(256, 8) k_ldd_tree_edges(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m,
+                                                           const uint32_t *P, const uint32_t *stamp, Dev d) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t w = (uint32_t)i, c = P[w];
+        if (c == w) continue;
+        const uint32_t want = stamp[w] - 1;
+        uint64_t b, e;
+        vertex_range(I, w, m, b, e, d);
+        bool found = false;
+        for (uint64_t x = b; x < e && !found; ++x) {
+            const uint32_t u = ld_stream(A + x);
+            if (u < n && P[u] == c && stamp[u] == want) {
+                d.forest[w] = make_uint2(u, w);
+                found = true;
+            }
+        }
+        if (!found) atomicOr(d.err, ERR_NONCONVERGED);
+    }
 }
 
 // Relabel clusters to their smallest members: cmin[c] = min{v : P[v] = c}
@@ -832,19 +987,34 @@ struct Work {
     Scratch sc;
     size_t o_defer = 0, o_pick = 0;
     size_t o_ctl = 0, o_chunks = 0, o_counts = 0, o_prev = 0, o_light = 0, o_vis = 0, o_q0 = 0, o_q1 = 0,
-           o_bm0 = 0, o_bm1 = 0, o_cand = 0;
+           o_bm0 = 0, o_bm1 = 0, o_cand = 0, o_loop = 0, o_stamp = 0, o_sf = 0, o_ff = 0, o_fcount = 0,
+           o_hooks = 0;
+    bool has_hooks = false;
     bool has_counts = false, has_sv = false, has_bfs = false, has_ldd = false;
     uint64_t chunk_cap = 0;
     Ctl *ctl() const { return sc.at<Ctl>(o_ctl); }
 };
 
-void plan(Work &w, const Graph &g, int sample_kind, uint32_t freq_samples, int finish_kind, bool finish_phase) {
+// forest: also the spanning-forest arrays (sampling edges by child / hooked
+// root, finish edges by hooked root, (NONE, NONE) where empty).
+void plan(Work &w, const Graph &g, int sample_kind, uint32_t freq_samples, int finish_kind, bool finish_phase,
+          bool forest = false) {
     const uint64_t n = g.n;
+    if (finish_kind == CC_FINISH_UF_HOOKS) {
+        w.has_hooks = true;
+        w.o_hooks = w.sc.reserve(n * 4);
+    }
+    if (forest) {
+        w.o_sf = w.sc.reserve(n * 8);
+        w.o_ff = w.sc.reserve(n * 8);
+        w.o_fcount = w.sc.reserve(8);
+        if (sample_kind == CC_SAMPLE_LDD) w.o_stamp = w.sc.reserve(n * 4);
+    }
     w.o_ctl = w.sc.reserve(sizeof(Ctl));
     w.chunk_cap = chunk_capacity(n, g.m);
     w.o_chunks = w.sc.reserve(w.chunk_cap * sizeof(ChunkRef));
     if (sample_kind == CC_SAMPLE_KOUT) {
-        w.o_defer = w.sc.reserve(n * 4);
+        w.o_defer = w.sc.reserve(n * 8);
         w.o_pick = w.sc.reserve(n * 4);
     }
     if (sample_kind != CC_SAMPLE_NONE && freq_samples == 0) {
@@ -864,6 +1034,7 @@ void plan(Work &w, const Graph &g, int sample_kind, uint32_t freq_samples, int f
         w.o_q1 = w.sc.reserve(n * 4);
         w.o_bm0 = w.sc.reserve(words * 4);
         w.o_bm1 = w.sc.reserve(words * 4);
+        w.o_loop = w.sc.reserve(sizeof(BfsLoop));
     }
     if (sample_kind == CC_SAMPLE_LDD) {
         w.has_ldd = true;
@@ -881,26 +1052,17 @@ void plan(Work &w, const Graph &g, int sample_kind, uint32_t freq_samples, int f
     } while (0)
 #define CC_LAUNCH() CC_TRY(cudaGetLastError())
 
+// After the scratch is allocated: UF-Hooks' hooks array starts all free.
+cc_status attach_hooks(Work &w, Dev &d, uint32_t n, cudaStream_t s) {
+    if (!w.has_hooks) return CC_OK;
+    d.hooks = w.sc.at<uint32_t>(w.o_hooks);
+    CC_TRY(cudaMemsetAsync(d.hooks, 0xFF, (size_t)n * 4, s));
+    return CC_OK;
+}
+
 template <class Fn>
 cc_status with_engine(const cc_finish_opt &f, Fn &&fn) {
-    if (f.kind == CC_FINISH_UF_ASYNC) {
-        switch (f.find) {
-            case CC_FIND_NAIVE: return fn(UnionAsync<FIND_NAIVE>{});
-            case CC_FIND_SPLIT: return fn(UnionAsync<FIND_SPLIT>{});
-            default: return fn(UnionAsync<FIND_HALVE>{});
-        }
-    }
-    // UF-Rem-CAS; also the engine of k-out sampling under SV / LT finishes.
-    const int key = (f.kind == CC_FINISH_UF_REM_CAS ? f.splice : CC_SPLICE_SPLIT_ONE) * 3 +
-                    (f.kind == CC_FINISH_UF_REM_CAS ? f.find : CC_FIND_NAIVE);
-    switch (key) {
-        case 0: return fn(UnionRem<SPLICE_SPLIT_ONE, FIND_NAIVE>{});
-        case 1: return fn(UnionRem<SPLICE_SPLIT_ONE, FIND_SPLIT>{});
-        case 2: return fn(UnionRem<SPLICE_SPLIT_ONE, FIND_HALVE>{});
-        case 3: return fn(UnionRem<SPLICE_HALVE_ONE, FIND_NAIVE>{});
-        case 4: return fn(UnionRem<SPLICE_HALVE_ONE, FIND_SPLIT>{});
-        default: return fn(UnionRem<SPLICE_HALVE_ONE, FIND_HALVE>{});
-    }
+    return with_uf_engine(f.kind, f.find, f.splice, fn);
 }
 
 // ---------------------------------------------------------------- phases
@@ -923,11 +1085,17 @@ cc_status bfs_sample(const Graph &g, const cc_sample_opt &so, uint32_t *P, Work 
         unsigned long long mf;
     };
     Lv *hl = nullptr;
-    CC_TRY(cudaMallocHost(&hl, sizeof(Lv)));
+    CC_TRY(cudaMallocHost(&hl, sizeof(Lv) + sizeof(BfsLoop)));
     struct Free {
         Lv *p;
         ~Free() { cudaFreeHost(p); }
     } fr{hl};
+    BfsLoop *hloop = reinterpret_cast<BfsLoop *>(hl + 1);
+    BfsLoop *loop = w.sc.at<BfsLoop>(w.o_loop);
+    // persistent top-down levels: one cooperative launch of every co-resident block
+    int per_sm = 0;
+    CC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bfs_push_levels<OffT>, BFS_LOOP_TPB, 0));
+    const unsigned loop_grid = (unsigned)(per_sm < 2 ? per_sm : 2) * di->sms;
     *info = -1;
     for (uint32_t t = 0; t < so.bfs_tries; ++t) {
         const uint32_t src = (uint32_t)(draw64(so.seed ^ TAG_BFS, t) % n);
@@ -935,6 +1103,8 @@ cc_status bfs_sample(const Graph &g, const cc_sample_opt &so, uint32_t *P, Work 
             CC_PROF("k_iota", s);
             k_iota<<<gv, TPB, 0, s>>>(P, n);
         }
+        // a failed try leaves no tree edges behind
+        if (d.forest && t > 0) CC_TRY(cudaMemsetAsync(d.forest, 0xFF, (size_t)n * 8, s));
         CC_TRY(cudaMemsetAsync(vis, 0, words * 4, s));
         CC_TRY(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
         {
@@ -1001,8 +1171,43 @@ cc_status bfs_sample(const Graph &g, const cc_sample_opt &so, uint32_t *P, Work 
                 }
                 CC_LAUNCH();
             } else {
+                if (loop_grid > 0 && mf <= BFS_LOOP_MF_MAX) {
+                    memset(hloop, 0, sizeof(BfsLoop));
+                    hloop->cnt[0] = (uint32_t)nf;
+                    hloop->mfc[0] = mf;
+                    CC_TRY(cudaMemcpyAsync(loop, hloop, sizeof(BfsLoop), cudaMemcpyHostToDevice, s));
+                    uint32_t *qc = q[cur], *qn = q[nx], *c0 = &ctl->nfront[cur], *c1 = &ctl->nfront[nx];
+                    uint32_t *mv = &ctl->minv;
+                    const uint64_t unexplored0 = unexplored, mfmax = BFS_LOOP_MF_MAX;
+                    uint32_t nn = n, srcv = src, maxl = BFS_LOOP_LEVELS;
+                    uint64_t mm = g.m;
+                    const OffT *Ip = I;
+                    const uint32_t *Ap = g.A;
+                    Dev dd = d;
+                    void *args[] = {&Ip, &Ap, &nn, &mm, &P, &vis, &qc, &qn, &srcv, &loop, &c0, &c1, &mv,
+                                    const_cast<uint64_t *>(&unexplored0), const_cast<uint64_t *>(&mfmax), &maxl,
+                                    &dd};
+                    {
+                        CC_PROF("k_bfs_push_levels", s);
+                        CC_TRY(cudaLaunchCooperativeKernel((const void *)k_bfs_push_levels<OffT>, loop_grid,
+                                                           BFS_LOOP_TPB, args, 0, s));
+                    }
+                    CC_TRY(cudaMemcpyAsync(hloop, loop, sizeof(BfsLoop), cudaMemcpyDeviceToHost, s));
+                    CC_TRY(cudaStreamSynchronize(s));
+                    if (hloop->bar.abort) return CC_ERR_NONCONVERGED;
+                    const uint32_t L = hloop->levels;
+                    if (L > 0) {
+                        if (L & 1) cur = nx;
+                        nf = hloop->cnt[L % 3];
+                        mf = hloop->mfc[L % 3];
+                        reached += hloop->reached;
+                        explored_edges += hloop->explored;
+                        level += L - 1;
+                        continue;
+                    }
+                }
                 CC_TRY(cudaMemsetAsync(&ctl->nchunks, 0, 4, s));
-                BFSEdge f{P, vis, q[nx], &ctl->nfront[nx], &ctl->minv, src, NONE};
+                BFSEdge f{P, vis, q[nx], &ctl->nfront[nx], &ctl->minv, src, NONE, d.forest};
                 {
                     CC_PROF("k_list_bin", s);
                     k_list_bin<OffT, BFSEdge><<<gv, TPB, 0, s>>>(I, g.A, n, g.m, q[cur], &ctl->nfront[cur], f, chunks,
@@ -1039,6 +1244,7 @@ cc_status bfs_sample(const Graph &g, const cc_sample_opt &so, uint32_t *P, Work 
             return CC_OK;
         }
     }
+    if (d.forest) CC_TRY(cudaMemsetAsync(d.forest, 0xFF, (size_t)n * 8, s));
     {
         CC_PROF("k_iota", s);
         k_iota<<<gv, TPB, 0, s>>>(P, n);
@@ -1057,6 +1263,7 @@ cc_status ldd_sample(const Graph &g, const cc_sample_opt &so, uint32_t *P, Work 
     uint32_t *vis = w.sc.at<uint32_t>(w.o_vis);
     uint32_t *q[2] = {w.sc.at<uint32_t>(w.o_q0), w.sc.at<uint32_t>(w.o_q1)};
     uint32_t *cand = w.sc.at<uint32_t>(w.o_cand);
+    uint32_t *stamp = d.forest ? w.sc.at<uint32_t>(w.o_stamp) : nullptr;
     ChunkRef *chunks = w.sc.at<ChunkRef>(w.o_chunks);
     const unsigned gv = grid_for(di, n, TPB);
     const unsigned gc = grid_for(di, (uint64_t)1 << 40, TPB);
@@ -1078,7 +1285,8 @@ cc_status ldd_sample(const Graph &g, const cc_sample_opt &so, uint32_t *P, Work 
         {
             CC_PROF("k_ldd_wake", s);
             k_ldd_wake<<<grid_for(di, S1 - S, TPB), TPB, 0, s>>>((uint32_t)S, (uint32_t)S1, P, vis, q[cur],
-                                                                  &ctl->nfront[cur], &ctl->last_round, r);
+                                                                  &ctl->nfront[cur], &ctl->last_round, r, stamp,
+                                                                  r + 1);
         }
         CC_TRY(cudaMemsetAsync(&ctl->nfront[nx], 0, 4, s));
         CC_TRY(cudaMemsetAsync(&ctl->nchunks, 0, 4, s));
@@ -1094,7 +1302,8 @@ cc_status ldd_sample(const Graph &g, const cc_sample_opt &so, uint32_t *P, Work 
         }
         {
             CC_PROF("k_ldd_commit", s);
-            k_ldd_commit<<<gv, TPB, 0, s>>>(P, vis, cand, q[nx], &ctl->nfront[nx], &ctl->last_round, r);
+            k_ldd_commit<<<gv, TPB, 0, s>>>(P, vis, cand, q[nx], &ctl->nfront[nx], &ctl->last_round, r, stamp,
+                                            r + 1);
         }
         CC_TRY(cudaMemsetAsync(&ctl->nfront[cur], 0, 4, s));
         CC_LAUNCH();
@@ -1122,12 +1331,17 @@ cc_status ldd_sample(const Graph &g, const cc_sample_opt &so, uint32_t *P, Work 
         }
         {
             CC_PROF("k_ldd_commit", s);
-            k_ldd_commit<<<gv, TPB, 0, s>>>(P, vis, cand, q[nx], &ctl->nfront[nx], &ctl->last_round, r);
+            k_ldd_commit<<<gv, TPB, 0, s>>>(P, vis, cand, q[nx], &ctl->nfront[nx], &ctl->last_round, r, stamp,
+                                            r + 1);
         }
         CC_TRY(cudaMemsetAsync(&ctl->nfront[cur], 0, 4, s));
         CC_LAUNCH();
         cur = nx;
         ++r;
+    }
+    if (stamp) {
+        CC_PROF("k_ldd_tree_edges", s);
+        k_ldd_tree_edges<OffT><<<gv, TPB, 0, s>>>(I, g.A, n, g.m, P, stamp, d);
     }
     // clusters -> min-id stars (cand is all NONE again and serves as cmin)
     {
@@ -1167,26 +1381,31 @@ cc_status sample_phase(const Graph &g, const cc_sample_opt &so, const cc_finish_
     return with_engine(fo, [&](auto eng) -> cc_status {
         using E = decltype(eng);
         const OffT *I = static_cast<const OffT *>(g.I);
-        uint32_t *defer = w.sc.at<uint32_t>(w.o_defer);
+        uint2 *defer = w.sc.at<uint2>(w.o_defer);
         Ctl *ctl = w.ctl();
         CC_TRY(cudaMemsetAsync(&ctl->ndefer, 0, 4, s));
         uint32_t *pick1 = so.k == 2 ? w.sc.at<uint32_t>(w.o_pick) : nullptr;
         {
             CC_PROF("k_kout_hook_first", s);
-            k_kout_hook_first<OffT><<<gv, TPB, 0, s>>>(I, g.A, g.n, g.m, P, defer, &ctl->ndefer, pick1, so.seed, d);
+            k_kout_hook_first<OffT><<<gv, TPB, 0, s>>>(I, g.A, g.n, g.m, P, defer, &ctl->ndefer, pick1, so.k,
+                                                       so.kout_rule, so.seed, d);
         }
         {
             CC_PROF("k_kout_defer", s);
-            k_kout_defer<OffT, E><<<gv, TPB, 0, s>>>(I, g.A, g.n, g.m, P, defer, &ctl->ndefer, d);
+            k_kout_defer<E><<<gv, TPB, 0, s>>>(g.n, P, defer, &ctl->ndefer, d);
         }
         if (so.k > 1) {
             {
                 CC_PROF("k_compress_mid", s);
                 k_shortcut<false><<<gv, TPB, 0, s>>>(P, nullptr, g.n, nullptr, d);
             }
-            CC_PROF("k_kout_rest", s);
-            if (pick1) k_kout_apply_pick<E><<<gv, TPB, 0, s>>>(pick1, g.n, P, d);
-            else launch_kout<OffT, E>(gv, s, I, g.A, g.n, g.m, so.k, so.seed, P, d, 1u, so.k);
+            if (pick1) {
+                CC_PROF("k_kout_apply_pick", s);
+                k_kout_apply_pick<E><<<gv, TPB, 0, s>>>(pick1, g.n, P, d);
+            } else {
+                CC_PROF("k_kout_rest", s);
+                launch_kout<OffT, E>(gv, s, I, g.A, g.n, g.m, so.k, so.kout_rule, so.seed, P, d, 1u, so.k);
+            }
         }
         if (count_into) {
             CC_TRY(cudaMemsetAsync(count_into, 0, (size_t)g.n * 4, s));
@@ -1249,7 +1468,8 @@ cc_status finish_phase(const Graph &g, const cc_finish_opt &fo, const uint32_t *
     CC_TRY(cudaMemsetAsync(&ctl->nchunks, 0, 4, s));
     CC_TRY(cudaMemsetAsync(&ctl->edges, 0, 8, s));
     uint32_t *light = w.sc.at<uint32_t>(w.o_light);
-    if (fo.kind == CC_FINISH_UF_REM_CAS || fo.kind == CC_FINISH_UF_ASYNC) {
+    if (fo.kind == CC_FINISH_UF_REM_CAS || fo.kind == CC_FINISH_UF_ASYNC || fo.kind == CC_FINISH_UF_HOOKS ||
+        fo.kind == CC_FINISH_UF_EARLY) {
         // No vertex skipped: one pass, each undirected edge applied once
         // (from its larger endpoint).  With L_max: the candidate set
         // {u : label[u] != L_max} is fixed first (Algorithm 7's filter),
@@ -1293,16 +1513,23 @@ cc_status finish_phase(const Graph &g, const cc_finish_opt &fo, const uint32_t *
         CC_LAUNCH();
         return CC_OK;
     }
-    // SV / LT-PRF: candidate lists once, then rounds until nothing changes.
-    uint32_t *prev = w.sc.at<uint32_t>(w.o_prev);
+    // SV / LT-PRF and the other min-label finishes: candidate lists once,
+    // then rounds until nothing changes.
     CC_TRY(cudaMemsetAsync(&ctl->nlight, 0, 4, s));
     {
         CC_PROF("k_cand_bin", s);
         k_cand_bin<OffT><<<gv, TPB, 0, s>>>(I, n, g.m, P, lmax_p, light, &ctl->nlight, chunks, &ctl->nchunks,
                                             w.chunk_cap, &ctl->edges, d);
     }
-    CC_TRY(cudaMemcpyAsync(prev, P, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
     CC_LAUNCH();
+    if (fo.kind != CC_FINISH_SV && fo.kind != CC_FINISH_LT_PRF) {
+        MinLabelIn in{g.I,     sizeof(OffT) == 8, g.A,           n,         g.m,          P,
+                      lmax_p,  light,             &ctl->nlight, chunks,    &ctl->nchunks, w.chunk_cap,
+                      &ctl->edges};
+        return minlabel_finish(in, fo, di, d, s, rounds_out);
+    }
+    uint32_t *prev = w.sc.at<uint32_t>(w.o_prev);
+    CC_TRY(cudaMemcpyAsync(prev, P, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
     uint32_t *hchanged = nullptr;
     CC_TRY(cudaMallocHost(&hchanged, 4));
     struct Free {
@@ -1367,11 +1594,12 @@ cc_status run_static(const Graph &g, const cc_sample_opt &so, const cc_finish_op
                      cc_stats *stats, cudaStream_t s) {
     const DeviceInfo *di = device_info();
     if (!di) return CC_ERR_CUDA;
-    const Dev d = make_dev(di, g.n);
+    Dev d = make_dev(di, g.n);
     Work w;
     plan(w, g, so.kind, so.freq_samples, fo.kind, true);
     cc_status st = w.sc.alloc(s);
     if (st != CC_OK) return st;
+    if ((st = attach_hooks(w, d, g.n, s)) != CC_OK) return st;
     CC_TRY(cudaMemsetAsync(w.ctl(), 0, sizeof(Ctl), s));
     int32_t info = 0;
     const bool fused = so.kind == CC_SAMPLE_KOUT && so.freq_samples == 0;
@@ -1396,6 +1624,80 @@ cc_status run_static(const Graph &g, const cc_sample_opt &so, const cc_finish_op
         stats->reserved = 0;
         stats->edges_finish = h.edges;
     }
+    return CC_OK;
+}
+
+// ---------------------------------------------------------------- spanning forest
+// Filter step of the spanning-forest algorithm: the non-empty slots of the
+// sampling and finish edge arrays, appended to out as (u, v) word pairs.
+// A forest has at most n - 1 pairs; more would mean a broken invariant, so
+// slots past n are flagged and not written (out holds n pairs).
+__global__ void __launch_bounds__(256, 8) k_forest_compact(const uint2 *sf, const uint2 *ff, uint32_t n, uint32_t *out,
+                                                           uint32_t *count, Dev d) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint2 ab[2] = {sf[i], ff[i]};
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            if (ab[j].x == NONE) continue;
+            const uint32_t k = append_one(count);
+            if (k >= n) { atomicOr(d.err, ERR_NONCONVERGED); continue; }
+            out[2 * (uint64_t)k] = ab[j].x;
+            out[2 * (uint64_t)k + 1] = ab[j].y;
+        }
+    }
+}
+
+// The spanning-forest algorithm: labels and edge arrays initialised, the
+// sampling emits its tree edges (k-out: the hooking edges; BFS: the tree
+// edge at each child; LDD: the searches' tree edges), IdentifyFrequent, a
+// root-based finish stores each hooking edge at the hooked root, and the
+// non-empty slots are filtered out.  Sampling edges and finish edges live
+// in separate arrays: the sampled clusters are relabelled to their minimum
+// member, which may already hold its own tree edge from the sampling.
+template <typename OffT>
+cc_status run_forest(const Graph &g, const cc_sample_opt &so, const cc_finish_opt &fo, uint32_t *labels,
+                     uint32_t *forest_out, uint64_t *count_out, cudaStream_t s) {
+    const DeviceInfo *di = device_info();
+    if (!di) return CC_ERR_CUDA;
+    Dev d = make_dev(di, g.n);
+    Work w;
+    plan(w, g, so.kind, so.freq_samples, fo.kind, true, true);
+    const size_t o_lab = labels ? 0 : w.sc.reserve((size_t)g.n * 4);
+    cc_status st = w.sc.alloc(s);
+    if (st != CC_OK) return st;
+    if ((st = attach_hooks(w, d, g.n, s)) != CC_OK) return st;
+    uint32_t *P = labels ? labels : w.sc.at<uint32_t>(o_lab);
+    uint2 *sf = w.sc.at<uint2>(w.o_sf), *ff = w.sc.at<uint2>(w.o_ff);
+    uint32_t *fcount = w.sc.at<uint32_t>(w.o_fcount);
+    CC_TRY(cudaMemsetAsync(w.ctl(), 0, sizeof(Ctl), s));
+    CC_TRY(cudaMemsetAsync(sf, 0xFF, (size_t)g.n * 8, s));
+    CC_TRY(cudaMemsetAsync(ff, 0xFF, (size_t)g.n * 8, s));
+    CC_TRY(cudaMemsetAsync(fcount, 0, 8, s));
+    Dev ds = d, df = d;
+    ds.forest = sf;
+    df.forest = ff;
+    int32_t info = 0;
+    const bool fused = so.kind == CC_SAMPLE_KOUT && so.freq_samples == 0;
+    st = sample_phase<OffT>(g, so, fo, P, w, di, ds, s, &info, fused ? w.sc.at<uint32_t>(w.o_counts) : nullptr);
+    if (st != CC_OK) return st;
+    const uint32_t *lmax_p = nullptr;
+    if (so.kind != CC_SAMPLE_NONE) {
+        st = identify_phase(P, g.n, so.freq_samples, so.seed, &w.ctl()->lmax, w, di, d, s, true, fused);
+        if (st != CC_OK) return st;
+        lmax_p = &w.ctl()->lmax;
+    }
+    st = finish_phase<OffT>(g, fo, lmax_p, P, w, di, df, s, nullptr);
+    if (st != CC_OK) return st;
+    {
+        CC_PROF("k_forest_compact", s);
+        k_forest_compact<<<grid_for(di, g.n, TPB), TPB, 0, s>>>(sf, ff, g.n, forest_out, fcount, d);
+    }
+    CC_LAUNCH();
+    uint32_t hc = 0;
+    CC_TRY(cudaMemcpyAsync(&hc, fcount, 4, cudaMemcpyDeviceToHost, s));
+    CC_TRY(cudaStreamSynchronize(s));
+    *count_out = hc < g.n ? hc : g.n;
     return CC_OK;
 }
 
@@ -1426,7 +1728,7 @@ cc_status bfs_capped(const Graph &g, uint32_t src, uint32_t cap, uint32_t *P, Wo
         const int nx = cur ^ 1;
         CC_TRY(cudaMemsetAsync(&ctl->nfront[nx], 0, 4, s));
         CC_TRY(cudaMemsetAsync(&ctl->nchunks, 0, 4, s));
-        BFSEdge f{P, vis, q[nx], &ctl->nfront[nx], &ctl->minv, src, NONE};
+        BFSEdge f{P, vis, q[nx], &ctl->nfront[nx], &ctl->minv, src, NONE, d.forest};
         {
             CC_PROF("k_list_bin", s);
             k_list_bin<OffT, BFSEdge><<<gv, TPB, 0, s>>>(I, g.A, n, g.m, q[cur], &ctl->nfront[cur], f, chunks,
@@ -1551,6 +1853,34 @@ cc_status cc_static(const void *offsets, int offsets_u64, const uint32_t *edges,
     return cc_static_ex(offsets, offsets_u64, edges, n, m, sample, finish, labels_out, nullptr, stream);
 }
 
+cc_status cc_spanning_forest(const void *offsets, int offsets_u64, const uint32_t *edges, uint32_t n, uint64_t m,
+                             const cc_sample_opt *sample, const cc_finish_opt *finish, uint32_t *forest_out,
+                             uint64_t *count_out, uint32_t *labels_out, void *stream) {
+    cc_status st = check_graph(offsets, offsets_u64, edges, n, m);
+    if (st != CC_OK) return st;
+    cc_sample_opt so;
+    cc_finish_opt fo;
+    resolve_opts(sample, finish, so, fo);
+    if ((st = check_sample(so)) != CC_OK || (st = check_finish(fo)) != CC_OK) return st;
+    // root-based union-find finishes only (not SV / Liu-Tarjan / Stergiou /
+    // label propagation, not Rem with SpliceAtomic)
+    if (fo.kind != CC_FINISH_UF_REM_CAS && fo.kind != CC_FINISH_UF_ASYNC && fo.kind != CC_FINISH_UF_HOOKS &&
+        fo.kind != CC_FINISH_UF_EARLY)
+        return CC_ERR_UNSUPPORTED;
+    if (fo.kind == CC_FINISH_UF_REM_CAS && fo.splice == CC_SPLICE_ATOMIC) return CC_ERR_UNSUPPORTED;
+    if (!count_out) return CC_ERR_INVALID;
+    if (n > 0 && (!forest_out || !aligned(forest_out, 4))) return CC_ERR_INVALID;
+    if (labels_out && !aligned(labels_out, 4)) return CC_ERR_INVALID;
+    *count_out = 0;
+    if (n == 0) return CC_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Graph g{offsets, offsets_u64 != 0, edges, n, m};
+    st = offsets_u64 ? run_forest<uint64_t>(g, so, fo, labels_out, forest_out, count_out, s)
+                     : run_forest<uint32_t>(g, so, fo, labels_out, forest_out, count_out, s);
+    if (st != CC_OK) return st;
+    return cc_device_error(stream, nullptr);
+}
+
 cc_status cc_static_host(const void *offsets, int offsets_u64, const uint32_t *edges, uint32_t n, uint64_t m,
                          const cc_sample_opt *sample, const cc_finish_opt *finish, uint32_t *labels_out,
                          void *stream) {
@@ -1592,7 +1922,8 @@ cc_status cc_sample(const void *offsets, int offsets_u64, const uint32_t *edges,
     if ((st = w.sc.alloc(s)) != CC_OK) return st;
     CC_TRY(cudaMemsetAsync(w.ctl(), 0, sizeof(Ctl), s));
     int32_t info = 0;
-    const Dev d = make_dev(di, n);
+    Dev d = make_dev(di, n);
+    if ((st = attach_hooks(w, d, n, s)) != CC_OK) return st;
     st = offsets_u64 ? sample_phase<uint64_t>(g, so, fo, labels_out, w, di, d, s, &info, nullptr)
                      : sample_phase<uint32_t>(g, so, fo, labels_out, w, di, d, s, &info, nullptr);
     if (st != CC_OK) return st;
@@ -1644,7 +1975,8 @@ cc_status cc_finish(const void *offsets, int offsets_u64, const uint32_t *edges,
     Work w;
     plan(w, g, CC_SAMPLE_NONE, 1, fo.kind, true);
     if ((st = w.sc.alloc(s)) != CC_OK) return st;
-    const Dev d = make_dev(di, n);
+    Dev d = make_dev(di, n);
+    if ((st = attach_hooks(w, d, n, s)) != CC_OK) return st;
     CC_TRY(cudaMemsetAsync(w.ctl(), 0, sizeof(Ctl), s));
     {
         CC_PROF("k_check_forest", s);

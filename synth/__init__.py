@@ -367,3 +367,18 @@ def selector_graph(i: int, seed: int = 1, scale_lo: int = 14, scale_hi: int = 22
     cnt = max(1, n // 34)
     sz = (4 + (hash3(gseed, 710, torch.arange(cnt, dtype=torch.int64)) % 61)).tolist()
     return cliques_fast(sz, device=device)
+
+
+def edge_weights(g: CSR, seed: int = 1) -> torch.Tensor:
+    """float32[m] weights for g's CSR entries, exponential with mean 1 (the
+    paper's weighted inputs draw exponential weights with a constant mean),
+    equal on both stored copies of an undirected edge: the draw hashes
+    (min(u, v), max(u, v))."""
+    off = g.offsets
+    src = torch.repeat_interleave(torch.arange(g.n, dtype=torch.int64, device=off.device), off[1:] - off[:-1])
+    dst = g.edges.to(torch.int64)
+    key = torch.minimum(src, dst) * (1 << 32) + torch.maximum(src, dst)
+    del src, dst
+    h = hash3(seed, 41, key).to(torch.float64)
+    u = (h + 0.5) / 2.0**32
+    return (-torch.log(u)).to(torch.float32)

@@ -79,8 +79,19 @@ def test_validation_rejects_before_any_device_work():
     assert _call_static(8, 0, 6, 10, 5, labels=16) == 1           # edges not 4-aligned
     assert _call_static(8, 0, 8, 10, 5, labels=18) == 1           # labels not 4-aligned
     res = cc.sample_opt()
-    res.reserved = 3
+    res.kout_rule = 3                                              # no such k-out rule
     assert _call_static(8, 0, 8, 10, 5, so=res, labels=1) == 1
+    rem_compress = cc.finish_opt("uf_rem_cas", "compress")          # Rem's Compress excludes FindCompress
+    assert _call_static(8, 0, 8, 10, 5, fo=rem_compress, labels=1) == 1
+    for bad in (cc.FinishOpt(9, 0, 0, 0), cc.FinishOpt(0, 4, 0, 0), cc.FinishOpt(0, 0, 3, 0),
+                cc.FinishOpt(0, 0, 0, 1),                      # Liu-Tarjan rules on a union-find kind
+                cc.finish_opt("liu_tarjan", lt_rules=0),       # Connect without Alter
+                cc.finish_opt("liu_tarjan", lt_rules=2 | 4),   # ExtendedConnect with RootUpdate
+                cc.finish_opt("liu_tarjan", lt_rules=3),       # no such connect rule
+                cc.finish_opt("liu_tarjan", lt_rules=32)):     # unknown bit
+        assert _call_static(8, 0, 8, 10, 5, fo=bad, labels=1) == 1
+    for name in cc.LT_VARIANTS:                               # the sixteen variants pass validation
+        assert _call_static(8, 0, 8, 0, 0, fo=cc.finish_opt(name), labels=1) == 0
 
 
 def test_empty_graph_is_a_no_op():

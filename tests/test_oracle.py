@@ -580,3 +580,63 @@ def test_spanning_forest_workload_shapes():
         F = oracle.spanning_forest(off, edg)
         assert len(F) == links == g.n - int((lab == np.arange(g.n)).sum())
         assert oracle.check_forest(off, edg, F, lab) == 0
+
+
+# ---------------------------------------------------------------- minimum spanning forests
+def scipy_msf_weight(g, w):
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import minimum_spanning_tree
+    off, edg = g.numpy()
+    A = csr_matrix((np.asarray(w, dtype=np.float64), edg, off), shape=(g.n, g.n))
+    return float(minimum_spanning_tree(A).sum())
+
+
+def test_kruskal_matches_scipy_and_brute_force():
+    for g in (synth.rmat(11, 8, seed=2), synth.grid2d(40, 30, 0.2, seed=1), synth.erdos_renyi(3000, 1.5, seed=3)):
+        w = synth.edge_weights(g, 5).numpy()
+        F, W = oracle.msf_kruskal(*g.numpy(), w)
+        assert abs(W - scipy_msf_weight(g, w)) <= 1e-9 * max(W, 1.0)
+        assert oracle.check_forest(*g.numpy(), F) == 0
+    # brute force: the lightest acyclic edge set of size n - #components
+    rng = np.random.default_rng(11)
+    for t in range(60):
+        n = int(rng.integers(2, 7))
+        allp = list(itertools.combinations(range(n), 2))
+        pairs = [p for p in allp if rng.random() < 0.6]
+        if not pairs:
+            continue
+        g = synth.from_edge_list(n, pairs)
+        wd = {frozenset(p): float(np.float32(rng.random() + 0.01)) for p in pairs}
+        off, edg = g.numpy()
+        src = np.repeat(np.arange(n), np.diff(off))
+        w = np.array([wd[frozenset((int(a), int(b)))] for a, b in zip(src, edg)], dtype=np.float32)
+        k = n - len(np.unique(closure_labels(n, pairs)))
+        best = min(sum(wd[frozenset(p)] for p in sub) for sub in itertools.combinations(pairs, k)
+                   if len(np.unique(closure_labels(n, list(sub)))) == n - k)
+        _, W = oracle.msf_kruskal(off, edg, w)
+        assert abs(W - best) <= 1e-6
+
+
+@pytest.mark.parametrize("eps", [0.01, 0.25, 1.0, 4.0])
+def test_amsf_within_its_bound(eps):
+    for g in (synth.rmat(11, 8, seed=4), synth.grid2d(50, 40, 0.3, seed=2)):
+        off, edg = g.numpy()
+        w = synth.edge_weights(g, 9).numpy()
+        _, opt = oracle.msf_kruskal(off, edg, w)
+        F, W = oracle.amsf(off, edg, w, eps)
+        assert oracle.check_forest(off, edg, F) == 0
+        assert opt * (1 - 1e-9) <= W <= (1 + eps) * opt * (1 + 1e-9)
+
+
+def test_amsf_closed_forms():
+    g = synth.rmat(10, 8, seed=7)
+    off, edg = g.numpy()
+    w = synth.edge_weights(g, 2).numpy()
+    # buckets thinner than any weight gap: Kruskal's order, the exact weight
+    _, opt = oracle.msf_kruskal(off, edg, w)
+    _, W = oracle.amsf(off, edg, w, 1e-9)
+    assert abs(W - opt) <= 1e-9 * opt
+    # equal weights: every spanning forest is minimum, one bucket
+    ones = np.ones(g.m, np.float32)
+    F, W = oracle.amsf(off, edg, ones, 0.25)
+    assert W == len(F) == oracle.cc_uf(off, edg)[1]

@@ -15,8 +15,14 @@ pytestmark = pytest.mark.gpu
 SAMPLES = ["none", "kout", "bfs", "ldd"]
 UF_VARIANTS = [("uf_rem_cas", "naive", "split_one"), ("uf_rem_cas", "naive", "halve_one"),
                ("uf_rem_cas", "split", "split_one"), ("uf_rem_cas", "halve", "halve_one"),
+               ("uf_rem_cas", "naive", "atomic"), ("uf_rem_cas", "split", "atomic"),
+               ("uf_rem_cas", "halve", "atomic"),
                ("uf_async", "naive", "split_one"), ("uf_async", "split", "split_one"),
-               ("uf_async", "halve", "split_one")]
+               ("uf_async", "halve", "split_one"), ("uf_async", "compress", "split_one"),
+               ("uf_hooks", "naive", "split_one"), ("uf_hooks", "split", "split_one"),
+               ("uf_hooks", "halve", "split_one"), ("uf_hooks", "compress", "split_one"),
+               ("uf_early", "naive", "split_one"), ("uf_early", "split", "split_one"),
+               ("uf_early", "halve", "split_one"), ("uf_early", "compress", "split_one")]
 FINISHES = UF_VARIANTS + [("sv", "naive", "split_one"), ("lt_prf", "naive", "split_one")]
 
 
@@ -99,12 +105,30 @@ def test_medium_graphs_and_work_counts(sample, fin):
 
 
 @pytest.mark.parametrize("k", [1, 2, 3, 5])
-def test_kout_sampled_labels_bit_exact(k):
+@pytest.mark.parametrize("rule", ["hybrid", "afforest", "pure"])
+def test_kout_sampled_labels_bit_exact(k, rule):
     for g in (synth.rmat(15, 8, seed=2), synth.grid2d(300, 200, 0.3, seed=3)):
         off, edg = on_gpu(g)
-        lab, info = cc.cc_sample(off, edg, cc.sample_opt("kout", k=k, seed=77))
-        want = oracle.kout_sample(*g.numpy(), k=k, seed=77)
+        lab, info = cc.cc_sample(off, edg, cc.sample_opt("kout", k=k, seed=77, kout_rule=rule))
+        want = oracle.kout_sample(*g.numpy(), k=k, seed=77, rule=rule)
         assert np.array_equal(lab.cpu().numpy().view(np.uint32), want)
+
+
+@pytest.mark.parametrize("rule", ["afforest", "pure"])
+@pytest.mark.parametrize("fin", [("uf_rem_cas", "naive", "split_one"), ("uf_hooks", "compress", "split_one"),
+                                 ("uf_early", "halve", "split_one"), ("sv", "naive", "split_one")],
+                         ids=lambda f: f[0])
+def test_kout_rules_full_pipeline(rule, fin):
+    """Each rule through sampling, IdentifyFrequent and the finish: the
+    oracle's L_max, finish edge count and labels."""
+    for g in (synth.rmat(17, 16, seed=4), synth.grid2d(500, 400, 0.3, seed=2)):
+        off, edg = g.numpy()
+        want, ost = oracle.connectivity(off, edg, "kout", fin[0], k=2, seed=13, kout_rule=rule)
+        got, st = gpu_labels(g, "kout", fin, seed=13, kout_rule=rule)
+        assert np.array_equal(got, want), (g.name, rule, fin)
+        assert st["lmax"] == ost["lmax"]
+        sampled = oracle.kout_sample(off, edg, 2, 13, rule=rule)
+        assert st["edges_finish"] == int(np.diff(off)[sampled != ost["lmax"]].sum())
 
 
 @pytest.mark.parametrize("tries,seed", [(3, 1), (1, 2), (3, 7)])
@@ -115,6 +139,21 @@ def test_bfs_sampled_labels_bit_exact(tries, seed):
         want, t = oracle.bfs_sample(*g.numpy(), tries=tries, seed=seed)
         assert info == t
         assert np.array_equal(lab.cpu().numpy().view(np.uint32), want)
+
+
+def test_bfs_long_paths_run_many_persistent_launches():
+    """High-diameter inputs keep the top-down levels in the persistent launch;
+    a path longer than its per-launch level cap (65536) continues across
+    launches.  Labels and the successful try match the oracle."""
+    for g in (synth.path(150001), synth.grid2d(700, 650, 0.0), synth.grid2d(900, 800, 0.4, seed=7)):
+        off, edg = on_gpu(g)
+        lab, info = cc.cc_sample(off, edg, cc.sample_opt("bfs", bfs_tries=3, seed=2))
+        want, t = oracle.bfs_sample(*g.numpy(), tries=3, seed=2)
+        assert info == t
+        assert np.array_equal(lab.cpu().numpy().view(np.uint32), want)
+        full, _ = gpu_labels(g, "bfs", seed=2)
+        assert np.array_equal(full, oracle.cc_uf(*g.numpy())[0])
+    assert cc.device_error() == 0
 
 
 def test_bfs_sample_retries_and_fallback():
