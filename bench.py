@@ -57,6 +57,8 @@ def parse():
     p.add_argument("--no-incr", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-forest", action="store_true")
+    p.add_argument("--no-amsf", action="store_true")
+    p.add_argument("--amsf-eps", type=float, default=0.25)
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--combos", action="store_true", help="also time every sampling x finish combination")
     p.add_argument("--matrix", action="store_true",
@@ -179,21 +181,30 @@ def make_graph(scale, ef, device):
     return synth.rmat(scale, ef, seed=1, device=device)
 
 
+SECTOR = 32   # bytes: the DRAM access granule of a random 4-byte read
+
+
 def algorithmic_bytes(kernel, n, m, m_finish, n_nz, k, off_bytes):
-    """Compulsory bytes of one launch of `kernel`, counted at word
-    granularity: offsets `off_bytes` per vertex, edges 4 B, parent / label
-    words 4 B.  n_nz: vertices with at least one edge; m_finish: edges out of
-    vertices whose sampled label is not L_max."""
+    """Compulsory bytes of one launch of `kernel`.  Streams (offsets, labels,
+    edge ranges) count at word granularity: offsets `off_bytes` per vertex,
+    edges, parent and label words 4 B.  A random read into the edge array
+    (8.4 GB, no reuse) counts as the 32-byte sector it must bring in (the
+    per-vertex figure of the sampled variants: about k sectors per vertex
+    for k picked edges); random parent reads count 4 B, as the parent array
+    is hot in L2.  n_nz: vertices with at least one edge; m_finish: edges
+    out of vertices whose sampled label is not L_max."""
     ob = off_bytes
     table = {
         "k_iota": 4 * n,                                            # write P
-        # offsets, first edge and (k = 2) random pick of each non-isolated
-        # vertex, write P and the stashed pick
-        "k_kout_hook_first": ob * (n + 1) + 8 * n_nz + 8 * n,
-        # stashed pick, own parent, picked vertex's parent
+        # offsets; the first edge and (k = 2) the random pick of each
+        # non-isolated vertex, one random sector each; write P and the
+        # stashed pick
+        "k_kout_hook_first": ob * (n + 1) + min(k, 2) * SECTOR * n_nz + 8 * n,
+        # stashed pick and own parent (streams), the picked vertex's parent
         "k_kout_apply_pick": 8 * n + 4 * n_nz,
-        # offsets, (k-1) picked edges, own parent and picked parent per pick
-        "k_kout_rest": ob * (n + 1) + n_nz * (k - 1) * (4 + 4 + 4),
+        # offsets, own parent, (k-1) picked edges (random sectors) and their
+        # parents
+        "k_kout_rest": ob * (n + 1) + n_nz * (k - 1) * (SECTOR + 4) + 4 * n,
         "k_compress_mid": 8 * n,                                    # read + write P
         "k_compress_count": 8 * n,
         "k_compress": 8 * n,
@@ -370,6 +381,9 @@ def run_ours(args):
     if args.matrix:
         out["matrix"] = bench_matrix(args, cc, synth, dev)
 
+    if not args.no_amsf:
+        out["amsf"] = bench_amsf(args, cc, synth, g, dev, ncomp)
+
     if not args.no_batched:
         out["batched"] = bench_batched(args, cc, synth, dev)
 
@@ -402,6 +416,29 @@ def bench_combos(args, cc, off, edg, labels, ref, m):
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / reps
             res[f"{s}+{f}"] = {"ms": round(ms, 3), "gedges_s": round(m / (ms * 1e-3) / 1e9, 2), "exact": same}
+    return res
+
+
+def bench_amsf(args, cc, synth, g, dev, ncomp):
+    """Approximate MSF (Section 5.1) on the benchmark graph with exponential
+    weights (mean 1, the paper's weighted inputs), eps from --amsf-eps: each
+    mode once after one untimed call, with the forest size checked."""
+    import torch
+    w = synth.edge_weights(g, 1).to(dev)
+    buf = torch.empty(2 * g.n, dtype=torch.int32, device=dev)
+    res = {"eps": args.amsf_eps, "weights": "exponential, mean 1"}
+    for mode in ("nf_s", "coo", "nf"):
+        pairs, wt, _ = cc.cc_amsf(g.offsets, g.edges, w, args.amsf_eps, mode, forest_out=buf)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        pairs, wt, _ = cc.cc_amsf(g.offsets, g.edges, w, args.amsf_eps, mode, forest_out=buf)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        res[mode] = {"ms": round(ms, 3), "gedges_s": round(g.m / (ms * 1e-3) / 1e9, 2), "forest_edges": pairs.shape[0],
+                     "size_ok": pairs.shape[0] == g.n - ncomp, "weight": round(wt, 3)}
+    del w, buf
+    torch.cuda.empty_cache()
     return res
 
 

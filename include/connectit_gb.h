@@ -161,6 +161,31 @@ cc_status cc_spanning_forest(const void *offsets, int offsets_u64, const uint32_
                              uint64_t m, const cc_sample_opt *sample, const cc_finish_opt *finish,
                              uint32_t *forest_out, uint64_t *count_out, uint32_t *labels_out, void *stream);
 
+/* Approximate minimum spanning forest (Section 5.1): edge weights are
+ * bucketed by ratio 1 + epsilon from the smallest weight, buckets are taken
+ * lightest first, and each adds a spanning forest of its edges over the
+ * connectivity of the lighter buckets (UF-Rem-CAS, SplitAtomicOne,
+ * FindNaive).  The forest weighs at most (1 + epsilon) times a minimum
+ * spanning forest (up to float rounding of the bucket bounds, about 1e-7
+ * relative).
+ * weights: device float[m], positive and finite, equal on both stored
+ *   copies of an edge (other weights are skipped and flagged
+ *   CC_DEVERR_BAD_EDGE).
+ * epsilon in [1e-3, 64]; more than CC_AMSF_MAX_BUCKETS buckets between the
+ *   smallest and largest weight: CC_ERR_INVALID.
+ * mode: CC_AMSF_NF (every bucket reads the whole CSR), CC_AMSF_NF_S (the
+ *   same, skipping the vertices of the largest component so far),
+ *   CC_AMSF_COO (edges grouped by bucket first, each read once).
+ * forest_out: device uint32[2*n] (room for n pairs), *count_out pairs;
+ *   *weight_out: their total weight (host double).  labels_out: optional
+ *   device uint32[n], canonical labels.  Synchronises the stream; returns
+ *   the device error status. */
+#define CC_AMSF_MAX_BUCKETS 65536
+enum { CC_AMSF_NF = 0, CC_AMSF_NF_S = 1, CC_AMSF_COO = 2 };
+cc_status cc_amsf(const void *offsets, int offsets_u64, const uint32_t *edges, const float *weights, uint32_t n,
+                  uint64_t m, float epsilon, int mode, uint32_t *forest_out, uint64_t *count_out,
+                  double *weight_out, uint32_t *labels_out, void *stream);
+
 /* cc_static on HOST buffers (offsets, edges, labels_out in host memory,
  * ideally pinned): copies the graph to library-allocated device memory,
  * runs cc_static, copies the labels back and synchronises.  Returns the

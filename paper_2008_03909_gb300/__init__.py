@@ -92,6 +92,10 @@ _SIGS = {
                                           ctypes.c_uint64, ctypes.POINTER(SampleOpt), ctypes.POINTER(FinishOpt),
                                           ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64), ctypes.c_void_p,
                                           ctypes.c_void_p]),
+    "cc_amsf": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32,
+                               ctypes.c_uint64, ctypes.c_float, ctypes.c_int, ctypes.c_void_p,
+                               ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double), ctypes.c_void_p,
+                               ctypes.c_void_p]),
     "cc_static_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint32,
                                       ctypes.c_uint64, ctypes.POINTER(SampleOpt), ctypes.POINTER(FinishOpt),
                                       ctypes.c_void_p, ctypes.c_void_p]),
@@ -264,6 +268,33 @@ def cc_spanning_forest(offsets, edges, sample: SampleOpt | None = None, finish: 
                                     ctypes.c_void_p(labels_out.data_ptr() if labels_out is not None else 0),
                                     _stream(stream)), "cc_spanning_forest")
     return forest_out[: 2 * cnt.value].view(-1, 2), labels_out
+
+
+AMSF_MODE = {"nf": 0, "nf_s": 1, "coo": 2}
+
+
+def cc_amsf(offsets, edges, weights, epsilon: float = 0.25, mode: str = "nf_s", forest_out=None, labels_out=None,
+            stream=None):
+    """Approximate minimum spanning forest: (pairs int32[count, 2] view of
+    forest_out, total weight, labels or None)."""
+    Ip, u64, Ap, n, m = _graph_args(offsets, edges)
+    _dev(weights, (torch.float32,), "weights")
+    if weights.numel() != m:
+        raise ValueError("weights needs one value per CSR entry")
+    if forest_out is None:
+        forest_out = torch.empty(2 * max(n, 1), dtype=torch.int32, device=offsets.device)
+    _dev(forest_out, (torch.int32,), "forest_out")
+    if forest_out.numel() < 2 * n:
+        raise ValueError("forest_out needs room for 2 * n values")
+    if labels_out is not None:
+        _dev(labels_out, (torch.int32,), "labels_out")
+    cnt, wt = ctypes.c_uint64(0), ctypes.c_double(0.0)
+    _check(lib().cc_amsf(Ip, u64, Ap, ctypes.c_void_p(weights.data_ptr() if m else 0), n, m, epsilon,
+                         AMSF_MODE[mode] if isinstance(mode, str) else mode, ctypes.c_void_p(forest_out.data_ptr()),
+                         ctypes.byref(cnt), ctypes.byref(wt),
+                         ctypes.c_void_p(labels_out.data_ptr() if labels_out is not None else 0), _stream(stream)),
+           "cc_amsf")
+    return forest_out[: 2 * cnt.value].view(-1, 2), wt.value, labels_out
 
 
 def cc_static_host(offsets: torch.Tensor, edges: torch.Tensor, sample=None, finish=None,

@@ -226,7 +226,8 @@ __device__ __forceinline__ uint32_t find_from(uint32_t *P, uint32_t x, uint32_t 
 // the sense of the spanning-forest appendix: a link hooks a root exactly
 // once, so when d.forest is set the hooking edge (u, v) is stored at the
 // hooked root's slot.  pu = P[u] and pv = P[v] are passed in already loaded
-// (callers batch those loads); pu == pv means nothing to do.
+// (callers batch those loads); pu == pv means nothing to do.  unite returns
+// the root it hooked, or NONE when the two were already in one tree.
 
 // UF-Async (Algorithm 10; the CAS is on the larger root's own slot): find
 // both roots, CAS the larger root under the smaller, retry from the current
@@ -234,7 +235,7 @@ __device__ __forceinline__ uint32_t find_from(uint32_t *P, uint32_t x, uint32_t 
 template <int FIND>
 struct UnionAsync {
     static constexpr int find_kind = FIND;
-    __device__ static __forceinline__ bool unite(uint32_t *P, uint32_t u, uint32_t v, uint32_t pu,
+    __device__ static __forceinline__ uint32_t unite(uint32_t *P, uint32_t u, uint32_t v, uint32_t pu,
                                                  uint32_t pv, const Dev &d) {
         uint32_t ru = find_from<FIND>(P, u, pu, d);
         uint32_t rv = find_from<FIND>(P, v, pv, d);
@@ -244,13 +245,13 @@ struct UnionAsync {
             uint32_t old = atomicCAS(P + ru, ru, rv);
             if (old == ru) {
                 if (d.forest) d.forest[ru] = make_uint2(u, v);
-                return true;
+                return ru;
             }
             ru = find_from<FIND>(P, ru, old, d);
             rv = find_from<FIND>(P, rv, ld_rel(P + rv), d);
-            if (!g.step(d)) return false;
+            if (!g.step(d)) return NONE;
         }
-        return false;
+        return NONE;
     }
 };
 
@@ -262,7 +263,7 @@ struct UnionAsync {
 template <int FIND>
 struct UnionHooks {
     static constexpr int find_kind = FIND;
-    __device__ static __forceinline__ bool unite(uint32_t *P, uint32_t u, uint32_t v, uint32_t pu,
+    __device__ static __forceinline__ uint32_t unite(uint32_t *P, uint32_t u, uint32_t v, uint32_t pu,
                                                  uint32_t pv, const Dev &d) {
         uint32_t ru = find_from<FIND>(P, u, pu, d);
         uint32_t rv = find_from<FIND>(P, v, pv, d);
@@ -275,7 +276,7 @@ struct UnionHooks {
                 if (h == NONE) {
                     st_rel(P + ru, rv);
                     if (d.forest) d.forest[ru] = make_uint2(u, v);
-                    return true;
+                    return ru;
                 }
                 // claimed by another union whose store may not be visible
                 // yet: continue from the parent it is about to write
@@ -283,9 +284,9 @@ struct UnionHooks {
             }
             ru = find_from<FIND>(P, pr, ld_rel(P + pr), d);
             rv = find_from<FIND>(P, rv, ld_rel(P + rv), d);
-            if (!g.step(d)) return false;
+            if (!g.step(d)) return NONE;
         }
-        return false;
+        return NONE;
     }
 };
 
@@ -297,19 +298,19 @@ struct UnionHooks {
 template <int FIND>
 struct UnionEarly {
     static constexpr int find_kind = FIND;
-    __device__ static __forceinline__ bool unite(uint32_t *P, uint32_t u, uint32_t v, uint32_t pu,
+    __device__ static __forceinline__ uint32_t unite(uint32_t *P, uint32_t u, uint32_t v, uint32_t pu,
                                                  uint32_t pv, const Dev &d) {
         uint32_t ru = pu, rv = pv;
-        bool linked = false;
+        uint32_t linked = NONE;
         Guard g;
         while (ru != rv) {
-            if (!g.step(d)) return false;
+            if (!g.step(d)) return NONE;
             if (ru < rv) { uint32_t t = ru; ru = rv; rv = t; }
             const uint32_t z = ld_rel(P + ru);
             if (z == ru) {
                 if (atomicCAS(P + ru, ru, rv) == ru) {
                     if (d.forest) d.forest[ru] = make_uint2(u, v);
-                    linked = true;
+                    linked = ru;
                     break;
                 }
                 continue;   // linked by another thread: no longer a root
@@ -339,7 +340,7 @@ struct UnionEarly {
 template <int SPLICE, int FIND>
 struct UnionRem {
     static constexpr int find_kind = FIND;
-    __device__ static __forceinline__ bool unite(uint32_t *P, uint32_t u, uint32_t v, uint32_t pu,
+    __device__ static __forceinline__ uint32_t unite(uint32_t *P, uint32_t u, uint32_t v, uint32_t pu,
                                                  uint32_t pv, const Dev &d) {
         uint32_t ru = u, rv = v, pru = pu, prv = pv;
         Guard g;
@@ -356,7 +357,7 @@ struct UnionRem {
                         find_from<FIND>(P, u, ld_rel(P + u), d);
                         find_from<FIND>(P, v, ld_rel(P + v), d);
                     }
-                    return true;
+                    return ru;
                 }
                 pru = old;
             } else if (SPLICE == SPLICE_SPLIT_ONE) {
@@ -378,9 +379,9 @@ struct UnionRem {
                     ru = pru;
                 }
             }
-            if (!g.step(d)) return false;
+            if (!g.step(d)) return NONE;
         }
-        return false;
+        return NONE;
     }
 };
 

@@ -1005,7 +1005,7 @@ void plan(Work &w, const Graph &g, int sample_kind, uint32_t freq_samples, int f
         w.o_hooks = w.sc.reserve(n * 4);
     }
     if (forest) {
-        w.o_sf = w.sc.reserve(n * 8);
+        if (sample_kind == CC_SAMPLE_BFS || sample_kind == CC_SAMPLE_LDD) w.o_sf = w.sc.reserve(n * 8);
         w.o_ff = w.sc.reserve(n * 8);
         w.o_fcount = w.sc.reserve(8);
         if (sample_kind == CC_SAMPLE_LDD) w.o_stamp = w.sc.reserve(n * 4);
@@ -1648,6 +1648,21 @@ __global__ void __launch_bounds__(256, 8) k_forest_compact(const uint2 *sf, cons
     }
 }
 
+// The same filter when every hooked root ends as a non-root and nothing
+// else does: slot v holds an edge exactly when label[v] != v.
+__global__ void __launch_bounds__(256, 8) k_forest_compact_hooked(const uint2 *ff, const uint32_t *L, uint32_t n,
+                                                                  uint32_t *out, uint32_t *count, Dev d) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        if (L[i] == (uint32_t)i) continue;
+        const uint2 e = ff[i];
+        const uint32_t k = append_one(count);
+        if (k >= n) { atomicOr(d.err, ERR_NONCONVERGED); continue; }
+        out[2 * (uint64_t)k] = e.x;
+        out[2 * (uint64_t)k + 1] = e.y;
+    }
+}
+
 // The spanning-forest algorithm: labels and edge arrays initialised, the
 // sampling emits its tree edges (k-out: the hooking edges; BFS: the tree
 // edge at each child; LDD: the searches' tree edges), IdentifyFrequent, a
@@ -1668,11 +1683,19 @@ cc_status run_forest(const Graph &g, const cc_sample_opt &so, const cc_finish_op
     if (st != CC_OK) return st;
     if ((st = attach_hooks(w, d, g.n, s)) != CC_OK) return st;
     uint32_t *P = labels ? labels : w.sc.at<uint32_t>(o_lab);
-    uint2 *sf = w.sc.at<uint2>(w.o_sf), *ff = w.sc.at<uint2>(w.o_ff);
+    // k-out and no sampling hook roots in one union-find from start to end:
+    // one edge array, and a slot is filled exactly when its vertex ends as a
+    // non-root, so the array needs no clearing.  BFS / LDD tree edges sit at
+    // children, which the relabelling to the smallest member can also make
+    // hooked roots, so they take a second, cleared array.
+    const bool one = so.kind == CC_SAMPLE_KOUT || so.kind == CC_SAMPLE_NONE;
+    uint2 *ff = w.sc.at<uint2>(w.o_ff), *sf = one ? ff : w.sc.at<uint2>(w.o_sf);
     uint32_t *fcount = w.sc.at<uint32_t>(w.o_fcount);
     CC_TRY(cudaMemsetAsync(w.ctl(), 0, sizeof(Ctl), s));
-    CC_TRY(cudaMemsetAsync(sf, 0xFF, (size_t)g.n * 8, s));
-    CC_TRY(cudaMemsetAsync(ff, 0xFF, (size_t)g.n * 8, s));
+    if (!one) {
+        CC_TRY(cudaMemsetAsync(sf, 0xFF, (size_t)g.n * 8, s));
+        CC_TRY(cudaMemsetAsync(ff, 0xFF, (size_t)g.n * 8, s));
+    }
     CC_TRY(cudaMemsetAsync(fcount, 0, 8, s));
     Dev ds = d, df = d;
     ds.forest = sf;
@@ -1689,7 +1712,10 @@ cc_status run_forest(const Graph &g, const cc_sample_opt &so, const cc_finish_op
     }
     st = finish_phase<OffT>(g, fo, lmax_p, P, w, di, df, s, nullptr);
     if (st != CC_OK) return st;
-    {
+    if (one) {
+        CC_PROF("k_forest_compact", s);
+        k_forest_compact_hooked<<<grid_for(di, g.n, TPB), TPB, 0, s>>>(ff, P, g.n, forest_out, fcount, d);
+    } else {
         CC_PROF("k_forest_compact", s);
         k_forest_compact<<<grid_for(di, g.n, TPB), TPB, 0, s>>>(sf, ff, g.n, forest_out, fcount, d);
     }
