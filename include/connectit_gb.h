@@ -284,9 +284,13 @@ cc_status cc_batched_autotune(const uint64_t *gv, uint32_t G, const void *offset
  * A handle owns a resident parent array P (n uint32 in device memory).
  * cc_incr_create runs Initialize: static connectivity of the base graph
  *   (offsets/edges device pointers; both may be NULL when m == 0) into P.
- *   Finish kinds: the union-find ones (SV / LT batches: CC_ERR_UNSUPPORTED).
+ *   Finish kinds: the union-find ones (Section 3.5's types 1 and 3) and SV
+ *   / Liu-Tarjan PRF (type 2); the Liu-Tarjan rule sets, Stergiou and
+ *   label propagation return CC_ERR_UNSUPPORTED.
  * cc_incr_insert_batch: Insert(u, v) for k pairs (device uint32[2k],
- *   interleaved u0 v0 u1 v1 ...), each a Union.
+ *   interleaved u0 v0 u1 v1 ...), each a Union; with SV / PRF the batch's
+ *   pairs go through that finish's rounds (hooks, full shortcut) until a
+ *   round changes nothing, and the call synchronises once per round.
  * cc_incr_query_batch: IsConnected(u, v) for q pairs -> answers_out (device
  *   uint8[q], 1 = connected).  A query sees every insert enqueued earlier on
  *   the handle (inserts and queries are separate phases, the

@@ -1,10 +1,12 @@
 // cc_incr.cu -- batch-incremental connectivity (Section 3.5, Algorithm 3,
-// Appendix B.4).  A handle keeps the union-find parent array P resident in
-// device memory.  Initialize runs static connectivity on the base graph
-// into P; each batch's inserts are Unions (the handle's union-find engine)
-// and its queries compare the roots of both endpoints.  Inserts and queries
-// are separate kernels on one stream, so a query sees every earlier insert
-// (the phase-concurrent setting of Section 3.5, type 3).
+// Appendix B.4).  A handle keeps the parent array P resident in device
+// memory.  Initialize runs static connectivity on the base graph into P.
+// With a union-find finish each batch's inserts are Unions (the handle's
+// engine: Section 3.5's types 1 and 3); with SV or Liu-Tarjan PRF (type 2)
+// the batch's pairs go through that finish's rounds (hooks, then a full
+// shortcut) until a round changes nothing.  Queries compare the roots of
+// both endpoints.  Inserts and queries are separate kernels on one stream,
+// so a query sees every earlier insert.
 #include "cc_internal.h"
 
 using namespace ccg;
@@ -15,6 +17,7 @@ struct cc_incr {
     uint32_t *P;
     cc_finish_opt fo;
     uint32_t *hooks;   // UF-Hooks: the resident hooks array (all free after the base graph)
+    uint32_t *prev;    // SV / LT-PRF: P at a round's start, plus one changed word at prev[n]
 };
 
 namespace {
@@ -51,6 +54,42 @@ __global__ void __launch_bounds__(256, 8) k_incr_insert(uint32_t *P, uint32_t n,
 #pragma unroll
         for (int j = 0; j < 4; ++j)
             if (ok[j] && pu[j] != pv[j]) E::unite(P, u[j], v[j], pu[j], pv[j], d);
+    }
+}
+
+// Type 2 (SV, Liu-Tarjan PRF): one round over a batch's pairs.  SV hooks
+// the larger of the two parents under the smaller if it was a root at the
+// round's start (writeMin); PRF offers each parent to the other parent
+// under the same root condition.  P is flat (every vertex at its root)
+// between rounds, so the parents are the roots.
+template <bool SV>
+__global__ void __launch_bounds__(256, 8) k_incr_round(uint32_t *P, const uint32_t *prev, uint32_t n,
+                                                       const uint32_t *pairs, uint64_t k, uint32_t *changed,
+                                                       Dev d) {
+    bool hit = false;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < k; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t u = __ldcs(pairs + 2 * i), v = __ldcs(pairs + 2 * i + 1);
+        if (u >= n || v >= n) { atomicOr(d.err, ERR_BAD_EDGE); continue; }
+        const uint32_t x = ld_rel(P + u), y = ld_rel(P + v);
+        if (SV) {
+            const uint32_t l = x < y ? x : y, h = x < y ? y : x;
+            if (l != h && prev[h] == h) hit |= atomicMin(P + h, l) > l;
+        } else {
+            if (y < x && prev[x] == x) hit |= atomicMin(P + x, y) > y;
+            if (x < y && prev[y] == y) hit |= atomicMin(P + y, x) > x;
+        }
+    }
+    if (hit) *changed = 1u;
+}
+
+__global__ void k_incr_flag(uint32_t *err, uint32_t bits) { atomicOr(err, bits); }
+
+// FullShortcut: every vertex points at its root.
+__global__ void __launch_bounds__(256, 8) k_incr_shortcut(uint32_t *P, uint32_t n, Dev d) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = (uint32_t)i, p = ld_rel(P + v);
+        const uint32_t r = find_from<FIND_NAIVE>(P, v, p, d);
+        if (r != p) P[v] = r;
     }
 }
 
@@ -104,22 +143,26 @@ cc_status cc_incr_create(const void *offsets, int offsets_u64, const uint32_t *e
     cc_status st = check_sample(so);
     if (st == CC_OK) st = check_finish(fo);
     if (st != CC_OK) return st;
-    if (fo.kind != CC_FINISH_UF_REM_CAS && fo.kind != CC_FINISH_UF_ASYNC && fo.kind != CC_FINISH_UF_HOOKS &&
-        fo.kind != CC_FINISH_UF_EARLY)
+    // union-find (types 1 and 3) and SV / Liu-Tarjan PRF (type 2); the
+    // finishes that are not root-based have no batch-incremental form
+    if (fo.kind == CC_FINISH_LIU_TARJAN || fo.kind == CC_FINISH_STERGIOU || fo.kind == CC_FINISH_LABEL_PROP)
         return CC_ERR_UNSUPPORTED;
     const DeviceInfo *di = device_info();
     if (!di) return CC_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cc_incr *h = new cc_incr{di->device, n, nullptr, fo, nullptr};
+    cc_incr *h = new cc_incr{di->device, n, nullptr, fo, nullptr, nullptr};
     if (n > 0) {
         cudaError_t e = cudaMalloc(&h->P, (size_t)n * 4);
         if (e == cudaSuccess && fo.kind == CC_FINISH_UF_HOOKS) {
             e = cudaMalloc(&h->hooks, (size_t)n * 4);
             if (e == cudaSuccess) e = cudaMemsetAsync(h->hooks, 0xFF, (size_t)n * 4, s);
         }
+        if (e == cudaSuccess && (fo.kind == CC_FINISH_SV || fo.kind == CC_FINISH_LT_PRF))
+            e = cudaMalloc(&h->prev, ((size_t)n + 1) * 4);
         if (e != cudaSuccess) {
             if (h->P) cudaFree(h->P);
             if (h->hooks) cudaFree(h->hooks);
+            if (h->prev) cudaFree(h->prev);
             delete h;
             return from_cuda(e);
         }
@@ -135,6 +178,7 @@ cc_status cc_incr_create(const void *offsets, int offsets_u64, const uint32_t *e
         if (st != CC_OK) {
             cudaFree(h->P);
             if (h->hooks) cudaFree(h->hooks);
+            if (h->prev) cudaFree(h->prev);
             delete h;
             return st;
         }
@@ -153,6 +197,38 @@ cc_status cc_incr_insert_batch(cc_incr *h, const uint32_t *pairs, uint64_t k, vo
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Dev d = make_dev(di, h->n);
     d.hooks = h->hooks;
+    if (h->prev) {
+        // type 2: rounds until nothing changes; each round reads a flag on
+        // the host, so this call synchronises the stream once per round
+        const unsigned gk = grid_for(di, k, TPB), gn = grid_for(di, h->n, TPB);
+        uint32_t *changed = h->prev + h->n;
+        for (uint32_t r = 0;; ++r) {
+            if (r >= round_cap()) {
+                k_incr_flag<<<1, 1, 0, s>>>(di->err, CC_DEVERR_NONCONVERGED);
+                return from_cuda(cudaGetLastError());
+            }
+            cudaError_t e = cudaMemsetAsync(changed, 0, 4, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(h->prev, h->P, (size_t)h->n * 4, cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return from_cuda(e);
+            {
+                CC_PROF("k_incr_round", s);
+                if (h->fo.kind == CC_FINISH_SV)
+                    k_incr_round<true><<<gk, TPB, 0, s>>>(h->P, h->prev, h->n, pairs, k, changed, d);
+                else
+                    k_incr_round<false><<<gk, TPB, 0, s>>>(h->P, h->prev, h->n, pairs, k, changed, d);
+            }
+            {
+                CC_PROF("k_incr_shortcut", s);
+                k_incr_shortcut<<<gn, TPB, 0, s>>>(h->P, h->n, d);
+            }
+            uint32_t hc = 0;
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, changed, 4, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return from_cuda(e);
+            if (hc == 0) return CC_OK;
+        }
+    }
     const unsigned grid = grid_for(di, (k + 3) / 4, TPB);
     return with_uf_engine(h->fo.kind, h->fo.find, h->fo.splice, [&](auto eng) -> cc_status {
         using E = decltype(eng);
@@ -202,8 +278,9 @@ cc_status cc_incr_destroy(cc_incr *h) {
     if (!h) return CC_OK;
     cudaError_t e = cudaSuccess;
     if (h->P) e = cudaFree(h->P);
-    if (h->hooks) {
-        const cudaError_t e2 = cudaFree(h->hooks);
+    for (uint32_t *p : {h->hooks, h->prev}) {
+        if (!p) continue;
+        const cudaError_t e2 = cudaFree(p);
         if (e == cudaSuccess) e = e2;
     }
     delete h;

@@ -98,10 +98,10 @@ def test_empty_graph_is_a_no_op():
     assert _call_static(0, 0, 0, 0, 0) == 0
 
 
-def test_incremental_rejects_sv_lt():
+def test_incremental_rejects_non_root_based():
     L = cc.lib()
     h = ctypes.c_void_p(0)
-    fo = cc.finish_opt("sv")
+    fo = cc.finish_opt("PUS")
     so = cc.sample_opt()
     # n = 0 keeps this off the device: the finish kind is checked first
     assert L.cc_incr_create(None, 0, None, 0, 0, ctypes.byref(so), ctypes.byref(fo), None, ctypes.byref(h)) == 6

@@ -18,7 +18,8 @@ VARIANTS = [("uf_rem_cas", "naive", "split_one"), ("uf_rem_cas", "split", "halve
             ("uf_rem_cas", "naive", "atomic"), ("uf_rem_cas", "halve", "atomic"),
             ("uf_async", "compress", "split_one"), ("uf_hooks", "naive", "split_one"),
             ("uf_hooks", "compress", "split_one"), ("uf_early", "naive", "split_one"),
-            ("uf_early", "split", "split_one"), ("uf_early", "compress", "split_one")]
+            ("uf_early", "split", "split_one"), ("uf_early", "compress", "split_one"),
+            ("sv", "naive", "split_one"), ("lt_prf", "naive", "split_one")]
 
 
 def run_batches(base, n, fin, nbatches, seed, sizes, qfrac, sample="kout"):
@@ -50,8 +51,8 @@ def test_incremental_from_empty(fin):
     run_batches(None, 1 << 14, fin, 8, seed=1, sizes=[1, 10, 1000, 20000], qfrac=0.5)
 
 
-@pytest.mark.parametrize("fin", VARIANTS[:2] + VARIANTS[3:4] + VARIANTS[6:7] + VARIANTS[9:10] + VARIANTS[11:12],
-                         ids=lambda f: "-".join(f))
+@pytest.mark.parametrize("fin", VARIANTS[:2] + VARIANTS[3:4] + VARIANTS[6:7] + VARIANTS[9:10] + VARIANTS[11:12] +
+                         VARIANTS[14:16], ids=lambda f: "-".join(f))
 @pytest.mark.parametrize("sample", ["none", "kout", "ldd"])
 def test_incremental_on_base_graph(fin, sample):
     base = synth.rmat(15, 4, seed=3)
