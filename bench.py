@@ -368,7 +368,10 @@ def run_ours(args):
         same = bool(torch.equal(h_lab, lab.cpu()))
         out["e2e"] = {"value": round(world * m / e2e_s / 1e9, 3), "unit": "Gedges/s",
                       "h2d_bytes_per_step": b_csr, "d2h_bytes_per_step": 4 * n, "ms_per_step": round(e2e_s * 1e3, 3),
-                      "labels_equal_device_path": same}
+                      "labels_equal_device_path": same,
+                      "h2d": ("k-out reads the pinned CSR in place (offsets and about two 32-byte sectors per vertex "
+                              "cross the host link); h2d_bytes_per_step counts the whole host-resident input"
+                              if args.sample == "kout" else "the CSR is copied to the device each call")}
         del h_off, h_edg, h_lab
 
     # incremental: resident union-find, batches of inserts + queries

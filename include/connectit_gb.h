@@ -187,9 +187,14 @@ cc_status cc_amsf(const void *offsets, int offsets_u64, const uint32_t *edges, c
                   double *weight_out, uint32_t *labels_out, void *stream);
 
 /* cc_static on HOST buffers (offsets, edges, labels_out in host memory,
- * ideally pinned): copies the graph to library-allocated device memory,
- * runs cc_static, copies the labels back and synchronises.  Returns the
- * device error status. */
+ * ideally pinned): runs cc_static, copies the labels back and synchronises.
+ * The graph is copied to library-allocated device memory first, except
+ * with k-out sampling on pinned (device-addressable) offsets and edges:
+ * then the sampling reads them in place (the offsets and about two 32-byte
+ * sectors per vertex cross the host link instead of the whole CSR), and the
+ * finish reads in place too when the frequent cluster holds at least a
+ * quarter of the vertices (else the CSR is copied before the finish).
+ * Returns the device error status. */
 cc_status cc_static_host(const void *offsets, int offsets_u64, const uint32_t *edges, uint32_t n,
                          uint64_t m, const cc_sample_opt *sample, const cc_finish_opt *finish,
                          uint32_t *labels_out, void *stream);

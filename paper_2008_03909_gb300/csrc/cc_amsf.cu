@@ -338,15 +338,15 @@ __global__ void k_key_label(const unsigned long long *key, uint32_t *lmax) {
 __global__ void __launch_bounds__(256, 8) k_amsf_compact(const uint2 *ff, const float *fw, uint32_t n, uint32_t *out,
                                                          uint32_t *count, double *wsum, Dev d) {
     double acc = 0.0;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint2 e = ff[i];
-        if (e.x == NONE) continue;
-        const uint32_t k = append_one(count);
-        acc += (double)fw[i];
-        if (k >= n) { atomicOr(d.err, ERR_NONCONVERGED); continue; }
-        out[2 * (uint64_t)k] = e.x;
-        out[2 * (uint64_t)k + 1] = e.y;
-    }
+    block_compact(
+        n, count, [&](uint64_t i) { return ff[i].x != NONE; },
+        [&](uint64_t i, uint32_t k) {
+            acc += (double)fw[i];
+            if (k >= n) { atomicOr(d.err, ERR_NONCONVERGED); return; }
+            const uint2 e = ff[i];
+            out[2 * (uint64_t)k] = e.x;
+            out[2 * (uint64_t)k + 1] = e.y;
+        });
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
     if ((threadIdx.x & 31) == 0 && acc != 0.0) atomicAdd(wsum, acc);
 }

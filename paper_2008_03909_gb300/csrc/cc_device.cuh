@@ -515,6 +515,51 @@ __device__ __forceinline__ uint32_t append_one(uint32_t *counter) {
     return g.shfl(base, 0) + g.thread_rank();
 }
 
+// ---------------------------------------------------------------- compaction
+// Stream compaction of the index range [0, total) with one atomic per
+// block: each block takes a contiguous slice, counts the items it keeps,
+// reserves that many output slots with one atomicAdd on *count, then walks
+// the slice again in 256-item tiles and writes its items in slice order
+// (ballot prefix within a warp, warp totals through shared memory).  An
+// append per warp on one counter, the simple form, serialises millions of
+// atomics on one address.  Needs blockDim.x == 256.  keep(i) -> bool,
+// emit(i, slot).
+template <class Keep, class Emit>
+__device__ __forceinline__ void block_compact(uint64_t total, uint32_t *count, Keep keep, Emit emit) {
+    __shared__ uint32_t warp_sum[8];
+    __shared__ uint32_t base_s;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint64_t per = (total + gridDim.x - 1) / gridDim.x;
+    const uint64_t lo = per * blockIdx.x, hi = lo + per < total ? lo + per : total;
+    uint32_t c = 0;
+    for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) c += keep(i) ? 1u : 0u;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+    if (lane == 0) warp_sum[wid] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < 8; ++w) t += warp_sum[w];
+        base_s = t ? atomicAdd(count, t) : 0u;
+    }
+    __syncthreads();
+    uint32_t run = base_s;
+    for (uint64_t t0 = lo; t0 < hi; t0 += blockDim.x) {
+        const uint64_t i = t0 + threadIdx.x;
+        const bool k = i < hi && keep(i);
+        const uint32_t mask = __ballot_sync(0xFFFFFFFFu, k);
+        __syncthreads();   // warp_sum free again
+        if (lane == 0) warp_sum[wid] = __popc(mask);
+        __syncthreads();
+        uint32_t before = 0, tile = 0;
+        for (int w = 0; w < 8; ++w) {
+            before += w < wid ? warp_sum[w] : 0u;
+            tile += warp_sum[w];
+        }
+        if (k) emit(i, run + before + __popc(mask & ((1u << lane) - 1)));
+        run += tile;
+    }
+}
+
 // ---------------------------------------------------------------- edge maps
 // Edge functors provide
 //   bool begin(u)                 -- false: skip u's edges (unused by callers here)
@@ -544,10 +589,14 @@ __device__ __forceinline__ void light_edges(uint32_t u, uint64_t b, uint64_t e, 
     }
 }
 
-// One warp applies f to edges [b, e) of vertex u (e - b <= CHUNK).
+// One warp applies f to edges [b, e) of vertex u, lane-strided, four loads
+// in flight per lane.  (Aligned 16-byte group loads per lane were tried and
+// lost: the no-sampling finish's chunk pass went from 4.4 to 17.8 ms at
+// RMAT-26, the parent gathers of four neighbouring edges then sitting in one
+// lane.)
 template <class F>
-__device__ __forceinline__ void warp_chunk_edges(uint32_t u, uint64_t b, uint64_t e,
-                                                 const uint32_t *A, uint32_t n, F &f, const Dev &d) {
+__device__ __forceinline__ void warp_chunk_edges(uint32_t u, uint64_t b, uint64_t e, const uint32_t *A, uint32_t n,
+                                                 F &f, const Dev &d) {
     const int lane = threadIdx.x & 31;
     for (uint64_t x = b + lane; x < e; x += 128) {
         uint32_t v[4];

@@ -151,14 +151,14 @@ struct PairOut {
 // Alter: every edge (a, b) becomes (P[a], P[b]); edges inside one tree go.
 __global__ void __launch_bounds__(256, 8) k_alter(const uint32_t *Ein, const uint32_t *cin, const uint32_t *K, Keys ks,
                                                   uint32_t *Eout, uint32_t *cout) {
-    const uint32_t total = *cin;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint2 e = reinterpret_cast<const uint2 *>(Ein)[i];
-        const uint32_t a = ks.id(ld_rel(K + e.x)), b = ks.id(ld_rel(K + e.y));
-        if (a == b) continue;
-        reinterpret_cast<uint2 *>(Eout)[append_one(cout)] = make_uint2(a, b);
-    }
+    const uint2 *ein = reinterpret_cast<const uint2 *>(Ein);
+    auto altered = [&](uint64_t i) {
+        const uint2 e = ein[i];
+        return make_uint2(ks.id(ld_rel(K + e.x)), ks.id(ld_rel(K + e.y)));
+    };
+    block_compact(
+        *cin, cout, [&](uint64_t i) { const uint2 a = altered(i); return a.x != a.y; },
+        [&](uint64_t i, uint32_t k) { reinterpret_cast<uint2 *>(Eout)[k] = altered(i); });
 }
 
 // Shortcut: one step of pointer jumping (P[v] <- P[P[v]]), or FullShortcut

@@ -69,12 +69,9 @@ __global__ void __launch_bounds__(256, 8) k_probe_chunks(const OffT *I, const ui
         vertex_range(I, cr.u, m, b, e, d);
         const uint64_t cb = b + (uint64_t)cr.c * CHUNK;
         const uint64_t ce = cb + CHUNK < e ? cb + CHUNK : e;
-        uint32_t acc = 0;
-        for (uint64_t i = cb + lane; i < ce; i += 32) {
-            const uint32_t w = ld_stream(A + i);
-            if (w >= n) { atomicOr(d.err, ERR_BAD_EDGE); continue; }
-            acc += MODE == 0 ? 1u : x[w];
-        }
+        ProbeEdge<MODE> f{x, 0u};
+        warp_chunk_edges(cr.u, cb, ce, A, n, f, d);
+        uint32_t acc = f.acc;
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
         if (lane == 0) atomicAdd(out + cr.u, acc);
     }

@@ -1632,35 +1632,32 @@ cc_status run_static(const Graph &g, const cc_sample_opt &so, const cc_finish_op
 // sampling and finish edge arrays, appended to out as (u, v) word pairs.
 // A forest has at most n - 1 pairs; more would mean a broken invariant, so
 // slots past n are flagged and not written (out holds n pairs).
+// Two arrays (BFS / LDD sampling): items 0..n-1 are the sampling edges,
+// n..2n-1 the finish edges.
 __global__ void __launch_bounds__(256, 8) k_forest_compact(const uint2 *sf, const uint2 *ff, uint32_t n, uint32_t *out,
                                                            uint32_t *count, Dev d) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint2 ab[2] = {sf[i], ff[i]};
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            if (ab[j].x == NONE) continue;
-            const uint32_t k = append_one(count);
-            if (k >= n) { atomicOr(d.err, ERR_NONCONVERGED); continue; }
-            out[2 * (uint64_t)k] = ab[j].x;
-            out[2 * (uint64_t)k + 1] = ab[j].y;
-        }
-    }
+    block_compact(
+        2ull * n, count, [&](uint64_t i) { return (i < n ? sf[i] : ff[i - n]).x != NONE; },
+        [&](uint64_t i, uint32_t k) {
+            if (k >= n) { atomicOr(d.err, ERR_NONCONVERGED); return; }
+            const uint2 e = i < n ? sf[i] : ff[i - n];
+            out[2 * (uint64_t)k] = e.x;
+            out[2 * (uint64_t)k + 1] = e.y;
+        });
 }
 
-// The same filter when every hooked root ends as a non-root and nothing
-// else does: slot v holds an edge exactly when label[v] != v.
+// One array (k-out / no sampling): every hooked root ends as a non-root and
+// nothing else does, so slot v holds an edge exactly when label[v] != v.
 __global__ void __launch_bounds__(256, 8) k_forest_compact_hooked(const uint2 *ff, const uint32_t *L, uint32_t n,
                                                                   uint32_t *out, uint32_t *count, Dev d) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        if (L[i] == (uint32_t)i) continue;
-        const uint2 e = ff[i];
-        const uint32_t k = append_one(count);
-        if (k >= n) { atomicOr(d.err, ERR_NONCONVERGED); continue; }
-        out[2 * (uint64_t)k] = e.x;
-        out[2 * (uint64_t)k + 1] = e.y;
-    }
+    block_compact(
+        n, count, [&](uint64_t i) { return L[i] != (uint32_t)i; },
+        [&](uint64_t i, uint32_t k) {
+            if (k >= n) { atomicOr(d.err, ERR_NONCONVERGED); return; }
+            const uint2 e = ff[i];
+            out[2 * (uint64_t)k] = e.x;
+            out[2 * (uint64_t)k + 1] = e.y;
+        });
 }
 
 // The spanning-forest algorithm: labels and edge arrays initialised, the
@@ -1725,6 +1722,67 @@ cc_status run_forest(const Graph &g, const cc_sample_opt &so, const cc_finish_op
     CC_TRY(cudaStreamSynchronize(s));
     *count_out = hc < g.n ? hc : g.n;
     return CC_OK;
+}
+
+// Host-buffer entry, zero-copy form.  When the CSR lies in pinned host
+// memory that the device can address (over NVLink-C2C on Grace-Blackwell),
+// k-out sampling reads it in place: the offsets and about two 32-byte
+// sectors per vertex, instead of a copy of the whole CSR.  If the frequent
+// cluster then holds at least a quarter of the vertices, the finish reads in
+// place too (it reads only the other vertices' edges); otherwise the CSR is
+// copied to device memory first and the finish reads that copy.
+template <typename OffT>
+cc_status run_static_zero_copy(const Graph &gz, const void *h_off, const uint32_t *h_edg, const cc_sample_opt &so,
+                               const cc_finish_opt &fo, uint32_t *labels_host, cudaStream_t s) {
+    const DeviceInfo *di = device_info();
+    if (!di) return CC_ERR_CUDA;
+    Dev d = make_dev(di, gz.n);
+    Work w;
+    plan(w, gz, so.kind, so.freq_samples, fo.kind, true);
+    const size_t o_lab = w.sc.reserve((size_t)gz.n * 4);
+    cc_status st = w.sc.alloc(s);
+    if (st != CC_OK) return st;
+    if ((st = attach_hooks(w, d, gz.n, s)) != CC_OK) return st;
+    uint32_t *P = w.sc.at<uint32_t>(o_lab);
+    CC_TRY(cudaMemsetAsync(w.ctl(), 0, sizeof(Ctl), s));
+    int32_t info = 0;
+    const bool fused = so.freq_samples == 0;
+    st = sample_phase<OffT>(gz, so, fo, P, w, di, d, s, &info, fused ? w.sc.at<uint32_t>(w.o_counts) : nullptr);
+    if (st != CC_OK) return st;
+    st = identify_phase(P, gz.n, so.freq_samples, so.seed, &w.ctl()->lmax, w, di, d, s, true, fused);
+    if (st != CC_OK) return st;
+    unsigned long long key = 0;
+    CC_TRY(cudaMemcpyAsync(&key, &w.ctl()->key, 8, cudaMemcpyDeviceToHost, s));
+    CC_TRY(cudaStreamSynchronize(s));
+    // with exact counting the key holds the cluster's non-root count (size - 1)
+    const uint64_t lsize = (key >> 32) + 1;
+    Graph gf = gz;
+    Scratch copy;
+    if (so.freq_samples != 0 || 4 * lsize < gz.n) {
+        const size_t ob = (size_t)(gz.n + 1ull) * sizeof(OffT);
+        const size_t o_off = copy.reserve(ob), o_edg = copy.reserve((size_t)gz.m * 4);
+        if ((st = copy.alloc(s)) != CC_OK) return st;
+        CC_TRY(cudaMemcpyAsync(copy.at<void>(o_off), h_off, ob, cudaMemcpyHostToDevice, s));
+        if (gz.m) CC_TRY(cudaMemcpyAsync(copy.at<void>(o_edg), h_edg, (size_t)gz.m * 4, cudaMemcpyHostToDevice, s));
+        gf = Graph{copy.at<void>(o_off), gz.u64, gz.m ? copy.at<uint32_t>(o_edg) : nullptr, gz.n, gz.m};
+    }
+    uint32_t rounds = 0;
+    st = finish_phase<OffT>(gf, fo, &w.ctl()->lmax, P, w, di, d, s, &rounds);
+    if (st != CC_OK) return st;
+    CC_TRY(cudaMemcpyAsync(labels_host, P, (size_t)gz.n * 4, cudaMemcpyDeviceToHost, s));
+    CC_TRY(cudaStreamSynchronize(s));
+    return CC_OK;
+}
+
+// Device address of pinned host memory, or null.
+const void *host_device_view(const void *p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    return (a.type == cudaMemoryTypeHost && a.devicePointer) ? a.devicePointer : nullptr;
 }
 
 // Capped BFS (push only, at most `cap` levels) from src: levels run and
@@ -1916,6 +1974,19 @@ cc_status cc_static_host(const void *offsets, int offsets_u64, const uint32_t *e
     if (!labels_out) return CC_ERR_INVALID;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t ob = (size_t)(n + 1ull) * (offsets_u64 ? 8 : 4);
+    cc_sample_opt so;
+    cc_finish_opt fo;
+    resolve_opts(sample, finish, so, fo);
+    if ((st = check_sample(so)) != CC_OK || (st = check_finish(fo)) != CC_OK) return st;
+    const void *voff = host_device_view(offsets), *vedg = m ? host_device_view(edges) : nullptr;
+    if (so.kind == CC_SAMPLE_KOUT && voff && (vedg || !m) && aligned(voff, offsets_u64 ? 8 : 4) &&
+        (!m || aligned(vedg, 4))) {
+        Graph gz{voff, offsets_u64 != 0, static_cast<const uint32_t *>(vedg), n, m};
+        st = offsets_u64 ? run_static_zero_copy<uint64_t>(gz, offsets, edges, so, fo, labels_out, s)
+                         : run_static_zero_copy<uint32_t>(gz, offsets, edges, so, fo, labels_out, s);
+        if (st != CC_OK) return st;
+        return cc_device_error(stream, nullptr);
+    }
     Scratch sc;
     const size_t o_off = sc.reserve(ob), o_edg = sc.reserve((size_t)m * 4), o_lab = sc.reserve((size_t)n * 4);
     if ((st = sc.alloc(s)) != CC_OK) return st;

@@ -226,6 +226,19 @@ def test_repeat_runs_identical():
         assert np.array_equal(first, again)
 
 
+def test_host_buffer_zero_copy_and_fallback_copy():
+    """k-out on pinned host buffers reads them in place; a graph whose
+    frequent cluster is small copies the CSR before the finish.  Both give
+    the oracle's labels."""
+    for g in (synth.rmat(16, 16, seed=4), synth.erdos_renyi(1 << 17, 0.6, seed=2), synth.grid2d(300, 280, 0.45)):
+        want, _ = oracle.cc_uf(*g.numpy())
+        for u64 in (True, False):
+            off = (g.offsets if u64 else g.offsets_u32()).pin_memory()
+            lab = cc.cc_static_host(off, g.edges.pin_memory(), cc.sample_opt("kout"))
+            assert np.array_equal(lab.numpy().view(np.uint32), want), (g.name, u64)
+    assert cc.device_error() == 0
+
+
 def test_host_buffer_entry_point():
     g = synth.rmat(15, 8, seed=2)
     want, _ = oracle.cc_uf(*g.numpy())
