@@ -391,6 +391,15 @@ cc_status cc_mlp_backward(const float *params, const float *X, const float *acts
 cc_status cc_mlp_adam(float *params, const float *grads, float *m, float *v, uint32_t step, float lr, void *stream);
 cc_status cc_mlp_predict(const float *params, const float *X, uint32_t B, int32_t *class_out, void *stream);
 
+/* Self-check of the bounded grid barrier (the wait the persistent BFS
+ * levels use): a cooperative launch of one block per SM meets at the
+ * barrier three times.  skip_block >= 0 names a block that leaves without
+ * arriving; the others then give up after wait_ms (1..4000), flag
+ * CC_DEVERR_NONCONVERGED and leave, and the call returns
+ * CC_ERR_NONCONVERGED with *blocks_passed_out = 0 (host) and a usable
+ * context.  skip_block < 0: every block passes, CC_OK.  Synchronises. */
+cc_status cc_selftest_grid_barrier(int skip_block, uint32_t wait_ms, uint32_t *blocks_passed_out, void *stream);
+
 /* Synchronise `stream`, then read and clear the per-device sticky error
  * word (CC_DEVERR_* bits) into *bits_out (host; may be NULL).  Returns
  * CC_OK when the word was 0, else the matching status. */

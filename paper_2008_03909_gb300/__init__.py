@@ -96,6 +96,8 @@ _SIGS = {
                                ctypes.c_uint64, ctypes.c_float, ctypes.c_int, ctypes.c_void_p,
                                ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double), ctypes.c_void_p,
                                ctypes.c_void_p]),
+    "cc_selftest_grid_barrier": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32),
+                                                ctypes.c_void_p]),
     "cc_static_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint32,
                                       ctypes.c_uint64, ctypes.POINTER(SampleOpt), ctypes.POINTER(FinishOpt),
                                       ctypes.c_void_p, ctypes.c_void_p]),
@@ -268,6 +270,13 @@ def cc_spanning_forest(offsets, edges, sample: SampleOpt | None = None, finish: 
                                     ctypes.c_void_p(labels_out.data_ptr() if labels_out is not None else 0),
                                     _stream(stream)), "cc_spanning_forest")
     return forest_out[: 2 * cnt.value].view(-1, 2), labels_out
+
+
+def selftest_grid_barrier(skip_block: int = -1, wait_ms: int = 200, stream=None):
+    """(status, blocks that passed) of the bounded grid-barrier self-check."""
+    passed = ctypes.c_uint32(0)
+    st = lib().cc_selftest_grid_barrier(skip_block, wait_ms, ctypes.byref(passed), _stream(stream))
+    return st, passed.value
 
 
 AMSF_MODE = {"nf": 0, "nf_s": 1, "coo": 2}

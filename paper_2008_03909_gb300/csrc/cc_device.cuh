@@ -101,7 +101,7 @@ struct GridBar {
     uint32_t pad;
 };
 
-__device__ __forceinline__ bool grid_sync(GridBar *b, const Dev &d) {
+__device__ __forceinline__ bool grid_sync(GridBar *b, const Dev &d, uint64_t limit_ns = OP_TIME_LIMIT_NS) {
     __shared__ uint32_t ok_s;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -115,7 +115,7 @@ __device__ __forceinline__ bool grid_sync(GridBar *b, const Dev &d) {
             const uint64_t t0 = gtimer();
             while (ld_acq(&b->gen) == g) {
                 if (ld_rel(&b->abort)) { ok = false; break; }
-                if (gtimer() - t0 > OP_TIME_LIMIT_NS) {
+                if (gtimer() - t0 > limit_ns) {
                     atomicOr(d.err, ERR_NONCONVERGED);
                     atomicExch(&b->abort, 1u);
                     ok = false;

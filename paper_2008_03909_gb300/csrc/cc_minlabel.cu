@@ -149,16 +149,78 @@ struct PairOut {
 };
 
 // Alter: every edge (a, b) becomes (P[a], P[b]); edges inside one tree go.
-__global__ void __launch_bounds__(256, 8) k_alter(const uint32_t *Ein, const uint32_t *cin, const uint32_t *K, Keys ks,
-                                                  uint32_t *Eout, uint32_t *cout) {
+// First in place (an edge that goes becomes (NONE, NONE)), so each edge's
+// two parents are read once; then the survivors are compacted into the
+// other buffer with one atomic per block.
+__global__ void __launch_bounds__(256, 8) k_alter_in_place(uint32_t *E, const uint32_t *count, const uint32_t *K,
+                                                           Keys ks) {
+    const uint32_t total = *count;
+    uint2 *e2 = reinterpret_cast<uint2 *>(E);
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint2 e = e2[i];
+        if (e.x == NONE) continue;
+        const uint32_t a = ks.id(ld_rel(K + e.x)), b = ks.id(ld_rel(K + e.y));
+        e2[i] = a == b ? make_uint2(NONE, NONE) : make_uint2(a, b);
+    }
+}
+
+__global__ void __launch_bounds__(256, 8) k_alter_compact(const uint32_t *Ein, const uint32_t *cin, uint32_t *Eout,
+                                                          uint32_t *cout) {
     const uint2 *ein = reinterpret_cast<const uint2 *>(Ein);
-    auto altered = [&](uint64_t i) {
-        const uint2 e = ein[i];
-        return make_uint2(ks.id(ld_rel(K + e.x)), ks.id(ld_rel(K + e.y)));
-    };
     block_compact(
-        *cin, cout, [&](uint64_t i) { const uint2 a = altered(i); return a.x != a.y; },
-        [&](uint64_t i, uint32_t k) { reinterpret_cast<uint2 *>(Eout)[k] = altered(i); });
+        *cin, cout, [&](uint64_t i) { return ein[i].x != NONE; },
+        [&](uint64_t i, uint32_t k) { reinterpret_cast<uint2 *>(Eout)[k] = ein[i]; });
+}
+
+// The edge list of every vertex's edges at their CSR positions, for the
+// finish without sampling (every vertex is a candidate): no counter, a
+// self-loop becomes (NONE, NONE).  The candidate lists drive it: light
+// vertices one per thread, heavier ones as CHUNK-edge pieces spread over
+// the grid's warps (a hub's list is not left to one warp).
+__device__ __forceinline__ uint2 pair_or_none(uint32_t u, uint32_t v, uint32_t n) {
+    return (v == u || v >= n) ? make_uint2(NONE, NONE) : make_uint2(u, v);
+}
+
+template <typename OffT>
+__global__ void __launch_bounds__(256, 8) k_pairs_at_positions(const OffT *I, const uint32_t *A, uint32_t n,
+                                                               uint64_t m, const uint32_t *light,
+                                                               const uint32_t *nlight, const ChunkRef *chunks,
+                                                               const uint32_t *nchunks, uint64_t cap, uint32_t *E,
+                                                               Dev d) {
+    uint2 *e2 = reinterpret_cast<uint2 *>(E);
+    const uint32_t nl = *nlight;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nl; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t u = light[i];
+        uint64_t b, e;
+        vertex_range(I, u, m, b, e, d);
+        for (uint64_t x = b; x < e; x += 4) {
+            uint32_t v[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[j] = x + j < e ? ld_stream(A + x + j) : 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (x + j < e) e2[x + j] = pair_or_none(u, v[j], n);
+        }
+    }
+    const int lane = threadIdx.x & 31;
+    const uint32_t total = (uint32_t)((uint64_t)*nchunks < cap ? (uint64_t)*nchunks : cap);
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t c = warp; c < total; c += nwarps) {
+        const ChunkRef cr = chunks[c];
+        uint64_t b, e;
+        vertex_range(I, cr.u, m, b, e, d);
+        const uint64_t cb = b + (uint64_t)cr.c * CHUNK, ce = cb + CHUNK < e ? cb + CHUNK : e;
+        for (uint64_t x = cb + lane; x < ce; x += 128) {
+            uint32_t v[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[j] = x + 32 * j < ce ? ld_stream(A + x + 32 * j) : 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (x + 32 * j < ce) e2[x + 32 * j] = pair_or_none(cr.u, v[j], n);
+        }
+    }
 }
 
 // Shortcut: one step of pointer jumping (P[v] <- P[P[v]]), or FullShortcut
@@ -300,6 +362,7 @@ cc_status run_minlabel(const MinLabelIn &in, const cc_finish_opt &fo, const Devi
     const uint32_t n = in.n;
     const unsigned gv = grid_for(di, n, TPB);
     const unsigned gc = grid_for(di, (uint64_t)1 << 40, TPB);
+    auto ge_for = [&](uint64_t items) { return grid_for(di, items ? items : 1, TPB); };
     const bool alter = fo.kind == CC_FINISH_LIU_TARJAN && (fo.lt_rules & CC_LT_ALTER);
     const bool lp = fo.kind == CC_FINISH_LABEL_PROP;
     const bool rootup = fo.kind == CC_FINISH_LIU_TARJAN && (fo.lt_rules & CC_LT_ROOTUP);
@@ -342,14 +405,26 @@ cc_status run_minlabel(const MinLabelIn &in, const cc_finish_opt &fo, const Devi
         // are (P[u], P[v]).  So the list starts altered.  The edges are
         // taken as read, and then a round whose connect and shortcut change
         // nothing would end the loop before the first Alter.
-        PairOut po{E[1], &fl->npairs[1], cand_edges, d, false};
-        {
+        if (!in.lmax_p) {
+            // no sampling: every edge at its CSR position, no counter
+            const uint32_t m32 = (uint32_t)in.m;
+            ce = cudaMemcpyAsync(&fl->npairs[1], &m32, 4, cudaMemcpyHostToDevice, s);
+            if (ce != cudaSuccess) return from_cuda(ce);
+            CC_PROF("k_pairs_build", s);
+            k_pairs_at_positions<OffT><<<gv, TPB, 0, s>>>(I, in.A, n, in.m, in.light, in.nlight, in.chunks,
+                                                          in.nchunks, in.chunk_cap, E[1], d);
+        } else {
+            PairOut po{E[1], &fl->npairs[1], cand_edges, d, false};
             CC_PROF("k_pairs_build", s);
             k_lists<OffT, PairOut><<<gv, TPB, 0, s>>>(I, in.A, n, in.m, in.light, in.nlight, in.chunks, in.nchunks,
                                                        in.chunk_cap, po, &fl->changed, d);
         }
-        CC_PROF("k_alter", s);
-        k_alter<<<gv, TPB, 0, s>>>(E[1], &fl->npairs[1], K, ks, E[0], &fl->npairs[0]);
+        {
+            CC_PROF("k_alter", s);
+            k_alter_in_place<<<ge_for(cand_edges), TPB, 0, s>>>(E[1], &fl->npairs[1], K, ks);
+        }
+        CC_PROF("k_alter_compact", s);
+        k_alter_compact<<<gv, TPB, 0, s>>>(E[1], &fl->npairs[1], E[0], &fl->npairs[0]);
     }
     if ((ce = cudaGetLastError()) != cudaSuccess) return from_cuda(ce);
     const uint64_t cap = lp ? (uint64_t)n + 2 : (uint64_t)round_cap();
@@ -431,8 +506,12 @@ cc_status run_minlabel(const MinLabelIn &in, const cc_finish_opt &fo, const Devi
             if (alter) {
                 const int nx = cur ^ 1;
                 if ((ce = cudaMemsetAsync(&fl->npairs[nx], 0, 4, s)) != cudaSuccess) return from_cuda(ce);
-                CC_PROF("k_alter", s);
-                k_alter<<<gv, TPB, 0, s>>>(E[cur], &fl->npairs[cur], K, ks, E[nx], &fl->npairs[nx]);
+                {
+                    CC_PROF("k_alter", s);
+                    k_alter_in_place<<<ge_for(cand_edges), TPB, 0, s>>>(E[cur], &fl->npairs[cur], K, ks);
+                }
+                CC_PROF("k_alter_compact", s);
+                k_alter_compact<<<gv, TPB, 0, s>>>(E[cur], &fl->npairs[cur], E[nx], &fl->npairs[nx]);
                 cur = nx;
             }
             if ((ce = cudaGetLastError()) != cudaSuccess) return from_cuda(ce);

@@ -678,7 +678,10 @@ __global__ void __launch_bounds__(256, 8) k_bfs_relabel(uint32_t *P, const uint3
 // asks for bottom-up (frontier edges > unexplored / 14).
 // Frontier counts and edge sums rotate over three slots: level L reads slot
 // L % 3, appends into slot (L + 1) % 3, and clears slot (L + 2) % 3, which no
-// block reads after the barrier that ended level L - 1.
+// block reads after the barrier that ended level L - 1.  The edge sum a level
+// leaves for the next is its own frontier's (read with the offsets it loads
+// anyway), so the direction rule looks one level behind: that changes when
+// the launch hands over to bottom-up, never which vertices are reached.
 struct BfsLoop {
     GridBar bar;
     uint32_t cnt[3];
@@ -688,17 +691,14 @@ struct BfsLoop {
     unsigned long long explored;   // frontier edges of the levels run
 };
 
-template <typename OffT>
 struct BFSPushEdge {
-    const OffT *I;
-    uint64_t m;
     uint32_t *P;
     uint32_t *vis;
     uint32_t *next;
     uint32_t *nnext;
     uint32_t src;
     uint32_t my_min;
-    unsigned long long my_edges;
+    unsigned long long my_edges;   // edges of the frontier vertices this thread expanded
     Dev d;
     __device__ __forceinline__ void apply4(uint32_t u, const uint32_t (&v)[4], const bool (&ok)[4]) {
 #pragma unroll
@@ -712,9 +712,6 @@ struct BFSPushEdge {
             if (d.forest) d.forest[w] = make_uint2(u, w);
             next[append_one(nnext)] = w;
             my_min = w < my_min ? w : my_min;
-            uint64_t b, e;
-            vertex_range(I, w, m, b, e, d);
-            my_edges += e - b;
         }
     }
 };
@@ -749,12 +746,13 @@ __global__ void __launch_bounds__(BFS_LOOP_TPB, 2) k_bfs_push_levels(const OffT 
             L->cnt[(lv + 2) % 3] = 0;
             L->mfc[(lv + 2) % 3] = 0;
         }
-        BFSPushEdge<OffT> f{I, m, P, vis, nx, &L->cnt[(lv + 1) % 3], src, NONE, 0ull, d};
+        BFSPushEdge f{P, vis, nx, &L->cnt[(lv + 1) % 3], src, NONE, 0ull, d};
         for (uint64_t base = warp * 32; base < nf; base += nwarps * 32) {
             const bool act = base + lane < nf;
             const uint32_t u = act ? cur[base + lane] : 0;
             uint64_t b = 0, e = 0;
             if (act) vertex_range(I, u, m, b, e, d);
+            f.my_edges += e - b;
             const bool heavy = e - b > LIGHT_MAX;
             if (act && !heavy) light_edges(u, b, e, A, n, f, d);
             // heavier vertices: the whole warp walks their edges
@@ -1095,7 +1093,7 @@ cc_status bfs_sample(const Graph &g, const cc_sample_opt &so, uint32_t *P, Work 
     // persistent top-down levels: one cooperative launch of every co-resident block
     int per_sm = 0;
     CC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bfs_push_levels<OffT>, BFS_LOOP_TPB, 0));
-    const unsigned loop_grid = (unsigned)(per_sm < 2 ? per_sm : 2) * di->sms;
+    const unsigned loop_grid = (unsigned)(per_sm < 1 ? per_sm : 1) * di->sms;   // one block per SM: cheapest barrier
     *info = -1;
     for (uint32_t t = 0; t < so.bfs_tries; ++t) {
         const uint32_t src = (uint32_t)(draw64(so.seed ^ TAG_BFS, t) % n);
