@@ -361,7 +361,6 @@ cc_status run_minlabel(const MinLabelIn &in, const cc_finish_opt &fo, const Devi
     const OffT *I = static_cast<const OffT *>(in.I);
     const uint32_t n = in.n;
     const unsigned gv = grid_for(di, n, TPB);
-    const unsigned gc = grid_for(di, (uint64_t)1 << 40, TPB);
     auto ge_for = [&](uint64_t items) { return grid_for(di, items ? items : 1, TPB); };
     const bool alter = fo.kind == CC_FINISH_LIU_TARJAN && (fo.lt_rules & CC_LT_ALTER);
     const bool lp = fo.kind == CC_FINISH_LABEL_PROP;
