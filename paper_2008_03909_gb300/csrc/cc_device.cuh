@@ -589,6 +589,58 @@ __device__ __forceinline__ void light_edges(uint32_t u, uint64_t b, uint64_t e, 
     }
 }
 
+// Warp-cooperative light edges.  Every lane of the warp calls this (it is
+// warp-synchronous) with its own vertex u and edge range [b, b + deg),
+// deg <= LIGHT_MAX, or deg = 0 for none.  The warp walks the concatenation
+// of the 32 ranges in steps of 128 positions: lane L takes positions
+// step + 32j + L (j < 4), so the 32 lanes of one load instruction read 32
+// consecutive positions, which are consecutive words of A inside a vertex's
+// range, and no lane idles while another walks a longer list.  The owner of
+// position t is the last lane whose exclusive degree prefix is <= t (a
+// five-step shuffle search; a lane with deg = 0 is never that last lane for
+// t below the total).  f.apply4u takes the four edges with their own sources.
+template <class F>
+__device__ __forceinline__ void warp_light_edges(uint32_t u, uint64_t b, uint32_t deg, const uint32_t *A, uint32_t n,
+                                                 F &f, const Dev &d) {
+    const unsigned FULL = 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31;
+    uint32_t incl = deg;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const uint32_t excl = incl - deg;
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    // A index of position t within this lane's range: rel + t (mod 2^64)
+    const uint64_t rel = b - excl;
+    for (uint32_t s = 0; s < total; s += 128) {
+        uint32_t uu[4], v[4];
+        bool ok[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            uu[j] = 0;
+            v[j] = 0;
+            ok[j] = false;
+            if (s + 32 * j < total) {   // warp-uniform
+                const uint32_t t = s + 32 * j + lane;
+                int o = 0;
+#pragma unroll
+                for (int k = 16; k > 0; k >>= 1)
+                    if (__shfl_sync(FULL, excl, o + k) <= t) o += k;
+                uu[j] = __shfl_sync(FULL, u, o);
+                const uint64_t r = __shfl_sync(FULL, rel, o);
+                ok[j] = t < total;
+                v[j] = ok[j] ? ld_stream(A + (r + t)) : uu[j];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (ok[j] && v[j] >= n) { atomicOr(d.err, ERR_BAD_EDGE); ok[j] = false; }
+        f.apply4u(uu, v, ok);
+    }
+}
+
 // One warp applies f to edges [b, e) of vertex u, lane-strided, four loads
 // in flight per lane.  (Aligned 16-byte group loads per lane were tried and
 // lost: the no-sampling finish's chunk pass went from 4.4 to 17.8 ms at
@@ -694,6 +746,13 @@ struct UnionEdge {
                 pu = ld_rel(P + u);
             }
         }
+    }
+    // four edges with their own sources (warp_light_edges)
+    __device__ __forceinline__ void apply4u(const uint32_t (&u)[4], const uint32_t (&v)[4], const bool (&ok)[4]) {
+        bool act[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) act[j] = ok[j] && v[j] != u[j] && (!lower_only || v[j] < u[j]);
+        unite_pairs<E, 4>(P, u, v, act, d);
     }
     __device__ __forceinline__ void flush() {}
 };

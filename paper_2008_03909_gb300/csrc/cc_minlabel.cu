@@ -97,6 +97,11 @@ struct LTRule {
         for (int j = 0; j < 4; ++j)
             if (ok[j]) edge(u, v[j]);
     }
+    __device__ __forceinline__ void apply4u(const uint32_t (&u)[4], const uint32_t (&v)[4], const bool (&ok)[4]) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (ok[j]) edge(u[j], v[j]);
+    }
 };
 
 // Candidate edges read from the CSR: light candidates one per thread, the
@@ -106,13 +111,17 @@ __global__ void __launch_bounds__(256, 8) k_lists(const OffT *I, const uint32_t 
                                                   const uint32_t *light, const uint32_t *nlight, const ChunkRef *chunks,
                                                   const uint32_t *nchunks, uint64_t cap, F f, uint32_t *changed,
                                                   Dev d) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint32_t total = *nlight;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t u = light[i];
-        uint64_t b, e;
-        vertex_range(I, u, m, b, e, d);
-        light_edges(u, b, e, A, n, f, d);
+    for (uint64_t base = warp * 32; base < total; base += nw * 32) {
+        const bool act = base + lane < total;
+        const uint32_t u = act ? light[base + lane] : 0;
+        uint64_t b = 0, e = 0;
+        if (act) vertex_range(I, u, m, b, e, d);
+        const uint64_t deg = e - b;   // <= LIGHT_MAX: the binning listed light vertices only
+        warp_light_edges(u, b, deg > LIGHT_MAX ? LIGHT_MAX : (uint32_t)deg, A, n, f, d);
     }
     run_chunks(I, A, n, m, chunks, nchunks, cap, f, d);
     if (__any_sync(0xFFFFFFFFu, f.hit) && (threadIdx.x & 31) == 0) *changed = 1u;
@@ -144,6 +153,15 @@ struct PairOut {
             const uint32_t k = append_one(count);
             if (k >= cap) { atomicOr(d.err, ERR_NONCONVERGED); continue; }
             reinterpret_cast<uint2 *>(E)[k] = make_uint2(u, v[j]);
+        }
+    }
+    __device__ __forceinline__ void apply4u(const uint32_t (&u)[4], const uint32_t (&v)[4], const bool (&ok)[4]) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (!ok[j] || v[j] == u[j]) continue;
+            const uint32_t k = append_one(count);
+            if (k >= cap) { atomicOr(d.err, ERR_NONCONVERGED); continue; }
+            reinterpret_cast<uint2 *>(E)[k] = make_uint2(u[j], v[j]);
         }
     }
 };
@@ -275,6 +293,20 @@ struct StergiouRule {
             offer(ks.id(kw), ku);
         }
     }
+    __device__ __forceinline__ void apply4u(const uint32_t (&u)[4], const uint32_t (&v)[4], const bool (&ok)[4]) {
+        uint32_t ku[4], kw[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            ku[j] = ok[j] ? prev[u[j]] : 0;
+            kw[j] = ok[j] ? prev[v[j]] : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (!ok[j]) continue;
+            offer(ks.id(ku[j]), kw[j]);
+            offer(ks.id(kw[j]), ku[j]);
+        }
+    }
 };
 
 // ---------------------------------------------------------------- label propagation
@@ -306,6 +338,14 @@ struct LPRule {
             }
         }
     }
+    __device__ __forceinline__ void apply4u(const uint32_t (&u)[4], const uint32_t (&v)[4], const bool (&ok)[4]) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const bool one[4] = {ok[j], false, false, false};
+            const uint32_t w[4] = {v[j], 0, 0, 0};
+            apply4(u[j], w, one);
+        }
+    }
 };
 
 // Edges of a vertex list: light vertices one per thread, heavier ones by the
@@ -323,7 +363,7 @@ __global__ void __launch_bounds__(256, 8) k_frontier(const OffT *I, const uint32
         uint64_t b = 0, e = 0;
         if (act) vertex_range(I, u, m, b, e, d);
         const bool heavy = e - b > LIGHT_MAX;
-        if (act && !heavy) light_edges(u, b, e, A, n, f, d);
+        warp_light_edges(u, b, heavy ? 0u : (uint32_t)(e - b), A, n, f, d);
         uint32_t hm = __ballot_sync(0xFFFFFFFFu, heavy);
         while (hm) {
             const int l = __ffs(hm) - 1;

@@ -26,10 +26,29 @@ struct ProbeEdge {
     }
 };
 
+// The light path's reduction when the warp walks its 32 vertices' edges
+// together (warp_light_edges): each edge adds into its source's slot of
+// the warp's shared-memory sums (sums[u - base], vertices base .. base+31).
+template <int MODE>
+struct ProbeFlat {
+    const uint32_t *x;
+    uint32_t *sums;
+    uint64_t base;
+    __device__ __forceinline__ void apply4u(const uint32_t (&u)[4], const uint32_t (&v)[4], const bool (&ok)[4]) {
+        uint32_t val[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) val[j] = ok[j] ? (MODE == 0 ? 1u : x[v[j]]) : 0u;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (ok[j]) atomicAdd(sums + (uint32_t)(u[j] - base), val[j]);
+    }
+};
+
 // MODE 0: MapEdges, out[v] = #edges read; MODE 1: GatherEdges,
-// out[v] = sum of x[w] over neighbours w (mod 2^32).  Vertices of degree
-// <= LIGHT_MAX are reduced by one thread; heavier ones are zeroed here and
-// reduced in chunks by k_probe_chunks.
+// out[v] = sum of x[w] over neighbours w (mod 2^32).  The edges of the
+// vertices of degree <= LIGHT_MAX are walked by the warp together
+// (warp_light_edges); heavier vertices are zeroed here and reduced in
+// chunks by k_probe_chunks.
 template <typename OffT, int MODE>
 __global__ void __launch_bounds__(256, 8) k_probe_bin(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m,
                                                       const uint32_t *x, uint32_t *out, ChunkRef *chunks,
@@ -37,6 +56,8 @@ __global__ void __launch_bounds__(256, 8) k_probe_bin(const OffT *I, const uint3
     const int lane = threadIdx.x & 31;
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    __shared__ uint32_t sums_all[TPB];
+    uint32_t *sums = sums_all + (threadIdx.x & ~31u);
     for (uint64_t base = warp * 32; base < n; base += nw * 32) {
         const uint64_t v = base + lane;
         uint64_t b = 0, e = 0;
@@ -44,14 +65,14 @@ __global__ void __launch_bounds__(256, 8) k_probe_bin(const OffT *I, const uint3
         const uint64_t deg = e - b;
         const uint32_t nc = deg > LIGHT_MAX ? (uint32_t)((deg + CHUNK - 1) / CHUNK) : 0;
         const uint32_t slot = warp_append_full(nchunks, nc);
-        if (nc) {
-            write_chunks(chunks, cap, slot, nc, (uint32_t)v, d);
-            out[v] = 0;
-        } else if (v < n) {
-            ProbeEdge<MODE> f{x, 0u};
-            light_edges((uint32_t)v, b, e, A, n, f, d);
-            out[v] = f.acc;
-        }
+        if (nc) write_chunks(chunks, cap, slot, nc, (uint32_t)v, d);
+        sums[lane] = 0;
+        __syncwarp();
+        ProbeFlat<MODE> f{x, sums, base};
+        warp_light_edges((uint32_t)v, b, nc ? 0u : (uint32_t)deg, A, n, f, d);
+        __syncwarp();
+        if (v < n) out[v] = sums[lane];
+        __syncwarp();
     }
 }
 

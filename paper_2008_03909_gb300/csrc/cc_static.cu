@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(256, 8) k_range_bin(const OffT *I, const uint3
         uint32_t nc = deg > LIGHT_MAX ? (uint32_t)((deg + CHUNK - 1) / CHUNK) : 0;
         uint32_t slot = warp_append_full(nchunks, nc);
         if (nc) write_chunks(chunks, cap, slot, nc, u, d);
-        else if (deg) light_edges(u, b, e, A, n, f, d);
+        warp_light_edges(u, b, nc ? 0u : (uint32_t)deg, A, n, f, d);
     }
     f.flush();
     for (int o = 16; o > 0; o >>= 1) my_edges += __shfl_xor_sync(0xFFFFFFFFu, my_edges, o);
@@ -431,7 +431,7 @@ __global__ void __launch_bounds__(256, 8) k_list_bin(const OffT *I, const uint32
         uint32_t nc = deg > LIGHT_MAX ? (uint32_t)((deg + CHUNK - 1) / CHUNK) : 0;
         uint32_t slot = warp_append_full(nchunks, nc);
         if (nc) write_chunks(chunks, cap, slot, nc, u, d);
-        else if (deg) light_edges(u, b, e, A, n, f, d);
+        warp_light_edges(u, b, nc ? 0u : (uint32_t)deg, A, n, f, d);
     }
     f.flush();
 }
@@ -487,13 +487,19 @@ __global__ void __launch_bounds__(256, 8) k_cand_bin(const OffT *I, uint32_t n, 
 template <typename OffT, class F>
 __global__ void __launch_bounds__(256, 8) k_light_list(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, const uint32_t *list,
                              const uint32_t *count, F f, Dev d) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint32_t total = *count;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t u = list[i];
-        uint64_t b, e;
-        vertex_range(I, u, m, b, e, d);
-        light_edges(u, b, e, A, n, f, d);
+    for (uint64_t base = warp * 32; base < total; base += nw * 32) {
+        const bool act = base + lane < total;
+        const uint32_t u = act ? list[base + lane] : 0;
+        uint64_t b = 0, e = 0;
+        if (act) vertex_range(I, u, m, b, e, d);
+        // the list holds light vertices only; a longer range (malformed
+        // offsets) is cut to LIGHT_MAX edges rather than overrunning
+        const uint64_t deg = e - b;
+        warp_light_edges(u, b, deg > LIGHT_MAX ? LIGHT_MAX : (uint32_t)deg, A, n, f, d);
     }
     f.flush();
 }
@@ -514,6 +520,22 @@ struct SVEdge {
             uint32_t pv = ld_rel(P + v[j]);
             uint32_t l = pu < pv ? pu : pv, h = pu < pv ? pv : pu;
             if (l != h && __ldg(prev + h) == h) {
+                atomicMin(P + h, l);
+                hit = true;
+            }
+        }
+    }
+    __device__ __forceinline__ void apply4u(const uint32_t (&u)[4], const uint32_t (&v)[4], const bool (&ok)[4]) {
+        uint32_t pu[4], pv[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            pu[j] = ok[j] ? ld_rel(P + u[j]) : 0;
+            pv[j] = ok[j] ? ld_rel(P + v[j]) : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t l = pu[j] < pv[j] ? pu[j] : pv[j], h = pu[j] < pv[j] ? pv[j] : pu[j];
+            if (ok[j] && l != h && __ldg(prev + h) == h) {
                 atomicMin(P + h, l);
                 hit = true;
             }
@@ -540,6 +562,20 @@ struct LTEdge {
             uint32_t x = ld_rel(P + u), y = ld_rel(P + v[j]);
             if (y < x && __ldg(prev + x) == x) hit |= atomicMin(P + x, y) > y;
             if (x < y && __ldg(prev + y) == y) hit |= atomicMin(P + y, x) > x;
+        }
+    }
+    __device__ __forceinline__ void apply4u(const uint32_t (&u)[4], const uint32_t (&v)[4], const bool (&ok)[4]) {
+        uint32_t x[4], y[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            x[j] = ok[j] ? ld_rel(P + u[j]) : 0;
+            y[j] = ok[j] ? ld_rel(P + v[j]) : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (!ok[j]) continue;
+            if (y[j] < x[j] && __ldg(prev + x[j]) == x[j]) hit |= atomicMin(P + x[j], y[j]) > y[j];
+            if (x[j] < y[j] && __ldg(prev + y[j]) == y[j]) hit |= atomicMin(P + y[j], x[j]) > x[j];
         }
     }
     __device__ __forceinline__ void flush() {
@@ -571,6 +607,14 @@ struct BFSEdge {
             if (forest) forest[w] = make_uint2(u, w);
             next[append_one(nnext)] = w;
             my_min = w < my_min ? w : my_min;
+        }
+    }
+    __device__ __forceinline__ void apply4u(const uint32_t (&u)[4], const uint32_t (&v)[4], const bool (&ok)[4]) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const bool one[4] = {ok[j], false, false, false};
+            const uint32_t w[4] = {v[j], 0, 0, 0};
+            apply4(u[j], w, one);
         }
     }
     __device__ __forceinline__ void flush() {
@@ -674,18 +718,30 @@ __global__ void __launch_bounds__(256, 8) k_bfs_relabel(uint32_t *P, const uint3
 // small; one launch sequence and one host round trip per level would
 // dominate.  Here every block of a cooperative launch runs level after level
 // with a grid barrier between them, and the launch returns to the host once
-// the frontier is empty, its edges exceed `mf_max`, or the direction rule
-// asks for bottom-up (frontier edges > unexplored / 14).
+// the frontier is empty or holds more than BFS_LOOP_NF_MAX vertices, its
+// edges exceed `mf_max`, or the direction rule asks for bottom-up (frontier
+// edges > unexplored / 14).
 // Frontier counts and edge sums rotate over three slots: level L reads slot
 // L % 3, appends into slot (L + 1) % 3, and clears slot (L + 2) % 3, which no
 // block reads after the barrier that ended level L - 1.  The edge sum a level
 // leaves for the next is its own frontier's (read with the offsets it loads
 // anyway), so the direction rule looks one level behind: that changes when
-// the launch hands over to bottom-up, never which vertices are reached.
+// the launch hands over to bottom-up, never which vertices are reached (the
+// host takes the exact sum of the frontier it is handed).
+// A frontier vertex of degree > BFS_HUB_DEG (a hub) is not left to one warp
+// of this launch (a few warps per SM): its edges go to the chunk list as
+// CHUNK-edge pieces, and after the level's barrier the launch ends with the
+// level pending; the host runs the pieces as a full-occupancy chunk pass,
+// which completes the level.  Every block reads the same piece count after
+// the barrier, so all blocks leave together.
+constexpr uint64_t BFS_HUB_DEG = 1024;
+
 struct BfsLoop {
     GridBar bar;
     uint32_t cnt[3];
     uint32_t levels;
+    uint32_t npiece[3];
+    uint32_t pending;   // 1: level `levels` ran but its hubs' pieces (npiece[levels % 3]) did not
     unsigned long long mfc[3];
     unsigned long long reached;    // vertices claimed by the levels run
     unsigned long long explored;   // frontier edges of the levels run
@@ -714,11 +770,24 @@ struct BFSPushEdge {
             my_min = w < my_min ? w : my_min;
         }
     }
+    __device__ __forceinline__ void apply4u(const uint32_t (&u)[4], const uint32_t (&v)[4], const bool (&ok)[4]) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const bool one[4] = {ok[j], false, false, false};
+            const uint32_t w[4] = {v[j], 0, 0, 0};
+            apply4(u[j], w, one);
+        }
+    }
 };
 
 constexpr unsigned BFS_LOOP_TPB = 512;
 constexpr uint64_t BFS_LOOP_MF_MAX = 1ull << 24;   // frontier edges beyond which a level runs as its own launches
 constexpr uint32_t BFS_LOOP_LEVELS = 1u << 16;      // levels per launch at most (a launch stays well under a second)
+// frontier vertices beyond which a level runs as its own launches: the
+// launch's edge estimate lags one level, and a frontier this large (an
+// R-MAT level past the hubs) is where the lag would keep a level top-down
+// that the exact count sends bottom-up; high-diameter frontiers stay far below
+constexpr uint32_t BFS_LOOP_NF_MAX = 1u << 17;
 
 template <typename OffT>
 __global__ void __launch_bounds__(BFS_LOOP_TPB, 2) k_bfs_push_levels(const OffT *I, const uint32_t *A, uint32_t n,
@@ -727,7 +796,8 @@ __global__ void __launch_bounds__(BFS_LOOP_TPB, 2) k_bfs_push_levels(const OffT 
                                                                   BfsLoop *L, uint32_t *cnt_out0,
                                                                   uint32_t *cnt_out1, uint32_t *minv,
                                                                   uint64_t unexplored0, uint64_t mf_max,
-                                                                  uint32_t max_levels, Dev d) {
+                                                                  uint32_t max_levels, ChunkRef *chunks,
+                                                                  uint64_t chunk_cap, Dev d) {
     const int lane = threadIdx.x & 31;
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -739,12 +809,13 @@ __global__ void __launch_bounds__(BFS_LOOP_TPB, 2) k_bfs_push_levels(const OffT 
         const uint64_t mf = ld_rel64(&L->mfc[lv % 3]);
         if (lv > 0) reached += nf;
         const uint64_t unexplored = unexplored0 > explored ? unexplored0 - explored : 0;
-        if (nf == 0 || lv == max_levels || mf > mf_max || mf > unexplored / 14) break;
+        if (nf == 0 || lv == max_levels || nf > BFS_LOOP_NF_MAX || mf > mf_max || mf > unexplored / 14) break;
         uint32_t *cur = (lv & 1) ? q1 : q0;
         uint32_t *nx = (lv & 1) ? q0 : q1;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             L->cnt[(lv + 2) % 3] = 0;
             L->mfc[(lv + 2) % 3] = 0;
+            L->npiece[(lv + 2) % 3] = 0;
         }
         BFSPushEdge f{P, vis, nx, &L->cnt[(lv + 1) % 3], src, NONE, 0ull, d};
         for (uint64_t base = warp * 32; base < nf; base += nwarps * 32) {
@@ -754,9 +825,16 @@ __global__ void __launch_bounds__(BFS_LOOP_TPB, 2) k_bfs_push_levels(const OffT 
             if (act) vertex_range(I, u, m, b, e, d);
             f.my_edges += e - b;
             const bool heavy = e - b > LIGHT_MAX;
-            if (act && !heavy) light_edges(u, b, e, A, n, f, d);
-            // heavier vertices: the whole warp walks their edges
-            uint32_t hm = __ballot_sync(0xFFFFFFFFu, heavy);
+            const uint32_t npc = e - b > BFS_HUB_DEG ? (uint32_t)((e - b + CHUNK - 1) / CHUNK) : 0;
+            const uint32_t slot = warp_append_full(&L->npiece[lv % 3], npc);
+            // the list has room for every heavy vertex's pieces; past it
+            // (not reached) the warp walks the hub itself
+            const bool hub = npc && (uint64_t)slot + npc <= chunk_cap;
+            if (hub)
+                for (uint32_t c = 0; c < npc; ++c) chunks[slot + c] = ChunkRef{u, c};
+            warp_light_edges(u, b, heavy ? 0u : (uint32_t)(e - b), A, n, f, d);
+            // heavier vertices short of a hub: the whole warp walks their edges
+            uint32_t hm = __ballot_sync(0xFFFFFFFFu, heavy && !hub);
             while (hm) {
                 const int l = __ffs(hm) - 1;
                 hm &= hm - 1;
@@ -768,9 +846,13 @@ __global__ void __launch_bounds__(BFS_LOOP_TPB, 2) k_bfs_push_levels(const OffT 
         unsigned long long me = f.my_edges;
         for (int o = 16; o > 0; o >>= 1) me += __shfl_xor_sync(0xFFFFFFFFu, me, o);
         if (lane == 0 && me) atomicAdd(&L->mfc[(lv + 1) % 3], me);
-        my_min = f.my_min < my_min ? f.my_min : my_min;
         explored += mf;
         if (!grid_sync(&L->bar, d)) break;
+        my_min = f.my_min < my_min ? f.my_min : my_min;
+        if (ld_rel(&L->npiece[lv % 3])) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) L->pending = 1;
+            break;
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
         const uint32_t t = __shfl_xor_sync(0xFFFFFFFFu, my_min, o);
@@ -824,6 +906,19 @@ struct LDDEdge {
             if (vis[w >> 5] & (1u << (w & 31))) continue;
             if (ld_rel(cand + w) <= c) continue;
             if (atomicMin(cand + w, c) == NONE) next[append_one(nnext)] = w;
+        }
+    }
+    __device__ __forceinline__ void apply4u(const uint32_t (&u)[4], const uint32_t (&v)[4], const bool (&ok)[4]) {
+        uint32_t c[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) c[j] = ok[j] ? P[u[j]] : NONE;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (!ok[j]) continue;
+            const uint32_t w = v[j];
+            if (vis[w >> 5] & (1u << (w & 31))) continue;
+            if (ld_rel(cand + w) <= c[j]) continue;
+            if (atomicMin(cand + w, c[j]) == NONE) next[append_one(nnext)] = w;
         }
     }
     __device__ __forceinline__ void flush() {}
@@ -1181,10 +1276,12 @@ cc_status bfs_sample(const Graph &g, const cc_sample_opt &so, uint32_t *P, Work 
                     uint64_t mm = g.m;
                     const OffT *Ip = I;
                     const uint32_t *Ap = g.A;
+                    ChunkRef *ck = chunks;
+                    uint64_t ccap = w.chunk_cap;
                     Dev dd = d;
                     void *args[] = {&Ip, &Ap, &nn, &mm, &P, &vis, &qc, &qn, &srcv, &loop, &c0, &c1, &mv,
                                     const_cast<uint64_t *>(&unexplored0), const_cast<uint64_t *>(&mfmax), &maxl,
-                                    &dd};
+                                    &ck, &ccap, &dd};
                     {
                         CC_PROF("k_bfs_push_levels", s);
                         CC_TRY(cudaLaunchCooperativeKernel((const void *)k_bfs_push_levels<OffT>, loop_grid,
@@ -1194,13 +1291,53 @@ cc_status bfs_sample(const Graph &g, const cc_sample_opt &so, uint32_t *P, Work 
                     CC_TRY(cudaStreamSynchronize(s));
                     if (hloop->bar.abort) return CC_ERR_NONCONVERGED;
                     const uint32_t L = hloop->levels;
+                    if (hloop->pending) {
+                        // level L ran but for its hubs' pieces: run them at
+                        // full occupancy, then its next frontier is complete
+                        const int qc = (L & 1) ? nx : cur, qn = qc ^ 1;
+                        BFSEdge f{P, vis, q[qn], &loop->cnt[(L + 1) % 3], &ctl->minv, src, NONE, d.forest};
+                        {
+                            CC_PROF("k_chunks", s);
+                            k_chunks<OffT, BFSEdge><<<grid_for(di, (uint64_t)1 << 40, TPB), TPB, 0, s>>>(
+                                I, g.A, n, g.m, chunks, &loop->npiece[L % 3], w.chunk_cap, f, d);
+                        }
+                        CC_LAUNCH();
+                        CC_TRY(cudaMemcpyAsync(&ctl->nfront[qn], &loop->cnt[(L + 1) % 3], 4, cudaMemcpyDeviceToDevice,
+                                               s));
+                        CC_TRY(cudaMemsetAsync(&ctl->mf[qn], 0, 8, s));
+                        {
+                            CC_PROF("k_list_degrees", s);
+                            k_list_degrees<OffT><<<gv, TPB, 0, s>>>(I, g.m, q[qn], &ctl->nfront[qn], &ctl->mf[qn], d);
+                        }
+                        CC_LAUNCH();
+                        CC_TRY(cudaMemcpyAsync(&hl->nnext, &ctl->nfront[qn], 4, cudaMemcpyDeviceToHost, s));
+                        CC_TRY(cudaMemcpyAsync(&hl->mf, &ctl->mf[qn], 8, cudaMemcpyDeviceToHost, s));
+                        CC_TRY(cudaStreamSynchronize(s));
+                        nf = hl->nnext;
+                        mf = hl->mf;
+                        reached += hloop->reached + nf;
+                        explored_edges += hloop->explored;
+                        level += L;
+                        cur = qn;
+                        continue;
+                    }
                     if (L > 0) {
                         if (L & 1) cur = nx;
                         nf = hloop->cnt[L % 3];
-                        mf = hloop->mfc[L % 3];
                         reached += hloop->reached;
                         explored_edges += hloop->explored;
                         level += L - 1;
+                        // the launch's edge sum for the frontier it hands
+                        // over is one level behind: take the exact one
+                        CC_TRY(cudaMemsetAsync(&ctl->mf[cur], 0, 8, s));
+                        {
+                            CC_PROF("k_list_degrees", s);
+                            k_list_degrees<OffT><<<gv, TPB, 0, s>>>(I, g.m, q[cur], &ctl->nfront[cur], &ctl->mf[cur], d);
+                        }
+                        CC_LAUNCH();
+                        CC_TRY(cudaMemcpyAsync(&hl->mf, &ctl->mf[cur], 8, cudaMemcpyDeviceToHost, s));
+                        CC_TRY(cudaStreamSynchronize(s));
+                        mf = hl->mf;
                         continue;
                     }
                 }
