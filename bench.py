@@ -312,6 +312,20 @@ def run_ours(args):
         probes[name] = {"ms": round(pms, 4), "gedges_s": round(m / (pms * 1e-3) / 1e9, 2),
                         "csr_gbs": round((off_bytes * (n + 1) + 4 * m) / (pms * 1e-3) / 1e9, 1)}
     del xs, pout
+    # random-sector reads of the edge array (larger than L2), one per k-out
+    # pick: the rate the sampling kernel's random edge reads can reach
+    rs = 2 * n_nz
+    cc.cc_random_sectors(edg, rs, seed=3)
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record()
+    for _ in range(3):
+        cc.cc_random_sectors(edg, rs, seed=3)
+    p1.record()
+    torch.cuda.synchronize()
+    pms = p0.elapsed_time(p1) / 3
+    probes["random_sectors"] = {"ms": round(pms, 4), "reads": rs, "sector_gbs": round(32 * rs / (pms * 1e-3) / 1e9, 1)}
+    if roof is not None:
+        roof["random_sector_gbs"] = probes["random_sectors"]["sector_gbs"]
 
     # spanning forest with the same sampling and finish (the edges that
     # hooked roots are recorded as they are linked)

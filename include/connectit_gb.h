@@ -252,6 +252,19 @@ cc_status cc_map_edges(const void *offsets, int offsets_u64, const uint32_t *edg
 cc_status cc_gather_edges(const void *offsets, int offsets_u64, const uint32_t *edges, uint32_t n, uint64_t m,
                           const uint32_t *x, uint32_t *out, void *stream);
 
+/* Random-sector read rate: for i < count, read word
+ * floor(draw64(seed, i) * words / 2^64) of the device array x (uint32_t[words]),
+ * where draw64 is SplitMix64 (Steele, Lea and Flood, 2014):
+ * z = seed + (i + 1) * 0x9E3779B97F4A7C15, then the stafford-13 finaliser.
+ * *out (one device uint32) = the sum of the words read, mod 2^32.  Each read
+ * is one 32-byte sector at an unrelated position: on an array larger than
+ * L2 it measures the device's rate for the access a k-out pick makes (one
+ * random sector of the edge array), the ceiling of that sampling kernel.
+ * Errors: CC_ERR_INVALID for a null or unaligned pointer, or words == 0
+ * with count > 0.  Stream-ordered; *out is zeroed first on the stream. */
+cc_status cc_random_sectors(const uint32_t *x, uint64_t words, uint64_t count, uint64_t seed, uint32_t *out,
+                            void *stream);
+
 /* Batched static connectivity of many independent graphs in one persistent
  * launch (no counterpart in the paper, which labels one graph per call).
  * Each graph is labelled as Algorithm 1 with no sampling would label it:

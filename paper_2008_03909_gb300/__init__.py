@@ -138,6 +138,8 @@ _SIGS = {
                                     ctypes.c_void_p, ctypes.c_void_p]),
     "cc_gather_edges": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint32,
                                        ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "cc_random_sectors": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                         ctypes.c_void_p, ctypes.c_void_p]),
     "cc_features": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64,
                                    ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]),
     "cc_mlp_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]),
@@ -454,6 +456,18 @@ def cc_gather_edges(offsets, edges, x, out=None, stream=None) -> torch.Tensor:
         out = torch.empty(n, dtype=torch.int32, device=offsets.device)
     _check(lib().cc_gather_edges(Ip, u64, Ap, n, m, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                                  _stream(stream)), "cc_gather_edges")
+    return out
+
+
+def cc_random_sectors(x, count: int, seed: int = 1, out=None, stream=None) -> torch.Tensor:
+    """Random-sector reads: the sum mod 2^32 of `count` seeded random words of x
+    (int32 CUDA tensor), one device word."""
+    _dev(x, (torch.int32,), "x")
+    if out is None:
+        out = torch.empty(1, dtype=torch.int32, device=x.device)
+    _check(lib().cc_random_sectors(ctypes.c_void_p(x.data_ptr()), ctypes.c_uint64(x.numel()), ctypes.c_uint64(count),
+                                   ctypes.c_uint64(seed), ctypes.c_void_p(out.data_ptr()), _stream(stream)),
+           "cc_random_sectors")
     return out
 
 

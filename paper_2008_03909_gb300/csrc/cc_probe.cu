@@ -98,6 +98,28 @@ __global__ void __launch_bounds__(256, 8) k_probe_chunks(const OffT *I, const ui
     }
 }
 
+// Random sectors: word draw64(seed, i) * words / 2^64 of x for i < count,
+// eight independent loads in flight per thread, summed mod 2^32 into *out.
+// Each load touches one 32-byte sector at a position no neighbouring load
+// shares: on an array larger than L2 this is the device's rate for the
+// access that the k-out picks make (one random sector per pick).
+__global__ void __launch_bounds__(256, 8) k_probe_sectors(const uint32_t *x, uint64_t words, uint64_t count,
+                                                          uint64_t seed, uint32_t *out) {
+    const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    uint32_t acc = 0;
+    for (uint64_t i0 = tid * 8; i0 < count; i0 += stride * 8) {
+        uint32_t v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            v[j] = i0 + j < count ? ld_stream(x + __umul64hi(draw64(seed, i0 + j), words)) : 0u;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc += v[j];
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
+}
+
 template <typename OffT, int MODE>
 cc_status run_probe(const void *offsets, const uint32_t *edges, uint32_t n, uint64_t m, const uint32_t *x,
                     uint32_t *out, cudaStream_t s) {
@@ -129,6 +151,22 @@ cc_status run_probe(const void *offsets, const uint32_t *edges, uint32_t n, uint
 }  // namespace
 
 extern "C" {
+
+cc_status cc_random_sectors(const uint32_t *x, uint64_t words, uint64_t count, uint64_t seed, uint32_t *out,
+                            void *stream) {
+    if (!x || !out || !aligned(x, 4) || !aligned(out, 4) || (words == 0 && count > 0)) return CC_ERR_INVALID;
+    const DeviceInfo *di = device_info();
+    if (!di) return CC_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(out, 0, 4, s);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (count == 0) return CC_OK;
+    {
+        CC_PROF("k_probe_sectors", s);
+        k_probe_sectors<<<grid_for(di, (count + 7) / 8, TPB), TPB, 0, s>>>(x, words, count, seed, out);
+    }
+    return from_cuda(cudaGetLastError());
+}
 
 cc_status cc_map_edges(const void *offsets, int offsets_u64, const uint32_t *edges, uint32_t n, uint64_t m,
                        uint32_t *out, void *stream) {

@@ -314,3 +314,24 @@ def test_map_and_gather_edges_bit_exact(u64):
         src = np.repeat(np.arange(g.n), np.diff(o))
         np.add.at(want, src, x[e.astype(np.int64)].astype(np.uint64))
         assert np.array_equal(got, (want % 2**32).astype(np.uint32))
+
+
+def _splitmix64(seed, ctr):
+    """SplitMix64 (Steele, Lea and Flood, 2014) at counter ctr, in Python integers."""
+    M = (1 << 64) - 1
+    z = (seed + (ctr + 1) * 0x9E3779B97F4A7C15) & M
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M
+    return z ^ (z >> 31)
+
+
+@pytest.mark.parametrize("words,count", [(1, 5), (1000, 3), (123457, 10001), (1 << 20, 1 << 16)])
+def test_random_sectors_sum(words, count):
+    """The random-sector probe reads exactly the words its definition names."""
+    x = np.random.default_rng(words).integers(0, 2**32, size=words, dtype=np.uint64).astype(np.uint32)
+    got = cc.cc_random_sectors(torch.from_numpy(x.view(np.int32)).cuda(), count, seed=77)
+    idx = [(_splitmix64(77, i) * words) >> 64 for i in range(count)]
+    want = int(x[np.array(idx, dtype=np.int64)].astype(np.uint64).sum()) % 2**32
+    assert int(got.cpu().numpy().view(np.uint32)[0]) == want
+    empty = cc.cc_random_sectors(torch.from_numpy(x.view(np.int32)).cuda(), 0)
+    assert int(empty.item()) == 0
