@@ -89,7 +89,11 @@ struct Ctl {
     unsigned long long key;
     unsigned long long edges;
     unsigned long long mf[2];
-    uint32_t pad[15];
+    unsigned long long ldd_explored;   // LDD: frontier edges of the rounds so far
+    uint32_t ldd_pull;                 // LDD: 1 while the rounds run bottom-up
+    uint32_t ldd_push_nf;              // LDD: the frontier size the top-down kernels see (0 bottom-up)
+    uint32_t ldd_pull_chunks;          // LDD: chunk count of a bottom-up round
+    uint32_t pad[10];
 };
 
 // Launch accounting: one scope per kernel launch.  Counts every launch and,

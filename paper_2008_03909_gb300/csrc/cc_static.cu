@@ -939,6 +939,105 @@ __global__ void __launch_bounds__(256, 8) k_ldd_commit(uint32_t *P, uint32_t *vi
     if (blockIdx.x == 0 && threadIdx.x == 0 && total) atomicMax(last_round, round + 1);
 }
 
+// Bottom-up LDD rounds (direction optimisation, as for BFS): once the
+// frontier's edges exceed 1/14 of the edges not yet explored, every
+// uncovered vertex looks for a frontier neighbour instead of the frontier
+// pushing to every neighbour; a round stays bottom-up while the frontier
+// holds at least n/24 vertices.  Beside its edge count, the frontier is
+// marked in a bitmap (every round, so a round can switch).  ldd_push_nf is
+// the frontier size the top-down kernels see: 0 in a bottom-up round.
+template <typename OffT>
+__global__ void __launch_bounds__(256, 8) k_ldd_front(const OffT *I, uint64_t m, const uint32_t *list,
+                                                      const uint32_t *count, uint32_t *fbm,
+                                                      unsigned long long *out, Dev d) {
+    const uint32_t total = *count;
+    unsigned long long s = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t u = list[i];
+        uint64_t b, e;
+        vertex_range(I, u, m, b, e, d);
+        s += e - b;
+        atomicOr(fbm + (u >> 5), 1u << (u & 31));
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
+}
+
+__global__ void k_ldd_direction(Ctl *ctl, int cur, uint32_t n, uint64_t m) {
+    const unsigned long long mf = ctl->mf[cur], ex = ctl->ldd_explored;
+    const uint32_t nf = ctl->nfront[cur];
+    const unsigned long long unexplored = m > ex ? m - ex : 0;
+    const uint32_t pull = ctl->ldd_pull ? (nf >= n / 24) : (mf > unexplored / 14);
+    ctl->ldd_pull = pull;
+    ctl->ldd_push_nf = pull ? 0u : nf;
+    ctl->ldd_explored = ex + mf;
+}
+
+// A bottom-up round scans the uncovered vertices' edges instead: an
+// uncovered w with a frontier neighbour y takes P[y] as a candidate by the
+// same writeMin as a top-down claim, so w ends the round with the smallest
+// centre among its frontier neighbours either way, and the clustering does
+// not depend on the direction.  The first candidate queues w for the commit.
+struct LDDPullEdge {
+    const uint32_t *P;
+    const uint32_t *fbm;
+    uint32_t *cand;
+    uint32_t *next;
+    uint32_t *nnext;
+    __device__ __forceinline__ void offer(uint32_t w, uint32_t y) {
+        if (!((fbm[y >> 5] >> (y & 31)) & 1u)) return;
+        const uint32_t c = P[y];
+        if (ld_rel(cand + w) <= c) return;
+        if (atomicMin(cand + w, c) == NONE) next[append_one(nnext)] = w;
+    }
+    __device__ __forceinline__ void apply4(uint32_t w, const uint32_t (&y)[4], const bool (&ok)[4]) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (ok[j]) offer(w, y[j]);
+    }
+    __device__ __forceinline__ void apply4u(const uint32_t (&w)[4], const uint32_t (&y)[4], const bool (&ok)[4]) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (ok[j]) offer(w[j], y[j]);
+    }
+    __device__ __forceinline__ void flush() {}
+};
+
+// The uncovered vertices' edges in a bottom-up round (nothing in a
+// top-down round): lane L of a warp step takes vertex base + L when its
+// `vis` bit is clear; light ones are walked by the warp together, heavier
+// ones go to the chunk list.
+template <typename OffT>
+__global__ void __launch_bounds__(256, 8) k_ldd_pull_bin(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m,
+                                                         const uint32_t *vis, LDDPullEdge f, ChunkRef *chunks,
+                                                         uint32_t *nchunks, uint64_t cap, const Ctl *ctl, Dev d) {
+    if (!ctl->ldd_pull) return;
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t base = warp * 32; base < n; base += nw * 32) {
+        const uint32_t vword = vis[base >> 5];
+        if (vword == 0xFFFFFFFFu) continue;   // warp-uniform
+        const uint64_t w = base + lane;
+        uint64_t b = 0, e = 0;
+        if (w < n && !((vword >> lane) & 1u)) vertex_range(I, (uint32_t)w, m, b, e, d);
+        const uint64_t deg = e - b;
+        const uint32_t nc = deg > LIGHT_MAX ? (uint32_t)((deg + CHUNK - 1) / CHUNK) : 0;
+        const uint32_t slot = warp_append_full(nchunks, nc);
+        if (nc) write_chunks(chunks, cap, slot, nc, (uint32_t)w, d);
+        warp_light_edges((uint32_t)w, b, nc ? 0u : (uint32_t)deg, A, n, f, d);
+    }
+}
+
+// Clear the frontier's bitmap words, so the bitmap is empty for the next round.
+__global__ void __launch_bounds__(256, 8) k_ldd_unmark(const uint32_t *list, const uint32_t *count, uint32_t *bm) {
+    const uint32_t total = *count;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        bm[list[i] >> 5] = 0u;
+}
+
 // Spanning-forest edges of the LDD clusters (the searches' tree edges,
 // assigned to the child): a non-centre w was claimed in step t by a
 // frontier vertex of its own cluster that joined in step t - 1, so such a
@@ -1135,6 +1234,8 @@ void plan(Work &w, const Graph &g, int sample_kind, uint32_t freq_samples, int f
         w.o_q0 = w.sc.reserve(n * 4);
         w.o_q1 = w.sc.reserve(n * 4);
         w.o_cand = w.sc.reserve(n * 4);
+        w.o_bm0 = w.sc.reserve(words * 4);   // bottom-up rounds: the frontier's bitmap
+
     }
 }
 
@@ -1399,10 +1500,12 @@ cc_status ldd_sample(const Graph &g, const cc_sample_opt &so, uint32_t *P, Work 
     uint32_t *q[2] = {w.sc.at<uint32_t>(w.o_q0), w.sc.at<uint32_t>(w.o_q1)};
     uint32_t *cand = w.sc.at<uint32_t>(w.o_cand);
     uint32_t *stamp = d.forest ? w.sc.at<uint32_t>(w.o_stamp) : nullptr;
+    uint32_t *fbm = w.sc.at<uint32_t>(w.o_bm0);
     ChunkRef *chunks = w.sc.at<ChunkRef>(w.o_chunks);
     const unsigned gv = grid_for(di, n, TPB);
     const unsigned gc = grid_for(di, (uint64_t)1 << 40, TPB);
     CC_TRY(cudaMemsetAsync(vis, 0, words * 4, s));
+    CC_TRY(cudaMemsetAsync(fbm, 0, words * 4, s));
     CC_TRY(cudaMemsetAsync(cand, 0xFF, (size_t)n * 4, s));
     CC_TRY(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
     uint64_t S = 0;
@@ -1425,20 +1528,47 @@ cc_status ldd_sample(const Graph &g, const cc_sample_opt &so, uint32_t *P, Work 
         }
         CC_TRY(cudaMemsetAsync(&ctl->nfront[nx], 0, 4, s));
         CC_TRY(cudaMemsetAsync(&ctl->nchunks, 0, 4, s));
+        CC_TRY(cudaMemsetAsync(&ctl->mf[cur], 0, 8, s));
+        CC_TRY(cudaMemsetAsync(&ctl->ldd_pull_chunks, 0, 4, s));
+        {
+            CC_PROF("k_ldd_front", s);
+            k_ldd_front<OffT><<<gv, TPB, 0, s>>>(I, g.m, q[cur], &ctl->nfront[cur], fbm, &ctl->mf[cur], d);
+        }
+        {
+            CC_PROF("k_ldd_direction", s);
+            k_ldd_direction<<<1, 1, 0, s>>>(ctl, cur, n, g.m);
+        }
+        // top-down (the frontier size these see is 0 in a bottom-up round)
         LDDEdge f{P, vis, cand, q[nx], &ctl->nfront[nx]};
         {
             CC_PROF("k_list_bin", s);
-            k_list_bin<OffT, LDDEdge><<<gv, TPB, 0, s>>>(I, g.A, n, g.m, q[cur], &ctl->nfront[cur], f, chunks,
+            k_list_bin<OffT, LDDEdge><<<gv, TPB, 0, s>>>(I, g.A, n, g.m, q[cur], &ctl->ldd_push_nf, f, chunks,
                                                          &ctl->nchunks, w.chunk_cap, d);
         }
         {
             CC_PROF("k_chunks", s);
             k_chunks<OffT, LDDEdge><<<gc, TPB, 0, s>>>(I, g.A, n, g.m, chunks, &ctl->nchunks, w.chunk_cap, f, d);
         }
+        // bottom-up (returns at once in a top-down round)
+        LDDPullEdge fp{P, fbm, cand, q[nx], &ctl->nfront[nx]};
+        {
+            CC_PROF("k_ldd_pull_bin", s);
+            k_ldd_pull_bin<OffT><<<gv, TPB, 0, s>>>(I, g.A, n, g.m, vis, fp, chunks, &ctl->ldd_pull_chunks,
+                                                    w.chunk_cap, ctl, d);
+        }
+        {
+            CC_PROF("k_chunks", s);
+            k_chunks<OffT, LDDPullEdge><<<gc, TPB, 0, s>>>(I, g.A, n, g.m, chunks, &ctl->ldd_pull_chunks,
+                                                           w.chunk_cap, fp, d);
+        }
         {
             CC_PROF("k_ldd_commit", s);
             k_ldd_commit<<<gv, TPB, 0, s>>>(P, vis, cand, q[nx], &ctl->nfront[nx], &ctl->last_round, r, stamp,
                                             r + 1);
+        }
+        {
+            CC_PROF("k_ldd_unmark", s);
+            k_ldd_unmark<<<gv, TPB, 0, s>>>(q[cur], &ctl->nfront[cur], fbm);
         }
         CC_TRY(cudaMemsetAsync(&ctl->nfront[cur], 0, 4, s));
         CC_LAUNCH();
