@@ -106,31 +106,61 @@ __global__ void __launch_bounds__(256, 8) k_mark_frequent(const uint32_t *P, uin
 __device__ __forceinline__ bool in_bm(const uint32_t *bm, uint32_t v) { return (bm[v >> 5] >> (v & 31)) & 1u; }
 
 // ---------------------------------------------------------------- weighted edge walk
-// Light vertices (degree <= LIGHT_MAX) one per thread, four loads in
-// flight; the heavier ones as CHUNK-edge pieces, one warp each, so a hub's
-// edges spread over the whole grid.  Vertices whose bit is set in skip are
-// not read.  F provides begin() / end() (per block), want(w) (is the edge
-// read at all) and (u, v, w).
+// Light vertices (degree <= LIGHT_MAX) are walked by their warp together,
+// the 32 lanes' edge lists concatenated (the same walk as
+// warp_light_edges), so one load instruction reads 32 consecutive weights;
+// the heavier ones as CHUNK-edge pieces, one warp each, so a hub's edges
+// spread over the whole grid.  Vertices whose bit is set in skip are not
+// read.  F provides begin() / end() (per block), want(w) (is the edge read
+// at all) and (u, v, w).  Weights are read first: an edge whose weight the
+// pass does not want costs no edge read.
 template <class F>
-__device__ __forceinline__ void light_wedges(uint32_t u, uint64_t b, uint64_t e, const uint32_t *A, const float *W,
-                                             uint32_t n, F &f, const Dev &d) {
-    for (uint64_t x = b; x < e; x += 4) {
-        uint32_t v[4];
+__device__ __forceinline__ void warp_light_wedges(uint32_t u, uint64_t b, uint32_t deg, const uint32_t *A,
+                                                  const float *W, uint32_t n, F &f, const Dev &d) {
+    const unsigned FULL = 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31;
+    uint32_t incl = deg;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const uint32_t excl = incl - deg;
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    const uint64_t rel = b - excl;   // position t of this lane's list is edge rel + t (mod 2^64)
+    for (uint32_t s = 0; s < total; s += 128) {
+        uint32_t uu[4], v[4];
+        uint64_t pos[4];
         float w[4];
         bool ok[4];
-        // weights first: an edge whose weight the pass does not want
-        // costs no edge read
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            w[j] = x + j < e ? __ldcs(W + x + j) : 0.0f;
-            ok[j] = x + j < e && f.want(w[j]);
+            uu[j] = 0;
+            pos[j] = 0;
+            w[j] = 0.0f;
+            ok[j] = false;
+            if (s + 32 * j < total) {   // warp-uniform
+                const uint32_t t = s + 32 * j + lane;
+                int o = 0;
+#pragma unroll
+                for (int k = 16; k > 0; k >>= 1)
+                    if (__shfl_sync(FULL, excl, o + k) <= t) o += k;
+                uu[j] = __shfl_sync(FULL, u, o);
+                pos[j] = __shfl_sync(FULL, rel, o) + t;
+                if (t < total) {
+                    w[j] = __ldcs(W + pos[j]);
+                    ok[j] = true;
+                }
+            }
         }
 #pragma unroll
-        for (int j = 0; j < 4; ++j) v[j] = ok[j] ? ld_stream(A + x + j) : 0;
+        for (int j = 0; j < 4; ++j) ok[j] = ok[j] && f.want(w[j]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[j] = ok[j] ? ld_stream(A + pos[j]) : 0;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             if (ok[j] && v[j] >= n) { atomicOr(d.err, ERR_BAD_EDGE); ok[j] = false; }
-            if (ok[j]) f(u, v[j], w[j]);
+            if (ok[j]) f(uu[j], v[j], w[j]);
         }
     }
 }
@@ -140,14 +170,18 @@ __global__ void __launch_bounds__(256, 8) k_wedges(const OffT *I, const uint32_t
                                                    uint64_t m, const ChunkRef *chunks, const uint32_t *nchunks,
                                                    uint64_t cap, const uint32_t *skip, F f, Dev d) {
     f.begin();
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t u = (uint32_t)i;
-        if (skip && in_bm(skip, u)) continue;
-        uint64_t b, e;
-        vertex_range(I, u, m, b, e, d);
-        if (e - b <= LIGHT_MAX) light_wedges(u, b, e, A, W, n, f, d);
-    }
     const int lane = threadIdx.x & 31;
+    {
+        const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+        const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+        for (uint64_t base = warp * 32; base < n; base += nw * 32) {
+            const uint64_t i = base + lane;
+            uint64_t b = 0, e = 0;
+            if (i < n && !(skip && in_bm(skip, (uint32_t)i))) vertex_range(I, (uint32_t)i, m, b, e, d);
+            const uint64_t deg = e - b;
+            warp_light_wedges((uint32_t)i, b, deg <= LIGHT_MAX ? (uint32_t)deg : 0u, A, W, n, f, d);
+        }
+    }
     const uint32_t total = (uint32_t)((uint64_t)*nchunks < cap ? (uint64_t)*nchunks : cap);
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -309,12 +343,16 @@ __global__ void __launch_bounds__(256, 8) k_compress(uint32_t *P, uint32_t n, De
 // IdentifyFrequent on a flat forest: count the non-roots under their root
 // (a root's count is then its component size minus one, so the arg-max
 // with ties to the smallest label is unchanged), then the arg-max as a
-// packed (count << 32 | ~label) maximum.
+// packed (count << 32 | ~label) maximum.  Counts go through LabelCounter's
+// register slots: once one component holds most vertices, one atomic per
+// vertex on its root's counter would serialise on one address.
 __global__ void __launch_bounds__(256, 8) k_count_flat(const uint32_t *P, uint32_t n, uint32_t *cnt) {
+    LabelCounter lc;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t l = P[i];
-        if (l != (uint32_t)i && l < n) atomicAdd(cnt + l, 1u);
+        if (l != (uint32_t)i && l < n) lc.add(cnt, l);
     }
+    lc.flush(cnt);
 }
 
 __global__ void __launch_bounds__(256, 8) k_argmax(const uint32_t *cnt, uint32_t n, unsigned long long *key) {
