@@ -598,8 +598,9 @@ __device__ __forceinline__ void light_edges(uint32_t u, uint64_t b, uint64_t e, 
 // range, and no lane idles while another walks a longer list.  The owner of
 // position t is the last lane whose exclusive degree prefix is <= t (a
 // five-step shuffle search; a lane with deg = 0 is never that last lane for
-// t below the total).  f.apply4u takes the four edges with their own sources.
-template <class F>
+// t below the total).  f.apply4u takes the four edges with their own sources
+// (with POS, f.apply4p also takes their positions in A).
+template <class F, bool POS = false>
 __device__ __forceinline__ void warp_light_edges(uint32_t u, uint64_t b, uint32_t deg, const uint32_t *A, uint32_t n,
                                                  F &f, const Dev &d) {
     const unsigned FULL = 0xFFFFFFFFu;
@@ -616,11 +617,13 @@ __device__ __forceinline__ void warp_light_edges(uint32_t u, uint64_t b, uint32_
     const uint64_t rel = b - excl;
     for (uint32_t s = 0; s < total; s += 128) {
         uint32_t uu[4], v[4];
+        uint64_t pos[4];
         bool ok[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             uu[j] = 0;
             v[j] = 0;
+            pos[j] = 0;
             ok[j] = false;
             if (s + 32 * j < total) {   // warp-uniform
                 const uint32_t t = s + 32 * j + lane;
@@ -629,15 +632,21 @@ __device__ __forceinline__ void warp_light_edges(uint32_t u, uint64_t b, uint32_
                 for (int k = 16; k > 0; k >>= 1)
                     if (__shfl_sync(FULL, excl, o + k) <= t) o += k;
                 uu[j] = __shfl_sync(FULL, u, o);
-                const uint64_t r = __shfl_sync(FULL, rel, o);
+                pos[j] = __shfl_sync(FULL, rel, o) + t;
                 ok[j] = t < total;
-                v[j] = ok[j] ? ld_stream(A + (r + t)) : uu[j];
+                v[j] = ok[j] ? ld_stream(A + pos[j]) : uu[j];
             }
         }
+        // (with POS a bad edge stays in, flagged: the functor must write
+        // something at its position and checks the id itself)
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-            if (ok[j] && v[j] >= n) { atomicOr(d.err, ERR_BAD_EDGE); ok[j] = false; }
-        f.apply4u(uu, v, ok);
+            if (ok[j] && v[j] >= n) {
+                atomicOr(d.err, ERR_BAD_EDGE);
+                if (!POS) ok[j] = false;
+            }
+        if constexpr (POS) f.apply4p(uu, v, ok, pos);
+        else f.apply4u(uu, v, ok);
     }
 }
 

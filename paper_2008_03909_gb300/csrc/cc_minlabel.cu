@@ -68,12 +68,16 @@ struct RuleTag {
     static constexpr bool r = R;
 };
 
+// lower: every vertex is a candidate (no sampling), so each undirected
+// edge is applied once, from its larger endpoint; the rules offer both
+// ways, so the smaller endpoint's copy would repeat the same offers.
 template <int CONN, bool ROOTUP>
 struct LTRule {
     uint32_t *K;
     const uint32_t *prev;
     Keys ks;
     bool hit;
+    bool lower;
     __device__ __forceinline__ void offer(uint32_t z, uint32_t cand) {
         if (cand < ld_rel(K + z) && (!ROOTUP || prev[z] == ks.key(z))) hit |= atomicMin(K + z, cand) > cand;
     }
@@ -95,12 +99,12 @@ struct LTRule {
     __device__ __forceinline__ void apply4(uint32_t u, const uint32_t (&v)[4], const bool (&ok)[4]) {
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-            if (ok[j]) edge(u, v[j]);
+            if (ok[j] && !(lower && v[j] > u)) edge(u, v[j]);
     }
     __device__ __forceinline__ void apply4u(const uint32_t (&u)[4], const uint32_t (&v)[4], const bool (&ok)[4]) {
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-            if (ok[j]) edge(u[j], v[j]);
+            if (ok[j] && !(lower && v[j] > u[j])) edge(u[j], v[j]);
     }
 };
 
@@ -192,13 +196,28 @@ __global__ void __launch_bounds__(256, 8) k_alter_compact(const uint32_t *Ein, c
 }
 
 // The edge list of every vertex's edges at their CSR positions, for the
-// finish without sampling (every vertex is a candidate): no counter, a
-// self-loop becomes (NONE, NONE).  The candidate lists drive it: light
-// vertices one per thread, heavier ones as CHUNK-edge pieces spread over
-// the grid's warps (a hub's list is not left to one warp).
+// finish without sampling (every vertex is a candidate): no counter.  Each
+// undirected edge is kept once, at its larger endpoint's copy (the connect
+// rules offer both ways, and the symmetric CSR holds the other copy); the
+// smaller endpoint's copy, a self-loop and a bad id become (NONE, NONE).
+// The candidate lists drive it: light vertices walked by their warp
+// together, heavier ones as CHUNK-edge pieces spread over the grid's warps
+// (a hub's list is not left to one warp).
 __device__ __forceinline__ uint2 pair_or_none(uint32_t u, uint32_t v, uint32_t n) {
-    return (v == u || v >= n) ? make_uint2(NONE, NONE) : make_uint2(u, v);
+    return (v >= u || v >= n) ? make_uint2(NONE, NONE) : make_uint2(u, v);
 }
+
+// Writes (u, v) or (NONE, NONE) at each light edge's own CSR position.
+struct PositionPairs {
+    uint2 *e2;
+    uint32_t n;
+    __device__ __forceinline__ void apply4p(const uint32_t (&u)[4], const uint32_t (&v)[4], const bool (&ok)[4],
+                                            const uint64_t (&pos)[4]) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (ok[j]) e2[pos[j]] = pair_or_none(u[j], v[j], n);
+    }
+};
 
 template <typename OffT>
 __global__ void __launch_bounds__(256, 8) k_pairs_at_positions(const OffT *I, const uint32_t *A, uint32_t n,
@@ -208,20 +227,21 @@ __global__ void __launch_bounds__(256, 8) k_pairs_at_positions(const OffT *I, co
                                                                Dev d) {
     uint2 *e2 = reinterpret_cast<uint2 *>(E);
     const uint32_t nl = *nlight;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nl; i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t u = light[i];
-        uint64_t b, e;
-        vertex_range(I, u, m, b, e, d);
-        for (uint64_t x = b; x < e; x += 4) {
-            uint32_t v[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) v[j] = x + j < e ? ld_stream(A + x + j) : 0;
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (x + j < e) e2[x + j] = pair_or_none(u, v[j], n);
+    const int lane = threadIdx.x & 31;
+    {
+        // light candidates: the warp walks its 32 vertices' edges together
+        const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+        const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+        PositionPairs f{e2, n};
+        for (uint64_t base = warp * 32; base < nl; base += nw * 32) {
+            const bool act = base + lane < nl;
+            const uint32_t u = act ? light[base + lane] : 0;
+            uint64_t b = 0, e = 0;
+            if (act) vertex_range(I, u, m, b, e, d);
+            const uint64_t deg = e - b;
+            warp_light_edges<PositionPairs, true>(u, b, deg > LIGHT_MAX ? LIGHT_MAX : (uint32_t)deg, A, n, f, d);
         }
     }
-    const int lane = threadIdx.x & 31;
     const uint32_t total = (uint32_t)((uint64_t)*nchunks < cap ? (uint64_t)*nchunks : cap);
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -280,6 +300,7 @@ struct StergiouRule {
     const uint32_t *prev;
     Keys ks;
     bool hit;
+    bool lower;   // no sampling: each undirected edge from its larger endpoint (both offers are symmetric)
     __device__ __forceinline__ void offer(uint32_t z, uint32_t cand) {
         if (cand < ld_rel(cur + z)) hit |= atomicMin(cur + z, cand) > cand;
     }
@@ -287,7 +308,7 @@ struct StergiouRule {
         const uint32_t ku = prev[u];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            if (!ok[j]) continue;
+            if (!ok[j] || (lower && v[j] > u)) continue;
             const uint32_t kw = prev[v[j]];
             offer(ks.id(ku), kw);
             offer(ks.id(kw), ku);
@@ -295,14 +316,16 @@ struct StergiouRule {
     }
     __device__ __forceinline__ void apply4u(const uint32_t (&u)[4], const uint32_t (&v)[4], const bool (&ok)[4]) {
         uint32_t ku[4], kw[4];
+        bool go[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            ku[j] = ok[j] ? prev[u[j]] : 0;
-            kw[j] = ok[j] ? prev[v[j]] : 0;
+            go[j] = ok[j] && !(lower && v[j] > u[j]);
+            ku[j] = go[j] ? prev[u[j]] : 0;
+            kw[j] = go[j] ? prev[v[j]] : 0;
         }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            if (!ok[j]) continue;
+            if (!go[j]) continue;
             offer(ks.id(ku[j]), kw[j]);
             offer(ks.id(kw[j]), ku[j]);
         }
@@ -507,7 +530,7 @@ cc_status run_minlabel(const MinLabelIn &in, const cc_finish_opt &fo, const Devi
                     return from_cuda(ce);
             if (fo.kind == CC_FINISH_STERGIOU) {
                 CC_PROF("k_stergiou_connect", s);
-                StergiouRule f{K, prev, ks, false};
+                StergiouRule f{K, prev, ks, false, in.lmax_p == nullptr};
                 k_lists<OffT, StergiouRule><<<gv, TPB, 0, s>>>(I, in.A, n, in.m, in.light, in.nlight, in.chunks,
                                                                in.nchunks, in.chunk_cap, f, &fl->changed, d);
             } else {
@@ -516,7 +539,7 @@ cc_status run_minlabel(const MinLabelIn &in, const cc_finish_opt &fo, const Devi
                     constexpr int C = decltype(tag)::c;
                     constexpr bool R = decltype(tag)::r;
                     using Rule = LTRule<C, R>;
-                    Rule f{K, prev, ks, false};
+                    Rule f{K, prev, ks, false, in.lmax_p == nullptr};
                     if (alter) {
                         CC_PROF("k_lt_connect_pairs", s);
                         k_pairs<Rule><<<gv, TPB, 0, s>>>(E[cur], &fl->npairs[cur], f, &fl->changed);
