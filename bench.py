@@ -92,17 +92,18 @@ def job_rate(units_per_rank: int, world: int, ms: float) -> float:
 
 def kernel_traffic(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu capture
-    (profiles/traffic.json), or None when the kernels' source has changed
-    since the counters were taken."""
+    (profiles/traffic.json), or None when the kernels' sources (the files
+    it lists, hashed together) have changed since the counters were taken."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             tj = json.load(f)
         ent = tj["kernels"].get(kernel)
-        src = os.path.join(ROOT, tj["source"])
-        with open(src, "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()
-        if ent is None or sha != tj["source_sha256"]:
+        h = hashlib.sha256()
+        for src in tj["sources"]:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+        if ent is None or h.hexdigest() != tj["sources_sha256"]:
             return None
         return int(ent["bytes_per_launch"])
     except Exception:
