@@ -600,11 +600,39 @@ __device__ __forceinline__ void light_edges(uint32_t u, uint64_t b, uint64_t e, 
 // five-step shuffle search; a lane with deg = 0 is never that last lane for
 // t below the total).  f.apply4u takes the four edges with their own sources
 // (with POS, f.apply4p also takes their positions in A).
+// When the lanes' lists are short and even (a grid, a sparse random graph),
+// each lane walking its own list, four edges a step, takes no more steps
+// and needs no search: the warp does that when ceil(max deg / 4) steps are
+// at most one more than the concatenated walk's ceil(total / 128).
 template <class F, bool POS = false>
 __device__ __forceinline__ void warp_light_edges(uint32_t u, uint64_t b, uint32_t deg, const uint32_t *A, uint32_t n,
                                                  F &f, const Dev &d) {
     const unsigned FULL = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31;
+    const uint32_t mx = __reduce_max_sync(FULL, deg);
+    if ((mx + 3) / 4 <= (__reduce_add_sync(FULL, deg) + 127) / 128 + 1) {   // warp-uniform
+        for (uint32_t x = 0; x < deg; x += 4) {
+            uint32_t uu[4], v[4];
+            uint64_t pos[4];
+            bool ok[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                uu[j] = u;
+                pos[j] = b + x + j;
+                ok[j] = x + j < deg;
+                v[j] = ok[j] ? ld_stream(A + pos[j]) : u;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (ok[j] && v[j] >= n) {
+                    atomicOr(d.err, ERR_BAD_EDGE);
+                    if (!POS) ok[j] = false;
+                }
+            if constexpr (POS) f.apply4p(uu, v, ok, pos);
+            else f.apply4(u, v, ok);
+        }
+        return;
+    }
     uint32_t incl = deg;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {

@@ -92,7 +92,7 @@ struct Ctl {
     unsigned long long ldd_explored;   // LDD: frontier edges of the rounds so far
     uint32_t ldd_pull;                 // LDD: 1 while the rounds run bottom-up
     uint32_t ldd_push_nf;              // LDD: the frontier size the top-down kernels see (0 bottom-up)
-    uint32_t ldd_pull_chunks;          // LDD: chunk count of a bottom-up round
+    uint32_t ldd_done;                 // LDD: blocks of the frontier pass done (the last one decides)
     uint32_t pad[10];
 };
 

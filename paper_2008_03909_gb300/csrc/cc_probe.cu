@@ -34,6 +34,13 @@ struct ProbeFlat {
     const uint32_t *x;
     uint32_t *sums;
     uint64_t base;
+    __device__ __forceinline__ void apply4(uint32_t u, const uint32_t (&v)[4], const bool (&ok)[4]) {
+        uint32_t acc = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (ok[j]) acc += MODE == 0 ? 1u : x[v[j]];
+        if (ok[0]) atomicAdd(sums + (uint32_t)(u - base), acc);
+    }
     __device__ __forceinline__ void apply4u(const uint32_t (&u)[4], const uint32_t (&v)[4], const bool (&ok)[4]) {
         uint32_t val[4];
 #pragma unroll

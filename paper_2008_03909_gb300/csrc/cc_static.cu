@@ -876,18 +876,32 @@ __global__ void __launch_bounds__(BFS_LOOP_TPB, 2) k_bfs_push_levels(const OffT 
 // a vertex claimed in step t has stamp t.
 __global__ void __launch_bounds__(256, 8) k_ldd_wake(uint32_t s0, uint32_t s1, uint32_t *P, uint32_t *vis, uint32_t *front,
                            uint32_t *nfront, uint32_t *last_round, uint32_t round, uint32_t *stamp,
-                           uint32_t step) {
-    bool any = false;
-    for (uint64_t i = s0 + blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < s1;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t v = (uint32_t)i, bit = 1u << (v & 31);
-        if (vis[v >> 5] & bit) continue;
-        atomicOr(vis + (v >> 5), bit);
-        P[v] = v;
-        if (stamp) stamp[v] = step - 1;
-        front[append_one(nfront)] = v;
-        any = true;
+                           uint32_t step, Ctl *ctl, int cur) {
+    // the round's counters start at zero (the next round's frontier count
+    // was cleared when the previous round ended)
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->mf[cur] = 0;
+        ctl->nchunks = 0;
+        ctl->ldd_done = 0;
     }
+    // the uncovered ids of [s0, s1) join the frontier with one atomic per
+    // block (block_compact; only this block touches its ids' bits, so the
+    // two passes see the same ones)
+    bool any = false;
+    block_compact(
+        (uint64_t)(s1 - s0), nfront,
+        [&](uint64_t i) {
+            const uint32_t v = s0 + (uint32_t)i;
+            return !((vis[v >> 5] >> (v & 31)) & 1u);
+        },
+        [&](uint64_t i, uint32_t k) {
+            const uint32_t v = s0 + (uint32_t)i;
+            atomicOr(vis + (v >> 5), 1u << (v & 31));
+            P[v] = v;
+            if (stamp) stamp[v] = step - 1;
+            front[k] = v;
+            any = true;
+        });
     if (any) atomicMax(last_round, round + 1);
 }
 
@@ -924,9 +938,19 @@ struct LDDEdge {
     __device__ __forceinline__ void flush() {}
 };
 
+// With fbm, the same launch also clears the frontier's bitmap words (the
+// frontier list `front`, count *nfront), so the bitmap is empty for the
+// next round.
 __global__ void __launch_bounds__(256, 8) k_ldd_commit(uint32_t *P, uint32_t *vis, uint32_t *cand, const uint32_t *next,
                              const uint32_t *nnext, uint32_t *last_round, uint32_t round, uint32_t *stamp,
-                             uint32_t step) {
+                             uint32_t step, uint32_t *fbm = nullptr, const uint32_t *front = nullptr,
+                             const uint32_t *nfront = nullptr) {
+    if (fbm) {
+        const uint32_t nf = *nfront;
+        for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nf;
+             i += (uint64_t)gridDim.x * blockDim.x)
+            fbm[front[i] >> 5] = 0u;
+    }
     const uint32_t total = *nnext;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
          i += (uint64_t)gridDim.x * blockDim.x) {
@@ -939,39 +963,53 @@ __global__ void __launch_bounds__(256, 8) k_ldd_commit(uint32_t *P, uint32_t *vi
     if (blockIdx.x == 0 && threadIdx.x == 0 && total) atomicMax(last_round, round + 1);
 }
 
-// Bottom-up LDD rounds (direction optimisation, as for BFS): once the
-// frontier's edges exceed 1/14 of the edges not yet explored, every
-// uncovered vertex looks for a frontier neighbour instead of the frontier
-// pushing to every neighbour; a round stays bottom-up while the frontier
-// holds at least n/24 vertices.  Beside its edge count, the frontier is
-// marked in a bitmap (every round, so a round can switch).  ldd_push_nf is
-// the frontier size the top-down kernels see: 0 in a bottom-up round.
+// Bottom-up LDD rounds (direction optimisation, as for BFS): a top-down
+// round reads the frontier's edges, a bottom-up one the uncovered
+// vertices' edges (all of them: the smallest centre is wanted, so a scan
+// cannot stop at the first frontier neighbour), and a round runs bottom-up
+// when the uncovered vertices' edges are fewer than twice the frontier's (a
+// bottom-up edge costs a bit test where a top-down one costs a candidate
+// read and often a writeMin).  Beside its edge count, the frontier is
+// marked in a bitmap every round, so any round can switch.  ldd_push_nf is
+// the frontier size the top-down pass sees: 0 in a bottom-up round.
 template <typename OffT>
-__global__ void __launch_bounds__(256, 8) k_ldd_front(const OffT *I, uint64_t m, const uint32_t *list,
-                                                      const uint32_t *count, uint32_t *fbm,
-                                                      unsigned long long *out, Dev d) {
+__global__ void __launch_bounds__(256, 8) k_ldd_front(const OffT *I, uint32_t n, uint64_t m, const uint32_t *list,
+                                                      const uint32_t *count, uint32_t *fbm, Ctl *ctl, int cur, Dev d) {
     const uint32_t total = *count;
     unsigned long long s = 0;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t u = list[i];
-        uint64_t b, e;
-        vertex_range(I, u, m, b, e, d);
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t base = warp * 32; base < total; base += nw * 32) {
+        const bool act = base + lane < total;
+        const uint32_t u = act ? list[base + lane] : 0;
+        uint64_t b = 0, e = 0;
+        if (act) vertex_range(I, u, m, b, e, d);
         s += e - b;
-        atomicOr(fbm + (u >> 5), 1u << (u & 31));
+        // one OR per distinct bitmap word in the warp
+        const uint32_t word = act ? (u >> 5) : NONE;
+        const unsigned grp = __match_any_sync(0xFFFFFFFFu, word);
+        const uint32_t bits = __reduce_or_sync(grp, act ? 1u << (u & 31) : 0u);
+        if (act && lane == __ffs(grp) - 1) atomicOr(fbm + word, bits);
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
-    if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
-}
-
-__global__ void k_ldd_direction(Ctl *ctl, int cur, uint32_t n, uint64_t m) {
-    const unsigned long long mf = ctl->mf[cur], ex = ctl->ldd_explored;
-    const uint32_t nf = ctl->nfront[cur];
-    const unsigned long long unexplored = m > ex ? m - ex : 0;
-    const uint32_t pull = ctl->ldd_pull ? (nf >= n / 24) : (mf > unexplored / 14);
-    ctl->ldd_pull = pull;
-    ctl->ldd_push_nf = pull ? 0u : nf;
-    ctl->ldd_explored = ex + mf;
+    if (lane == 0 && s) atomicAdd(&ctl->mf[cur], s);
+    // the last block to finish takes the round's direction
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&ctl->ldd_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        const unsigned long long mf = ld_rel64(&ctl->mf[cur]), ex = ctl->ldd_explored;
+        const unsigned long long rest = m > ex + mf ? m - ex - mf : 0;   // edges of the uncovered vertices
+        const uint32_t nf = total;
+        const uint32_t pull = rest < 2 * mf;
+        ctl->ldd_pull = pull;
+        ctl->ldd_push_nf = pull ? 0u : nf;
+        ctl->ldd_explored = ex + mf;
+    }
 }
 
 // A bottom-up round scans the uncovered vertices' edges instead: an
@@ -1001,21 +1039,36 @@ struct LDDPullEdge {
         for (int j = 0; j < 4; ++j)
             if (ok[j]) offer(w[j], y[j]);
     }
-    __device__ __forceinline__ void flush() {}
 };
 
-// The uncovered vertices' edges in a bottom-up round (nothing in a
-// top-down round): lane L of a warp step takes vertex base + L when its
-// `vis` bit is clear; light ones are walked by the warp together, heavier
-// ones go to the chunk list.
+// One LDD round's edge pass, either direction (the flag is the same for
+// every thread): top-down, the frontier list's light vertices are walked
+// by their warp and the heavier ones go to the chunk list; bottom-up, lane
+// L of a warp step takes vertex base + L when its `vis` bit is clear, with
+// the same split.
 template <typename OffT>
-__global__ void __launch_bounds__(256, 8) k_ldd_pull_bin(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m,
-                                                         const uint32_t *vis, LDDPullEdge f, ChunkRef *chunks,
-                                                         uint32_t *nchunks, uint64_t cap, const Ctl *ctl, Dev d) {
-    if (!ctl->ldd_pull) return;
+__global__ void __launch_bounds__(256, 8) k_ldd_bin(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m,
+                                                    const uint32_t *front, const uint32_t *vis, LDDEdge fpush,
+                                                    LDDPullEdge fpull, ChunkRef *chunks, uint32_t *nchunks,
+                                                    uint64_t cap, const Ctl *ctl, Dev d) {
     const int lane = threadIdx.x & 31;
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    if (!ctl->ldd_pull) {
+        const uint32_t total = ctl->ldd_push_nf;
+        for (uint64_t base = warp * 32; base < total; base += nw * 32) {
+            const bool act = base + lane < total;
+            const uint32_t u = act ? front[base + lane] : 0;
+            uint64_t b = 0, e = 0;
+            if (act) vertex_range(I, u, m, b, e, d);
+            const uint64_t deg = e - b;
+            const uint32_t nc = deg > LIGHT_MAX ? (uint32_t)((deg + CHUNK - 1) / CHUNK) : 0;
+            const uint32_t slot = warp_append_full(nchunks, nc);
+            if (nc) write_chunks(chunks, cap, slot, nc, u, d);
+            warp_light_edges(u, b, nc ? 0u : (uint32_t)deg, A, n, fpush, d);
+        }
+        return;
+    }
     for (uint64_t base = warp * 32; base < n; base += nw * 32) {
         const uint32_t vword = vis[base >> 5];
         if (vword == 0xFFFFFFFFu) continue;   // warp-uniform
@@ -1026,17 +1079,18 @@ __global__ void __launch_bounds__(256, 8) k_ldd_pull_bin(const OffT *I, const ui
         const uint32_t nc = deg > LIGHT_MAX ? (uint32_t)((deg + CHUNK - 1) / CHUNK) : 0;
         const uint32_t slot = warp_append_full(nchunks, nc);
         if (nc) write_chunks(chunks, cap, slot, nc, (uint32_t)w, d);
-        warp_light_edges((uint32_t)w, b, nc ? 0u : (uint32_t)deg, A, n, f, d);
+        warp_light_edges((uint32_t)w, b, nc ? 0u : (uint32_t)deg, A, n, fpull, d);
     }
 }
 
-// Clear the frontier's bitmap words, so the bitmap is empty for the next round.
-__global__ void __launch_bounds__(256, 8) k_ldd_unmark(const uint32_t *list, const uint32_t *count, uint32_t *bm) {
-    const uint32_t total = *count;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
-         i += (uint64_t)gridDim.x * blockDim.x)
-        bm[list[i] >> 5] = 0u;
+template <typename OffT>
+__global__ void __launch_bounds__(256, 8) k_ldd_chunks(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m,
+                                                       const ChunkRef *chunks, const uint32_t *nchunks, uint64_t cap,
+                                                       LDDEdge fpush, LDDPullEdge fpull, const Ctl *ctl, Dev d) {
+    if (ctl->ldd_pull) run_chunks(I, A, n, m, chunks, nchunks, cap, fpull, d);
+    else run_chunks(I, A, n, m, chunks, nchunks, cap, fpush, d);
 }
+
 
 // Spanning-forest edges of the LDD clusters (the searches' tree edges,
 // assigned to the child): a non-centre w was claimed in step t by a
@@ -1524,51 +1578,28 @@ cc_status ldd_sample(const Graph &g, const cc_sample_opt &so, uint32_t *P, Work 
             CC_PROF("k_ldd_wake", s);
             k_ldd_wake<<<grid_for(di, S1 - S, TPB), TPB, 0, s>>>((uint32_t)S, (uint32_t)S1, P, vis, q[cur],
                                                                   &ctl->nfront[cur], &ctl->last_round, r, stamp,
-                                                                  r + 1);
+                                                                  r + 1, ctl, cur);
         }
-        CC_TRY(cudaMemsetAsync(&ctl->nfront[nx], 0, 4, s));
-        CC_TRY(cudaMemsetAsync(&ctl->nchunks, 0, 4, s));
-        CC_TRY(cudaMemsetAsync(&ctl->mf[cur], 0, 8, s));
-        CC_TRY(cudaMemsetAsync(&ctl->ldd_pull_chunks, 0, 4, s));
         {
             CC_PROF("k_ldd_front", s);
-            k_ldd_front<OffT><<<gv, TPB, 0, s>>>(I, g.m, q[cur], &ctl->nfront[cur], fbm, &ctl->mf[cur], d);
+            k_ldd_front<OffT><<<gv, TPB, 0, s>>>(I, n, g.m, q[cur], &ctl->nfront[cur], fbm, ctl, cur, d);
+        }
+        LDDEdge fpush{P, vis, cand, q[nx], &ctl->nfront[nx]};
+        LDDPullEdge fpull{P, fbm, cand, q[nx], &ctl->nfront[nx]};
+        {
+            CC_PROF("k_ldd_bin", s);
+            k_ldd_bin<OffT><<<gv, TPB, 0, s>>>(I, g.A, n, g.m, q[cur], vis, fpush, fpull, chunks, &ctl->nchunks,
+                                               w.chunk_cap, ctl, d);
         }
         {
-            CC_PROF("k_ldd_direction", s);
-            k_ldd_direction<<<1, 1, 0, s>>>(ctl, cur, n, g.m);
-        }
-        // top-down (the frontier size these see is 0 in a bottom-up round)
-        LDDEdge f{P, vis, cand, q[nx], &ctl->nfront[nx]};
-        {
-            CC_PROF("k_list_bin", s);
-            k_list_bin<OffT, LDDEdge><<<gv, TPB, 0, s>>>(I, g.A, n, g.m, q[cur], &ctl->ldd_push_nf, f, chunks,
-                                                         &ctl->nchunks, w.chunk_cap, d);
-        }
-        {
-            CC_PROF("k_chunks", s);
-            k_chunks<OffT, LDDEdge><<<gc, TPB, 0, s>>>(I, g.A, n, g.m, chunks, &ctl->nchunks, w.chunk_cap, f, d);
-        }
-        // bottom-up (returns at once in a top-down round)
-        LDDPullEdge fp{P, fbm, cand, q[nx], &ctl->nfront[nx]};
-        {
-            CC_PROF("k_ldd_pull_bin", s);
-            k_ldd_pull_bin<OffT><<<gv, TPB, 0, s>>>(I, g.A, n, g.m, vis, fp, chunks, &ctl->ldd_pull_chunks,
-                                                    w.chunk_cap, ctl, d);
-        }
-        {
-            CC_PROF("k_chunks", s);
-            k_chunks<OffT, LDDPullEdge><<<gc, TPB, 0, s>>>(I, g.A, n, g.m, chunks, &ctl->ldd_pull_chunks,
-                                                           w.chunk_cap, fp, d);
+            CC_PROF("k_ldd_chunks", s);
+            k_ldd_chunks<OffT><<<gc, TPB, 0, s>>>(I, g.A, n, g.m, chunks, &ctl->nchunks, w.chunk_cap, fpush, fpull,
+                                                  ctl, d);
         }
         {
             CC_PROF("k_ldd_commit", s);
             k_ldd_commit<<<gv, TPB, 0, s>>>(P, vis, cand, q[nx], &ctl->nfront[nx], &ctl->last_round, r, stamp,
-                                            r + 1);
-        }
-        {
-            CC_PROF("k_ldd_unmark", s);
-            k_ldd_unmark<<<gv, TPB, 0, s>>>(q[cur], &ctl->nfront[cur], fbm);
+                                            r + 1, fbm, q[cur], &ctl->nfront[cur]);
         }
         CC_TRY(cudaMemsetAsync(&ctl->nfront[cur], 0, 4, s));
         CC_LAUNCH();
