@@ -338,11 +338,18 @@ struct StergiouRule {
 // a smaller neighbour's label (writeMin both ways, so a label held by a
 // vertex whose edges are skipped still spreads through its neighbours'
 // edges); a vertex whose label dropped joins the next frontier once.
+// in_front (bitmap of this round's frontier): an edge whose endpoints are
+// both in the frontier is applied once, from its larger endpoint (the rule
+// is symmetric in the endpoints).
 struct LPRule {
     uint32_t *K;
     uint32_t *mark;      // bitmap: already in the next frontier
     uint32_t *next;
     uint32_t *nnext;
+    const uint32_t *in_front;
+    __device__ __forceinline__ bool twice(uint32_t u, uint32_t w) const {
+        return w > u && ((in_front[w >> 5] >> (w & 31)) & 1u);
+    }
     __device__ __forceinline__ void lowered(uint32_t z) {
         const uint32_t bit = 1u << (z & 31);
         if (ld_rel(mark + (z >> 5)) & bit) return;
@@ -352,7 +359,7 @@ struct LPRule {
     __device__ __forceinline__ void apply4(uint32_t u, const uint32_t (&v)[4], const bool (&ok)[4]) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            if (!ok[j]) continue;
+            if (!ok[j] || twice(u, v[j])) continue;
             const uint32_t ku = ld_rel(K + u), kw = ld_rel(K + v[j]);
             if (ku < kw) {
                 if (atomicMin(K + v[j], ku) > ku) lowered(v[j]);
@@ -400,14 +407,24 @@ __global__ void __launch_bounds__(256, 8) k_frontier(const OffT *I, const uint32
 
 // Initial frontier: every vertex with edges outside the frequent cluster
 // (whose key is 0 when there is one).
+// The frontier's bitmap gets the same vertices (one OR per word per warp).
 template <typename OffT>
 __global__ void __launch_bounds__(256, 8) k_lp_init(const OffT *I, uint32_t n, uint64_t m, const uint32_t *K, Keys ks,
-                                                    uint32_t *list, uint32_t *count, Dev d) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t v = (uint32_t)i;
-        uint64_t b, e;
-        vertex_range(I, v, m, b, e, d);
-        if (e > b && !(ks.m0 != NONE && K[v] == 0)) list[append_one(count)] = v;
+                                                    uint32_t *list, uint32_t *count, uint32_t *in_front, Dev d) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t base = warp * 32; base < n; base += nw * 32) {
+        const uint64_t i = base + lane;
+        bool take = false;
+        if (i < n) {
+            uint64_t b, e;
+            vertex_range(I, (uint32_t)i, m, b, e, d);
+            take = e > b && !(ks.m0 != NONE && K[i] == 0);
+        }
+        const uint32_t bits = __ballot_sync(0xFFFFFFFFu, take);
+        if (lane == 0 && bits) in_front[base >> 5] = bits;
+        if (take) list[append_one(count)] = (uint32_t)i;
     }
 }
 
@@ -444,7 +461,7 @@ cc_status run_minlabel(const MinLabelIn &in, const cc_finish_opt &fo, const Devi
                  o_cmin = sc.reserve((size_t)n * 4);
     const size_t o_e0 = alter ? sc.reserve(cand_edges * 8) : 0, o_e1 = alter ? sc.reserve(cand_edges * 8) : 0;
     const size_t o_q0 = lp ? sc.reserve((size_t)n * 4) : 0, o_q1 = lp ? sc.reserve((size_t)n * 4) : 0,
-                 o_mark = lp ? sc.reserve(words * 4) : 0;
+                 o_mark = lp ? sc.reserve(2 * words * 4) : 0;   // next-frontier marks, this frontier's bitmap
     cc_status st = sc.alloc(s);
     if (st != CC_OK) return st;
     Flags *fl = sc.at<Flags>(o_fl);
@@ -494,10 +511,11 @@ cc_status run_minlabel(const MinLabelIn &in, const cc_finish_opt &fo, const Devi
     int cur = 0;
     if (lp) {
         uint32_t *q[2] = {sc.at<uint32_t>(o_q0), sc.at<uint32_t>(o_q1)};
-        uint32_t *mark = sc.at<uint32_t>(o_mark);
+        uint32_t *bm[2] = {sc.at<uint32_t>(o_mark), sc.at<uint32_t>(o_mark) + words};
+        if ((ce = cudaMemsetAsync(bm[0], 0, words * 4, s)) != cudaSuccess) return from_cuda(ce);
         {
             CC_PROF("k_lp_init", s);
-            k_lp_init<OffT><<<gv, TPB, 0, s>>>(I, n, in.m, K, ks, q[0], &fl->nfront[0], d);
+            k_lp_init<OffT><<<gv, TPB, 0, s>>>(I, n, in.m, K, ks, q[0], &fl->nfront[0], bm[0], d);
         }
         for (;;) {
             if ((st = read_flags()) != CC_OK) return st;
@@ -508,8 +526,9 @@ cc_status run_minlabel(const MinLabelIn &in, const cc_finish_opt &fo, const Devi
             }
             const int nx = cur ^ 1;
             if ((ce = cudaMemsetAsync(&fl->nfront[nx], 0, 4, s)) != cudaSuccess) return from_cuda(ce);
-            if ((ce = cudaMemsetAsync(mark, 0, words * 4, s)) != cudaSuccess) return from_cuda(ce);
-            LPRule f{K, mark, q[nx], &fl->nfront[nx]};
+            // bm[cur] marks this frontier; bm[nx] collects the next one
+            if ((ce = cudaMemsetAsync(bm[nx], 0, words * 4, s)) != cudaSuccess) return from_cuda(ce);
+            LPRule f{K, bm[nx], q[nx], &fl->nfront[nx], bm[cur]};
             {
                 CC_PROF("k_lp_round", s);
                 k_frontier<OffT, LPRule><<<gv, TPB, 0, s>>>(I, in.A, n, in.m, q[cur], &fl->nfront[cur], f, d);
