@@ -567,28 +567,6 @@ __device__ __forceinline__ void block_compact(uint64_t total, uint32_t *count, K
 // and are run over a vertex's edges in groups of four for memory-level
 // parallelism.  Bad edge ids (>= n) are dropped and flagged here.
 
-// One thread applies f to the edges [b, e) of vertex u (e - b <= LIGHT_MAX),
-// four independent loads at a time.  (Aligned 16-byte group loads were
-// tried here and lost: a group straddles the range ends of low-degree
-// vertices, doubling the functor calls on grids and sparse graphs.)
-template <class F>
-__device__ __forceinline__ void light_edges(uint32_t u, uint64_t b, uint64_t e, const uint32_t *A, uint32_t n,
-                                            F &f, const Dev &d) {
-    for (uint64_t x = b; x < e; x += 4) {
-        uint32_t v[4];
-        bool ok[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            ok[j] = x + j < e;
-            v[j] = ok[j] ? ld_stream(A + x + j) : u;
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if (ok[j] && v[j] >= n) { atomicOr(d.err, ERR_BAD_EDGE); ok[j] = false; }
-        f.apply4(u, v, ok);
-    }
-}
-
 // Warp-cooperative light edges.  Every lane of the warp calls this (it is
 // warp-synchronous) with its own vertex u and edge range [b, b + deg),
 // deg <= LIGHT_MAX, or deg = 0 for none.  The warp walks the concatenation
@@ -604,6 +582,9 @@ __device__ __forceinline__ void light_edges(uint32_t u, uint64_t b, uint64_t e, 
 // each lane walking its own list, four edges a step, takes no more steps
 // and needs no search: the warp does that when ceil(max deg / 4) steps are
 // at most one more than the concatenated walk's ceil(total / 128).
+// (Aligned 16-byte group loads in the per-lane walk were tried and lost: a
+// group straddles the range ends of low-degree vertices, doubling the
+// functor calls on grids and sparse graphs.)
 template <class F, bool POS = false>
 __device__ __forceinline__ void warp_light_edges(uint32_t u, uint64_t b, uint32_t deg, const uint32_t *A, uint32_t n,
                                                  F &f, const Dev &d) {
