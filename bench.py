@@ -61,6 +61,8 @@ def parse():
     p.add_argument("--amsf-eps", type=float, default=0.25)
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--combos", action="store_true", help="also time every sampling x finish combination")
+    p.add_argument("--minlabel", action="store_true",
+                   help="also time the sixteen Liu-Tarjan variants, Stergiou and label propagation (none / k-out)")
     p.add_argument("--matrix", action="store_true",
                    help="time every sampling x finish combination on the 16384x16384 grid (edge drop 0.3) "
                         "and on Erdos-Renyi n=2^25, average degree 1.2")
@@ -395,6 +397,8 @@ def run_ours(args):
 
     if args.combos:
         out["combos"] = bench_combos(args, cc, off, edg, labels, lab, m)
+    if args.minlabel:
+        out["minlabel"] = bench_minlabel(cc, off, edg, labels, lab, m)
 
     if args.matrix:
         out["matrix"] = bench_matrix(args, cc, synth, dev)
@@ -434,6 +438,32 @@ def bench_combos(args, cc, off, edg, labels, ref, m):
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / reps
             res[f"{s}+{f}"] = {"ms": round(ms, 3), "gedges_s": round(m / (ms * 1e-3) / 1e9, 2), "exact": same}
+    return res
+
+
+def bench_minlabel(cc, off, edg, labels, ref, m):
+    """The min-label finishes that need not be monotone (Appendix D's sixteen
+    Liu-Tarjan variants, Stergiou et al., label propagation), without
+    sampling and after k-out: time per call, rounds, labels equal to the
+    headline path's."""
+    import torch
+    res = {}
+    kinds = sorted(cc.LT_VARIANTS) + ["stergiou", "label_prop"]
+    for s in ("none", "kout"):
+        for f in kinds:
+            so, fo = cc.sample_opt(s), cc.finish_opt(f)
+            _, st = cc.cc_static(off, edg, so, fo, labels, stats=True)
+            same = bool(torch.equal(labels, ref))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 2
+            e0.record()
+            for _ in range(reps):
+                cc.cc_static(off, edg, so, fo, labels)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            res[f"{s}+{f}"] = {"ms": round(ms, 3), "gedges_s": round(m / (ms * 1e-3) / 1e9, 2),
+                               "rounds": int(st["rounds"]), "exact": same}
     return res
 
 
