@@ -52,6 +52,9 @@ def parse():
     p.add_argument("--splice", default="split_one")
     p.add_argument("--freq-samples", type=int, default=0)
     p.add_argument("--incr-scale", type=int, default=24)
+    p.add_argument("--incr-finish", default="uf_rem_cas",
+                   help="finish of the incremental handle: a union-find kind (batches of unions) or sv / lt_prf "
+                        "(type-2 batches: rounds on the resident forest)")
     p.add_argument("--incr-batches", type=int, default=100)
     p.add_argument("--incr-qfrac", type=float, default=0.5)
     p.add_argument("--no-incr", action="store_true")
@@ -642,7 +645,7 @@ def bench_incremental(args, cc, synth, dev):
     import torch
     base = synth.rmat(args.incr_scale, 16, seed=2, device=dev)
     n = base.n
-    inc = cc.Incremental(n, base.offsets, base.edges)
+    inc = cc.Incremental(n, base.offsets, base.edges, finish=cc.finish_opt(args.incr_finish))
     del base
     torch.cuda.empty_cache()
     sizes = synth.log_uniform_sizes(args.incr_batches, 1e3, 1e7, seed=3, stream=50)
@@ -699,7 +702,7 @@ def bench_incremental(args, cc, synth, dev):
 
     def served(interval_s):
         base = synth.rmat(args.incr_scale, 16, seed=2, device=dev)
-        inc2 = cc.Incremental(n, base.offsets, base.edges)
+        inc2 = cc.Incremental(n, base.offsets, base.edges, finish=cc.finish_opt(args.incr_finish))
         del base
         torch.cuda.empty_cache()
         srv = cc.Server(inc2, slots=4, slot_pairs=1 << 22)
@@ -723,7 +726,8 @@ def bench_incremental(args, cc, synth, dev):
 
     wall_srv, lat_srv, same_last = served(0.0)
     wall_pace, lat_pace, same_pace = served(wall / len(batches))
-    return {"base": f"rmat{args.incr_scale}_ef16", "n": n, "batches": len(batches), "query_fraction": qf,
+    return {"base": f"rmat{args.incr_scale}_ef16", "n": n, "finish": args.incr_finish, "batches": len(batches),
+            "query_fraction": qf,
             "inserts": total_ins, "queries": total_q,
             "updates_per_s_device": round(total_ins / dev_s, 1), "ops_per_s_device": round((total_ins + total_q) / dev_s, 1),
             "updates_per_s_e2e": round(total_ins / wall, 1), "ops_per_s_e2e": round((total_ins + total_q) / wall, 1),
