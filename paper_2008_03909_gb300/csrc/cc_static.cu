@@ -119,6 +119,11 @@ __global__ void __launch_bounds__(256, 8) k_shortcut(uint32_t *P, uint32_t *prev
 // One vertex per thread step at full occupancy (launch bounds for eight
 // 256-thread blocks per SM), with the next vertex's offsets prefetched.
 constexpr int KOUT_MINB = 8;
+// The first-edge queue of k_kout_hook_first: one region per block (grids of
+// at most 8 blocks per SM, so KOUT_MAX_BLOCKS covers 256 SMs).  The regions
+// hold n pairs plus, per warp of the grid, one 128-vertex step of slack.
+constexpr uint32_t KOUT_MAX_BLOCKS = 2048;
+__host__ inline uint64_t kout_defer_entries(uint64_t n) { return n + 128 + (uint64_t)KOUT_MAX_BLOCKS * 8 * 128; }
 
 template <typename OffT, class E, int NB>
 __global__ void __launch_bounds__(256, KOUT_MINB)
@@ -172,11 +177,21 @@ void launch_kout(unsigned grid, cudaStream_t s, const OffT *I, const uint32_t *A
 // still a root and the link keeps P[x] <= x.  Otherwise P[v] = v, and a
 // vertex with w0 > v (all its neighbours larger) is queued for a real Union
 // in part two as the pair (v, w0), so part two reads no offsets or edges.
+// The queue is cut into one region of `cap_blk` pairs per block, counted in
+// shared memory (dcount[block] at the end): one global counter for the
+// whole grid took an atomic per warp step on a single address, which
+// serialised (about 2 ns each, 0.5M of them at RMAT-26: most of the
+// kernel's time).  A block's warp steps hold at most cap_blk vertices, so
+// its region cannot overflow (checked, flagged).
 template <typename OffT>
 __global__ void __launch_bounds__(256, 8) k_kout_hook_first(const OffT *I, const uint32_t *A, uint32_t n,
                                                             uint64_t m, uint32_t *P, uint2 *defer,
-                                                            uint32_t *ndefer, uint32_t *pick1, uint32_t k,
-                                                            uint32_t rule, uint64_t seed, Dev d) {
+                                                            uint32_t *dcount, uint32_t cap_blk, uint32_t *pick1,
+                                                            uint32_t k, uint32_t rule, uint64_t seed, Dev d) {
+    __shared__ uint32_t nblk;
+    if (threadIdx.x == 0) nblk = 0;
+    __syncthreads();
+    uint2 *my_defer = defer + (uint64_t)blockIdx.x * cap_blk;
     const int lane = threadIdx.x & 31;
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -234,25 +249,34 @@ __global__ void __launch_bounds__(256, 8) k_kout_hook_first(const OffT *I, const
                 pick1[v] = r[j] == (uint32_t)v ? NONE : r[j];
             }
         }
-        uint32_t slot = warp_append_full(ndefer, nd);
+        uint32_t slot = warp_append_full(&nblk, nd);
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-            if (w[j] != NONE && w[j] > base + 32 * j + lane)
-                defer[slot++] = make_uint2((uint32_t)(base + 32 * j + lane), w[j]);
+            if (w[j] != NONE && w[j] > base + 32 * j + lane) {
+                if (slot < cap_blk) my_defer[slot] = make_uint2((uint32_t)(base + 32 * j + lane), w[j]);
+                else atomicOr(d.err, ERR_NONCONVERGED);
+                ++slot;
+            }
     }
+    __syncthreads();
+    if (threadIdx.x == 0) dcount[blockIdx.x] = nblk < cap_blk ? nblk : cap_blk;
 }
 
-// First edges, part two: Union(v, w0) for the queued (v, w0) pairs.
+// First edges, part two: Union(v, w0) for the queued (v, w0) pairs, the
+// regions of the first pass's `regions` blocks taken block by block.
 template <class E>
 __global__ void __launch_bounds__(256, KOUT_MINB)
-k_kout_defer(uint32_t n, uint32_t *P, const uint2 *defer, const uint32_t *ndefer, Dev d) {
-    const uint32_t total = *ndefer;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint2 q = defer[i];
-        uint32_t u1[1] = {q.x}, w1[1] = {q.y};
-        bool ok[1] = {q.y < n && q.y != q.x};
-        unite_pairs<E, 1>(P, u1, w1, ok, d);
+k_kout_defer(uint32_t n, uint32_t *P, const uint2 *defer, const uint32_t *dcount, uint32_t regions, uint32_t cap_blk,
+             Dev d) {
+    for (uint32_t r = blockIdx.x; r < regions; r += gridDim.x) {
+        const uint32_t total = dcount[r];
+        const uint2 *q0 = defer + (uint64_t)r * cap_blk;
+        for (uint32_t i = threadIdx.x; i < total; i += blockDim.x) {
+            const uint2 q = q0[i];
+            uint32_t u1[1] = {q.x}, w1[1] = {q.y};
+            bool ok[1] = {q.y < n && q.y != q.x};
+            unite_pairs<E, 1>(P, u1, w1, ok, d);
+        }
     }
 }
 
@@ -1231,7 +1255,7 @@ struct Graph {
 // Scratch layout of one call.
 struct Work {
     Scratch sc;
-    size_t o_defer = 0, o_pick = 0;
+    size_t o_defer = 0, o_dcount = 0, o_pick = 0;
     size_t o_ctl = 0, o_chunks = 0, o_counts = 0, o_prev = 0, o_light = 0, o_vis = 0, o_q0 = 0, o_q1 = 0,
            o_bm0 = 0, o_bm1 = 0, o_cand = 0, o_loop = 0, o_stamp = 0, o_sf = 0, o_ff = 0, o_fcount = 0,
            o_hooks = 0;
@@ -1260,7 +1284,10 @@ void plan(Work &w, const Graph &g, int sample_kind, uint32_t freq_samples, int f
     w.chunk_cap = chunk_capacity(n, g.m);
     w.o_chunks = w.sc.reserve(w.chunk_cap * sizeof(ChunkRef));
     if (sample_kind == CC_SAMPLE_KOUT) {
-        w.o_defer = w.sc.reserve(n * 8);
+        // per-block regions of the first-edge queue: n pairs plus one warp
+        // step's slack per warp of a grid of up to KOUT_MAX_BLOCKS blocks
+        w.o_defer = w.sc.reserve(kout_defer_entries(n) * 8);
+        w.o_dcount = w.sc.reserve((size_t)KOUT_MAX_BLOCKS * 4);
         w.o_pick = w.sc.reserve(n * 4);
     }
     if (sample_kind != CC_SAMPLE_NONE && freq_samples == 0) {
@@ -1678,17 +1705,21 @@ cc_status sample_phase(const Graph &g, const cc_sample_opt &so, const cc_finish_
         using E = decltype(eng);
         const OffT *I = static_cast<const OffT *>(g.I);
         uint2 *defer = w.sc.at<uint2>(w.o_defer);
-        Ctl *ctl = w.ctl();
-        CC_TRY(cudaMemsetAsync(&ctl->ndefer, 0, 4, s));
+        uint32_t *dcount = w.sc.at<uint32_t>(w.o_dcount);
+        // a block's warps take steps warp, warp + nw, ... of 128 vertices
+        const uint64_t steps = ((uint64_t)g.n + 127) / 128, nw = (uint64_t)gv * (TPB / 32);
+        const uint64_t cap_blk = (TPB / 32) * 128 * ((steps + nw - 1) / nw);
+        if (gv > KOUT_MAX_BLOCKS || (uint64_t)gv * cap_blk > kout_defer_entries(g.n) || cap_blk > 0xFFFFFFFFull)
+            return CC_ERR_INVALID;   // not reached: grids have at most 8 blocks per SM
         uint32_t *pick1 = so.k == 2 ? w.sc.at<uint32_t>(w.o_pick) : nullptr;
         {
             CC_PROF("k_kout_hook_first", s);
-            k_kout_hook_first<OffT><<<gv, TPB, 0, s>>>(I, g.A, g.n, g.m, P, defer, &ctl->ndefer, pick1, so.k,
-                                                       so.kout_rule, so.seed, d);
+            k_kout_hook_first<OffT><<<gv, TPB, 0, s>>>(I, g.A, g.n, g.m, P, defer, dcount, (uint32_t)cap_blk, pick1,
+                                                       so.k, so.kout_rule, so.seed, d);
         }
         {
             CC_PROF("k_kout_defer", s);
-            k_kout_defer<E><<<gv, TPB, 0, s>>>(g.n, P, defer, &ctl->ndefer, d);
+            k_kout_defer<E><<<gv, TPB, 0, s>>>(g.n, P, defer, dcount, gv, (uint32_t)cap_blk, d);
         }
         if (so.k > 1) {
             {
