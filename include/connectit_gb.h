@@ -232,9 +232,11 @@ cc_status cc_finish(const void *offsets, int offsets_u64, const uint32_t *edges,
  * file-scope device array of CC_NOALLOC_MAX_LABELS uint32 (16 MiB plus one
  * word), reserved on every GPU that loads the library until the process
  * exits.  n > CC_NOALLOC_MAX_LABELS returns CC_ERR_INVALID before anything
- * is enqueued.  The first call on a device looks up the scratch's device
- * address (a one-time set-up, done with that device current); make that
- * first call before any stream capture.  Every call reuses the same
+ * is enqueued.  Every call looks up the scratch's device address in the
+ * current device's context (so a context created again after
+ * cudaDeviceReset is served at its new address); the first call on a
+ * device also loads the library's device code there, so make that first
+ * call before any stream capture.  Every call reuses the same
  * scratch and zeroes the part it needs first, so calls whose work could
  * overlap on the GPU (unordered streams) race and must not be issued.
  * Label ids >= n are skipped and flagged (CC_DEVERR_BAD_EDGE). */
@@ -440,6 +442,11 @@ uint64_t cc_launch_count(void);
 
 const char *cc_status_str(cc_status s);
 const char *cc_version(void);
+/* The compute capability of the device code the runtime loaded for this
+ * library on the current device, as major * 10 + minor (103 for the
+ * sm_103a build); no paper counterpart.  Needs a device: CC_ERR_CUDA
+ * without one. */
+cc_status cc_binary_version(int *version_out);
 
 #ifdef __cplusplus
 }

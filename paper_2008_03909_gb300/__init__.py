@@ -162,6 +162,7 @@ _SIGS = {
     "cc_launch_count": (ctypes.c_uint64, []),
     "cc_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "cc_version": (ctypes.c_char_p, []),
+    "cc_binary_version": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int)]),
 }
 
 

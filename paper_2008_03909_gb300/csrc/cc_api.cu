@@ -151,6 +151,10 @@ LaunchScope::~LaunchScope() {
 
 using namespace ccg;
 
+// The kernel whose image cc_binary_version reports (every kernel of the
+// library is built for the same single target).
+static __global__ void k_version_probe() {}
+
 extern "C" {
 
 void cc_default_opts(cc_sample_opt *sample, cc_finish_opt *finish) {
@@ -228,5 +232,17 @@ const char *cc_status_str(cc_status s) {
 }
 
 const char *cc_version(void) { return "connectit-gb300 0.1 (sm_103a)"; }
+
+cc_status cc_binary_version(int *version_out) {
+    if (!version_out) return CC_ERR_INVALID;
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, (const void *)k_version_probe);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return from_cuda(e);
+    }
+    *version_out = a.binaryVersion;
+    return CC_OK;
+}
 
 }  // extern "C"

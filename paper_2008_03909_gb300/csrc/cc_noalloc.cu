@@ -13,8 +13,6 @@
 // the last call; each call zeroes the part it uses before counting.  Calls
 // whose work overlaps on the GPU (different streams without ordering) race
 // on it and must not be issued.
-#include <mutex>
-
 #include "cc_internal.h"
 
 using namespace ccg;
@@ -27,36 +25,27 @@ static __device__ __align__(256) uint32_t g_noalloc_counts[CC_NOALLOC_MAX_LABELS
 static __device__ __align__(256) unsigned long long g_noalloc_key;
 
 struct NoAllocScratch {
-    bool ready = false;
     uint32_t *counts = nullptr;
     unsigned long long *key = nullptr;
 };
-std::mutex g_na_mu;
-NoAllocScratch g_na[64];
 
-// Device addresses of the scratch arrays for the current device, looked up
-// once per device (host code cannot use the arrays' names as addresses).
-cc_status noalloc_scratch(NoAllocScratch **out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+// Device addresses of the scratch arrays in the current device's context
+// (host code cannot use the arrays' names as addresses).  They are looked
+// up on every call rather than cached: a context that was torn down and
+// created again (cudaDeviceReset) places the arrays at new addresses, and
+// the lookup is a host-side table read that allocates nothing.  The first
+// lookup on a device loads the library's device code there, so that first
+// call belongs before any stream capture.
+cc_status noalloc_scratch(NoAllocScratch *out) {
+    void *c = nullptr, *k = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&c, g_noalloc_counts);
+    if (e == cudaSuccess) e = cudaGetSymbolAddress(&k, g_noalloc_key);
+    if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return CC_ERR_CUDA;
     }
-    std::lock_guard<std::mutex> lk(g_na_mu);
-    NoAllocScratch &s = g_na[dev];
-    if (!s.ready) {
-        void *c = nullptr, *k = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&c, g_noalloc_counts);
-        if (e == cudaSuccess) e = cudaGetSymbolAddress(&k, g_noalloc_key);
-        if (e != cudaSuccess) {
-            (void)cudaGetLastError();
-            return CC_ERR_CUDA;
-        }
-        s.counts = static_cast<uint32_t *>(c);
-        s.key = static_cast<unsigned long long *>(k);
-        s.ready = true;
-    }
-    *out = &s;
+    out->counts = static_cast<uint32_t *>(c);
+    out->key = static_cast<unsigned long long *>(k);
     return CC_OK;
 }
 
@@ -107,9 +96,10 @@ extern "C" cc_status cc_identify_frequent_noalloc(const uint32_t *labels, uint32
     if (!lmax_out || (n > 0 && !labels)) return CC_ERR_INVALID;
     if (n > CC_NOALLOC_MAX_LABELS) return CC_ERR_INVALID;
     if (!aligned(lmax_out, 4) || (labels && !aligned(labels, 4))) return CC_ERR_INVALID;
-    NoAllocScratch *sc = nullptr;
-    cc_status st = noalloc_scratch(&sc);
+    NoAllocScratch scr;
+    cc_status st = noalloc_scratch(&scr);
     if (st != CC_OK) return st;
+    const NoAllocScratch *sc = &scr;
     const DeviceInfo *di = device_info();
     if (!di) return CC_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);

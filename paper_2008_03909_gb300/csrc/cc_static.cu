@@ -2101,15 +2101,28 @@ cc_status run_static_zero_copy(const Graph &gz, const void *h_off, const uint32_
     return CC_OK;
 }
 
-// Device address of pinned host memory, or null.
-const void *host_device_view(const void *p) {
-    if (!p) return nullptr;
-    cudaPointerAttributes a;
+// Device address of `bytes` bytes of pinned host memory starting at p, or
+// null.  Both the first and the last byte must lie in memory the device
+// maps, at the same offset from the device view (one registered region), or
+// the kernels could read past the mapping; the caller then takes the copying
+// path, where a short buffer fails on the host instead.
+const void *host_device_view(const void *p, size_t bytes) {
+    if (!p || bytes == 0) return nullptr;
+    cudaPointerAttributes a, z;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         (void)cudaGetLastError();
         return nullptr;
     }
-    return (a.type == cudaMemoryTypeHost && a.devicePointer) ? a.devicePointer : nullptr;
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    const char *last = static_cast<const char *>(p) + (bytes - 1);
+    if (cudaPointerGetAttributes(&z, last) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    if (z.type != cudaMemoryTypeHost || !z.devicePointer ||
+        static_cast<const char *>(z.devicePointer) != static_cast<const char *>(a.devicePointer) + (bytes - 1))
+        return nullptr;
+    return a.devicePointer;
 }
 
 // Capped BFS (push only, at most `cap` levels) from src: levels run and
@@ -2305,7 +2318,7 @@ cc_status cc_static_host(const void *offsets, int offsets_u64, const uint32_t *e
     cc_finish_opt fo;
     resolve_opts(sample, finish, so, fo);
     if ((st = check_sample(so)) != CC_OK || (st = check_finish(fo)) != CC_OK) return st;
-    const void *voff = host_device_view(offsets), *vedg = m ? host_device_view(edges) : nullptr;
+    const void *voff = host_device_view(offsets, ob), *vedg = m ? host_device_view(edges, (size_t)m * 4) : nullptr;
     if (so.kind == CC_SAMPLE_KOUT && voff && (vedg || !m) && aligned(voff, offsets_u64 ? 8 : 4) &&
         (!m || aligned(vedg, 4))) {
         Graph gz{voff, offsets_u64 != 0, static_cast<const uint32_t *>(vedg), n, m};

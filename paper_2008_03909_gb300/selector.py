@@ -8,7 +8,8 @@ The paper chooses by a hand-made decision tree (Section 4.7):
 UF-Rem-CAS with FindNaive; no sampling when m/n < 3; BFS (or LDD) sampling
 for dense, low-diameter graphs; k-out otherwise.  `paper_decision_tree`
 restates it on this library's features (low diameter: a BFS from the
-highest-degree vertex finishes within 64 levels).
+highest-degree vertex finishes within 64 levels and reaches at least half
+of the vertices).
 """
 from __future__ import annotations
 
@@ -32,10 +33,12 @@ def class_opts(c: int):
 def paper_decision_tree(feat: torch.Tensor) -> int:
     """The paper's rule on one feature vector (host floats)."""
     f = [float(x) for x in feat]
-    avg_deg, bfs_levels = f[2], f[14]
+    avg_deg, bfs_levels, bfs_reached = f[2], f[14], f[15]
     if avg_deg < 3.0:
         return CLASSES.index(("none", "uf_rem_cas"))
-    if bfs_levels < 1.0:           # the capped BFS finished: low diameter
+    # low diameter: the capped BFS finished AND it covered most of the graph
+    # (a hub inside a small component finishes early on any graph)
+    if bfs_levels < 1.0 and bfs_reached >= 0.5:
         return CLASSES.index(("bfs", "uf_rem_cas"))
     return DEFAULT
 

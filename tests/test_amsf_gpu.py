@@ -52,6 +52,29 @@ def test_forest_weight_within_bound(mode, eps):
     assert cc.device_error() == 0
 
 
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("eps", [0.05, 0.5, 2.0])
+def test_forest_edges_per_bucket(mode, eps):
+    # Section 5.1's buckets are processed lightest first, so after bucket i
+    # the forest spans the subgraph of buckets <= i: the returned forest's
+    # edges in buckets <= i number exactly n - #components of that subgraph,
+    # and the oracle's forest has the same counts
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(__file__))
+    from test_oracle import forest_bucket_counts
+    for i, g in enumerate((synth.rmat(12, 8, seed=3), synth.grid2d(60, 50, 0.35, seed=2),
+                           synth.erdos_renyi(9001, 1.5, seed=4))):
+        off, edg = g.numpy()
+        w = synth.edge_weights(g, 200 + i)
+        F, _, _ = run(g, w, eps, mode)
+        got, rank = forest_bucket_counts(off, edg, w.numpy(), F, eps)
+        Fo, _ = oracle.amsf(off, edg, w.numpy(), eps)
+        want, _ = forest_bucket_counts(off, edg, w.numpy(), Fo, eps)
+        assert np.array_equal(got, rank), (g.name, mode)
+        assert np.array_equal(got, want), (g.name, mode)
+
+
 def test_equal_weights_and_one_bucket():
     g = synth.rmat(14, 8, seed=5)
     off, edg = g.numpy()

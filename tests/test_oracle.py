@@ -358,6 +358,37 @@ def test_ldd_closed_forms():
     assert np.all(lab == 0) and r == 29  # vertex r+1 is claimed in round r
 
 
+def load_ldd_tie():
+    """The hand-worked tie fixture: (beta, graph, expected labels, rounds)."""
+    beta, n, pairs, want, rounds = None, None, [], None, None
+    with open(os.path.join(GOLDEN, "ldd_tie.txt")) as f:
+        for ln in f:
+            ln = ln.strip()
+            if not ln or ln.startswith("#"):
+                continue
+            if ln.startswith("beta"):
+                beta = float(ln.split()[1])
+            elif ln.startswith("labels"):
+                want = np.array([int(x) for x in ln.split()[1:]], dtype=np.uint32)
+            elif ln.startswith("rounds"):
+                rounds = int(ln.split()[1])
+            elif n is None:
+                n = int(ln)
+            else:
+                a, b = ln.split()
+                pairs.append((int(a), int(b)))
+    return beta, synth.from_edge_list(n, pairs), want, rounds
+
+
+def test_ldd_tie_takes_the_smallest_centre():
+    # a vertex claimed by two clusters in one round joins the smaller centre's
+    beta, g, want, rounds = load_ldd_tie()
+    lab, r = oracle.ldd_sample(*g.numpy(), beta=beta)
+    assert np.array_equal(lab, want) and r == rounds
+    # the schedule the hand derivation used
+    assert [oracle.ldd_schedule(g.n, beta, i) for i in range(5)] == [1, 2, 4, 11, 24]
+
+
 def test_ldd_schedule_counts():
     for beta in (0.2, 0.5, 1.0):
         for r in range(30):
@@ -626,6 +657,55 @@ def test_amsf_within_its_bound(eps):
         F, W = oracle.amsf(off, edg, w, eps)
         assert oracle.check_forest(off, edg, F) == 0
         assert opt * (1 - 1e-9) <= W <= (1 + eps) * opt * (1 + 1e-9)
+
+
+def amsf_bucket(w, eps):
+    """Bucket index of each weight: floor(log(w / Wmin) / log(1 + eps)) in
+    double, the index of the interval [Wmin(1+eps)^i, Wmin(1+eps)^(i+1))
+    holding w (Section 5.1)."""
+    w = np.asarray(w, dtype=np.float64)
+    return np.maximum(0, np.floor(np.log(w / w.min()) / np.log1p(eps))).astype(np.int64)
+
+
+def forest_bucket_counts(off, edg, w, F, eps):
+    """Forest edges per bucket (cumulative), with each pair's weight looked up
+    in the graph, against the rank of the subgraph of buckets <= i."""
+    src = np.repeat(np.arange(len(off) - 1), np.diff(off))
+    b = amsf_bucket(w, eps)
+    key = {(int(a), int(c)): int(x) for a, c, x in zip(src, edg, b)}
+    fb = np.array([key[(int(a), int(c))] for a, c in F], dtype=np.int64)
+    nb = int(b.max()) + 1 if b.size else 0
+    got = np.cumsum(np.bincount(fb, minlength=nb)) if nb else np.zeros(0, np.int64)
+    rank = np.zeros(nb, dtype=np.int64)
+    n = len(off) - 1
+    for i in range(nb):
+        keep = b <= i
+        lab = scipy_labels(n, src[keep], edg[keep].astype(np.int64))
+        rank[i] = n - len(np.unique(lab))
+    return got, rank
+
+
+@pytest.mark.parametrize("eps", [0.05, 0.5, 2.0])
+def test_amsf_per_bucket_ranks(eps):
+    # after bucket i the forest spans the subgraph of buckets <= i, so the
+    # forest edges of buckets <= i number n - #components of that subgraph
+    for g in (synth.rmat(10, 8, seed=4), synth.grid2d(30, 20, 0.3, seed=2), synth.cliques([3, 7, 1, 12])):
+        off, edg = g.numpy()
+        w = synth.edge_weights(g, 5).numpy()
+        F, _ = oracle.amsf(off, edg, w, eps)
+        got, rank = forest_bucket_counts(off, edg, w, F, eps)
+        assert np.array_equal(got, rank)
+
+
+def test_amsf_per_bucket_counts_catch_a_wrong_order():
+    # visiting the heaviest bucket first (a planted mistake, applied here to
+    # the oracle's inputs by reversing the weight order) breaks the counts
+    g = synth.rmat(9, 8, seed=3)
+    off, edg = g.numpy()
+    w = synth.edge_weights(g, 6).numpy()
+    F, _ = oracle.amsf(off, edg, (1.0 / w).astype(np.float32), 0.25)
+    got, rank = forest_bucket_counts(off, edg, w, F, 0.25)
+    assert not np.array_equal(got, rank)
 
 
 def test_amsf_closed_forms():

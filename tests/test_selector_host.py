@@ -7,10 +7,11 @@ from paper_2008_03909_gb300 import MLP_OUT
 from paper_2008_03909_gb300 import selector as sel
 
 
-def _feat(avg_deg, bfs_levels):
+def _feat(avg_deg, bfs_levels, reached=1.0):
     f = torch.zeros(16)
     f[2] = avg_deg
     f[14] = bfs_levels
+    f[15] = reached
     return f
 
 
@@ -27,6 +28,9 @@ def test_paper_decision_tree_branches():
     assert sel.CLASSES[sel.paper_decision_tree(_feat(16.0, 0.0))] == ("bfs", "uf_rem_cas")
     assert sel.CLASSES[sel.paper_decision_tree(_feat(16.0, 1.0))] == ("kout", "uf_rem_cas")
     assert sel.CLASSES[sel.paper_decision_tree(_feat(3.0, 5.0))] == ("kout", "uf_rem_cas")
+    # the BFS finished early but inside a small component: not low diameter
+    assert sel.CLASSES[sel.paper_decision_tree(_feat(16.0, 0.2, 0.01))] == ("kout", "uf_rem_cas")
+    assert sel.CLASSES[sel.paper_decision_tree(_feat(16.0, 0.2, 0.5))] == ("bfs", "uf_rem_cas")
 
 
 def test_regret_definition():

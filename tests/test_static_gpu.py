@@ -177,6 +177,22 @@ def test_ldd_sampled_labels_bit_exact(beta):
         assert np.array_equal(lab.cpu().numpy().view(np.uint32), want)
 
 
+def test_ldd_tie_golden():
+    # the hand-worked graph where vertex 19 is claimed by two clusters in the
+    # same round: the smaller centre must win on every run (the kernel's
+    # claims race, the rule does not)
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(__file__))
+    from test_oracle import load_ldd_tie
+    beta, g, want, rounds = load_ldd_tie()
+    off, edg = on_gpu(g)
+    for _ in range(20):
+        lab, r = cc.cc_sample(off, edg, cc.sample_opt("ldd", ldd_beta=beta))
+        assert r == rounds
+        assert np.array_equal(lab.cpu().numpy().view(np.uint32), want)
+
+
 @pytest.mark.parametrize("samples", [0, 1, 100, 4096])
 def test_identify_frequent_bit_exact(samples):
     rng = np.random.default_rng(3)

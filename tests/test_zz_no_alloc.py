@@ -55,6 +55,30 @@ def test_noalloc_matches_allocating_entry_point_twice():
     assert cc.device_error() == 0
 
 
+def test_noalloc_edges_of_the_range():
+    out = torch.empty(1, dtype=torch.int32, device="cuda")
+    # n == 0: nothing to count, the documented "none" result
+    empty = torch.empty(0, dtype=torch.int32, device="cuda")
+    L = cc.lib()
+    st = L.cc_identify_frequent_noalloc(None, 0, ctypes.c_void_p(out.data_ptr()),
+                                        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 0
+    torch.cuda.synchronize()
+    assert int(out.item()) & 0xFFFFFFFF == 0xFFFFFFFF
+    del empty
+    # n == the maximum: the whole scratch array in use, twice in a row with
+    # different frequent labels at opposite ends of the id range
+    n = cc.NOALLOC_MAX_LABELS
+    rng = np.random.default_rng(5)
+    for hot in (n - 1, 0):
+        arr = rng.integers(0, n, size=n).astype(np.uint32)
+        arr[: 1000] = hot
+        t = torch.from_numpy(arr.view(np.int32)).cuda()
+        got = _noalloc(t, out)
+        assert got == _alloc(t) == int(np.argmax(np.bincount(arr, minlength=n))) == hot
+    assert cc.device_error() == 0
+
+
 def test_noalloc_rejects_sizes_over_the_limit():
     L = cc.lib()
     # n above the maximum is refused before any device work (no pointer is read)
