@@ -55,27 +55,26 @@ def parse():
     p.add_argument("--incr-finish", default="uf_rem_cas",
                    help="finish of the incremental handle: a union-find kind (batches of unions) or sv / lt_prf "
                         "(type-2 batches: rounds on the resident forest)")
-    p.add_argument("--incr-batches", type=int, default=100)
-    p.add_argument("--incr-qfrac", type=float, default=0.5)
-    p.add_argument("--no-incr", action="store_true")
+    p.add_argument("--incr-batches", type=int, default=1000)
+    p.add_argument("--incr-qfrac", default="0.1,0.5,0.9",
+                   help="comma-separated query fractions of the served workload (one run each)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-forest", action="store_true")
     p.add_argument("--no-amsf", action="store_true")
     p.add_argument("--amsf-eps", type=float, default=0.25)
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--combos", action="store_true", help="also time every sampling x finish combination")
+    p.add_argument("--configs", default="1,2a,2b,2c,3,4,5",
+                   help="which workloads to measure besides the headline: 1 (R-MAT 16, u32 offsets, no sampling "
+                        "+ UF-Rem-CAS), 2a (every sampling x finish combination on the headline graph), 2b (16384^2 "
+                        "grid, edge drop 0.3), 2c (Erdos-Renyi 2^25, degree 1.2), 3 (10,000 packed graphs), 4 (the "
+                        "learned selector), 5 (the served incremental workload); 'none' for the headline only")
     p.add_argument("--minlabel", action="store_true",
                    help="also time the sixteen Liu-Tarjan variants, Stergiou and label propagation (none / k-out)")
-    p.add_argument("--matrix", action="store_true",
-                   help="time every sampling x finish combination on the 16384x16384 grid (edge drop 0.3) "
-                        "and on Erdos-Renyi n=2^25, average degree 1.2")
     p.add_argument("--batched-graphs", type=int, default=10000)
-    p.add_argument("--sel-train", type=int, default=300)
-    p.add_argument("--sel-test", type=int, default=100)
-    p.add_argument("--sel-scale-lo", type=int, default=12)
-    p.add_argument("--sel-scale-hi", type=int, default=18)
-    p.add_argument("--no-selector", action="store_true")
-    p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--sel-train", type=int, default=2000)
+    p.add_argument("--sel-test", type=int, default=200)
+    p.add_argument("--sel-scale-lo", type=int, default=14)
+    p.add_argument("--sel-scale-hi", type=int, default=22)
     p.add_argument("--cpu-seconds", type=float, default=20.0)
     return p.parse_args()
 
@@ -394,33 +393,85 @@ def run_ours(args):
                               if args.sample == "kout" else "the CSR is copied to the device each call")}
         del h_off, h_edg, h_lab
 
-    # incremental: resident union-find, batches of inserts + queries
-    if not args.no_incr:
-        out["incremental"] = bench_incremental(args, cc, synth, dev)
-
-    if args.combos:
-        out["combos"] = bench_combos(args, cc, off, edg, labels, lab, m)
-    if args.minlabel:
-        out["minlabel"] = bench_minlabel(cc, off, edg, labels, lab, m)
-
-    if args.matrix:
-        out["matrix"] = bench_matrix(args, cc, synth, dev)
-
-    if not args.no_amsf:
-        out["amsf"] = bench_amsf(args, cc, synth, g, dev, ncomp)
-
-    if not args.no_batched:
-        out["batched"] = bench_batched(args, cc, synth, dev)
-
-    if not args.no_selector:
-        out["selector"] = bench_selector(args, cc, synth, dev)
-
+    # the oracle on the host cores, on the headline graph (rank 0, one GPU)
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(off, edg, args.cpu_seconds)
+
+    # the other workloads, one GPU each: measured by a single-rank run only
+    # (under torchrun every rank holds its GPU for the headline alone)
+    want = set() if args.configs.strip() in ("", "none") or world > 1 else \
+        {c.strip() for c in args.configs.split(",")}
+    configs = {}
+    if "1" in want:
+        configs["1_rmat16_ef8_u32_none_uf_rem_cas"] = bench_config1(cc, synth, dev)
+    if "2a" in want:
+        configs["2a_rmat26_ef16_combinations"] = bench_combos(args, cc, off, edg, labels, lab, m)
+    if args.minlabel:
+        out["minlabel"] = bench_minlabel(cc, off, edg, labels, lab, m)
+    if not args.no_amsf and world == 1:
+        out["amsf"] = bench_amsf(args, cc, synth, g, dev, ncomp)
+    if "2b" in want or "2c" in want:
+        # free the headline graph first: the grid's CSR takes about 6 GB
+        del g, off, edg, labels, lab
+        torch.cuda.empty_cache()
+        configs.update(bench_matrix(args, cc, synth, dev, grid="2b" in want, er="2c" in want))
+    if "3" in want:
+        configs["3_batched_10000_graphs"] = bench_batched(args, cc, synth, dev)
+    if "4" in want:
+        configs["4_selector"] = bench_selector(args, cc, synth, dev)
+    if "5" in want:
+        configs["5_incremental_rmat24"] = {f"q{q}": bench_incremental(args, cc, synth, dev, float(q))
+                                           for q in args.incr_qfrac.split(",")}
+    out["configs"] = configs
     if dist:
         dist.barrier()
         dist.destroy_process_group()
     return out if rank == 0 else None
+
+
+def bench_config1(cc, synth, dev, reps=50):
+    """The small workload: R-MAT scale 16, edge factor 8, uint32 offsets, no
+    sampling + UF-Rem-CAS.  Its CSR (4.7 MB) fits in L2, so L2 is flushed
+    (a 256 MB write) before every timed call; each call is timed alone with
+    CUDA events and the median is reported.  Launch- and latency-bound: the
+    line also carries the launches per call."""
+    import torch
+    g = synth.rmat(16, 8, seed=1, device=dev)
+    off, edg, n, m = g.offsets.to(torch.int32), g.edges, g.n, g.m
+    so, fo = cc.sample_opt("none"), cc.finish_opt("uf_rem_cas")
+    labels = torch.empty(n, dtype=torch.int32, device=dev)
+    cc.cc_static(off, edg, so, fo, labels)
+    ok, ncomp = check_labels(off, edg, labels)
+    flush = torch.empty(64 << 20, dtype=torch.int32, device=dev)
+    times = []
+    l0 = cc.launch_count()
+    for _ in range(reps):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        cc.cc_static(off, edg, so, fo, labels)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    launches = (cc.launch_count() - l0) / reps
+    # warm (L2-resident) back-to-back calls, for comparison
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        cc.cc_static(off, edg, so, fo, labels)
+    e1.record()
+    torch.cuda.synchronize()
+    warm = e0.elapsed_time(e1) / reps
+    ms = statistics.median(times)
+    peak, _ = peaks()
+    b_csr = 4 * (n + 1) + 4 * m
+    del flush
+    return {"n": n, "m": m, "offsets": "u32", "sample": "none", "finish": "uf_rem_cas+naive+split_one",
+            "ms": round(ms, 4), "gedges_s": round(m / (ms * 1e-3) / 1e9, 3),
+            "ms_warm_back_to_back": round(warm, 4), "launches_per_call": launches,
+            "b_csr_bytes": b_csr, "hbm_roof_frac": round(b_csr / (peak * 1e9) / (ms * 1e-3), 4),
+            "bound": "launch and latency: the CSR is 4.7 MB, the parents 0.26 MB",
+            "l2": "flushed before each timed call (256 MB write)", "components": ncomp, "invariants_ok": ok}
 
 
 def bench_combos(args, cc, off, edg, labels, ref, m):
@@ -508,15 +559,19 @@ def check_labels(off, edg, lab):
     return ok, int((lab == ar).sum().item())
 
 
-def bench_matrix(args, cc, synth, dev):
+def bench_matrix(args, cc, synth, dev, grid=True, er=True):
     """Every sampling x finish combination on the high-diameter grid and on
     the near-percolation Erdos-Renyi graph: ms per call (one untimed call,
     then the mean of `reps`), Gedges/s, and whether the labels equal the
     no-sampling union-find labels (which are checked by the invariants)."""
     import torch
     res = {}
-    for name, make in (("grid16384x16384_p0.3", lambda: synth.grid2d(16384, 16384, 0.3, seed=1, device=dev)),
-                       ("er_n2^25_d1.2", lambda: synth.erdos_renyi(1 << 25, 1.2, seed=1, device=dev))):
+    todo = []
+    if grid:
+        todo.append(("2b_grid16384x16384_p0.3", lambda: synth.grid2d(16384, 16384, 0.3, seed=1, device=dev)))
+    if er:
+        todo.append(("2c_er_n2^25_d1.2", lambda: synth.erdos_renyi(1 << 25, 1.2, seed=1, device=dev)))
+    for name, make in todo:
         t0 = time.time()
         g = make()
         gen_s = time.time() - t0
@@ -602,24 +657,43 @@ def bench_selector(args, cc, synth, dev):
 
 
 def bench_batched(args, cc, synth, dev):
-    """Many small graphs: one autotuned persistent launch vs one cc_static
-    call per graph (no sampling, union-find finish), same labels."""
+    """The batched workload (10,000 graphs, uint32 packed CSR): one
+    autotuned persistent launch vs one cc_static call per graph (no
+    sampling, union-find finish), same labels.  The batch's CSR (about 1.8
+    GB) exceeds L2.  The launch's roofline counts its compulsory bytes: the
+    offsets 4(V+1), the edges 4M and the labels written 4V (parents live in
+    shared memory), over the kernel's own time."""
     import torch
     t0 = time.time()
     gs = synth.batch_config3(args.batched_graphs, seed=1)
     gv, off, edg = synth.pack(gs)
     gen_s = time.time() - t0
-    gv, off, edg = gv.to(dev), off.to(dev), edg.to(dev)
     V, M = off.numel() - 1, edg.numel()
+    if M < 2**32:
+        off = off.to(torch.int32)
+    gv, off, edg = gv.to(dev), off.to(dev), edg.to(dev)
+    ob = 4 if off.dtype == torch.int32 else 8
     lab, best, tune_ms = cc.cc_batched_autotune(gv, off, edg)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     reps = 10
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(reps):
         cc.cc_batched(gv, off, edg, best, lab)
     e1.record()
     torch.cuda.synchronize()
     ms_batched = e0.elapsed_time(e1) / reps
+    # the kernel alone, from the library's per-launch events
+    cc.profile_enable(True)
+    for _ in range(reps):
+        cc.cc_batched(gv, off, edg, best, lab)
+    torch.cuda.synchronize()
+    prof = cc.profile_read()
+    cc.profile_enable(False)
+    kl, kms = prof.get("k_batched", (reps, ms_batched * reps))
+    k_ms = kms / max(kl, 1)
+    peak, peak_kind = peaks()
+    ab = ob * (V + 1) + 4 * M + 4 * V
+    ach = ab / (k_ms * 1e-3) / 1e9
     # one plain launch per graph, on the same packed arrays
     ref = torch.empty_like(lab)
     gvh = gv.cpu().tolist()
@@ -633,15 +707,27 @@ def bench_batched(args, cc, synth, dev):
     e1.record()
     torch.cuda.synchronize()
     ms_plain = e0.elapsed_time(e1)
-    return {"graphs": len(gs), "vertices": V, "edges": M, "gen_s": round(gen_s, 1),
+    return {"graphs": len(gs), "vertices": V, "edges": M, "offsets": "u32" if ob == 4 else "u64",
+            "gen_s": round(gen_s, 1),
             "schedule": {"threads": best.threads, "smem_max_vertices": best.smem_max_vertices,
                          "vertex_mode": best.vertex_mode},
             "ms_batched": round(ms_batched, 4), "edges_per_s_batched": round(M / (ms_batched * 1e-3), 1),
+            "roofline": {"kernel": "k_batched", "bound": "hbm", "algorithmic_bytes": ab, "ms_avg": round(k_ms, 5),
+                         "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
+                         "peak_kind": peak_kind},
             "ms_per_graph_launches": round(ms_plain, 3), "edges_per_s_per_graph_launches": round(M / (ms_plain * 1e-3), 1),
             "speedup": round(ms_plain / ms_batched, 2), "labels_equal": bool(torch.equal(lab, ref))}
 
 
-def bench_incremental(args, cc, synth, dev):
+def bench_incremental(args, cc, synth, dev, qf):
+    """The served workload at query fraction qf: an R-MAT scale-24 edge
+    factor 16 base in a resident union-find, then the batches (log-uniform
+    in [1e3, 1e7] operations, inserts R-MAT distributed, queries uniform)
+    staged in pinned host memory.  Times the plain loop (one insert and one
+    query launch per batch, host -> device -> answers -> host, synchronous)
+    and the continuous-batching request loop, back to back and paced at the
+    plain loop's batch rate; every batch's answers of the request loop are
+    compared with the plain loop's."""
     import torch
     base = synth.rmat(args.incr_scale, 16, seed=2, device=dev)
     n = base.n
@@ -649,7 +735,6 @@ def bench_incremental(args, cc, synth, dev):
     del base
     torch.cuda.empty_cache()
     sizes = synth.log_uniform_sizes(args.incr_batches, 1e3, 1e7, seed=3, stream=50)
-    qf = args.incr_qfrac
     # stage every batch in pinned host memory (inserts R-MAT distributed,
     # queries uniform), then time host -> device -> answers -> host
     batches = []

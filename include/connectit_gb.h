@@ -279,11 +279,15 @@ cc_status cc_random_sectors(const uint32_t *x, uint64_t words, uint64_t count, u
  *   [0, n_g).  M = total directed edges.  Every graph must be symmetric.
  * labels_out (DEVICE uint32[V]): local vertex i of graph g gets the smallest
  *   local id of its component.
- * opt: schedule; NULL = cc_batch_default_opt.  threads per CTA in
- *   {128, 256, 512, 1024}; graphs of at most smem_max_vertices vertices
- *   (<= 51200) keep their parent array in shared memory, larger ones in
- *   their slice of labels_out; vertex_mode 0 = one thread per vertex,
- *   1 = one warp per vertex.  Any schedule gives the same labels.
+ * opt: schedule; NULL = cc_batch_default_opt (1024 threads, 65536,
+ *   mode 2).  threads per CTA in {128, 256, 512, 1024}; graphs of at most
+ *   smem_max_vertices vertices (<= 65536) keep their parent array in shared
+ *   memory as 16-bit local ids (2 bytes per vertex of the threshold per
+ *   CTA), larger ones in their slice of labels_out; vertex_mode 0 = one
+ *   thread per vertex, 1 = one warp per vertex, 2 = 32 vertices per warp,
+ *   the warp walking their concatenated edge lists.  Graphs are taken
+ *   largest first.  Any schedule gives the same labels.  Scratch: 4 G + 4
+ *   bytes (stream-ordered).
  * cc_batched_autotune times every candidate schedule on this batch (it
  *   synchronises), writes the fastest to *best_out (host) and its time in
  *   ms to *best_ms_out (host, may be NULL), and leaves labels_out computed. */

@@ -405,7 +405,7 @@ def profile_read() -> dict:
     return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].ms)) for i in range(cnt)}
 
 
-def batch_opt(threads=256, smem_max_vertices=12288, vertex_mode=0) -> BatchOpt:
+def batch_opt(threads=1024, smem_max_vertices=65536, vertex_mode=2) -> BatchOpt:
     return BatchOpt(threads, smem_max_vertices, vertex_mode, 0)
 
 

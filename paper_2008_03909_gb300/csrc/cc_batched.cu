@@ -4,12 +4,18 @@
 // the final shortcut).  There is no counterpart in the paper, which labels
 // one graph per call.
 //
-// Each CTA takes whole graphs from a global queue.  A graph of at most
-// `smem_max_vertices` vertices keeps its parent array in shared memory
-// (block-local atomics, one global write per vertex at the end); a larger
-// one uses its own slice of the output as the parent array.  Vertices are
-// mapped one per thread or one per warp.  cc_batched_autotune times the
-// candidate schedules on the caller's batch and returns the fastest.
+// A pre-pass orders the graphs largest first (four size classes per
+// octave), so the biggest graphs start at once instead of setting the tail.
+// Each CTA then takes whole graphs from a global queue in that order.  A
+// graph of at most `smem_max_vertices` (<= 65536) vertices keeps its parent
+// array in shared memory as 16-bit local ids (block-local atomics, one
+// coalesced global write per vertex at the end); a larger one uses its own
+// slice of the output as a 32-bit parent array in global memory (L2).
+// Vertices are mapped one per thread (mode 0), one per warp (mode 1), or 32
+// per warp with the warp walking the concatenation of their edge lists, 128
+// consecutive edge words per step (mode 2, the static path's light-vertex
+// walk).  cc_batched_autotune times the candidate schedules on the caller's
+// batch and returns the fastest.
 #include <vector>
 
 #include "cc_internal.h"
@@ -18,10 +24,19 @@ using namespace ccg;
 
 namespace {
 
-// Rem-CAS union on a parent array in shared or global memory, read through
+__device__ __forceinline__ uint32_t cas_par(uint32_t *p, uint32_t cmp, uint32_t val) {
+    return atomicCAS(p, cmp, val);
+}
+__device__ __forceinline__ uint32_t cas_par(uint16_t *p, uint32_t cmp, uint32_t val) {
+    return atomicCAS(reinterpret_cast<unsigned short *>(p), (unsigned short)cmp, (unsigned short)val);
+}
+
+// Rem-CAS union (Algorithm 14 with SplitAtomicOne) on a parent array of
+// 16-bit ids in shared memory or 32-bit ids in global memory, read through
 // volatile loads (coherent for the block in shared memory, L2 in global).
-__device__ __forceinline__ void unite_any(uint32_t *P, uint32_t u, uint32_t v, const Dev &d) {
-    volatile uint32_t *VP = P;
+template <typename T>
+__device__ __forceinline__ void unite_any(T *P, uint32_t u, uint32_t v, const Dev &d) {
+    volatile T *VP = P;
     uint32_t ru = u, rv = v, pru = VP[ru], prv = VP[rv];
     Guard g;
     while (pru != prv) {
@@ -30,12 +45,12 @@ __device__ __forceinline__ void unite_any(uint32_t *P, uint32_t u, uint32_t v, c
             t = pru; pru = prv; prv = t;
         }
         if (ru == pru) {
-            uint32_t old = atomicCAS(P + ru, ru, prv);
+            uint32_t old = cas_par(P + ru, ru, prv);
             if (old == ru) return;
             pru = old;
         } else {
             uint32_t w = VP[pru];
-            if (pru != w) atomicCAS(P + ru, pru, w);
+            if (pru != w) cas_par(P + ru, pru, w);
             ru = pru;
             pru = w;
         }
@@ -43,8 +58,9 @@ __device__ __forceinline__ void unite_any(uint32_t *P, uint32_t u, uint32_t v, c
     }
 }
 
-__device__ __forceinline__ uint32_t root_any(const uint32_t *P, uint32_t x, const Dev &d) {
-    const volatile uint32_t *VP = P;
+template <typename T>
+__device__ __forceinline__ uint32_t root_any(const T *P, uint32_t x, const Dev &d) {
+    const volatile T *VP = P;
     uint32_t p = VP[x];
     Guard g;
     while (p != x) {
@@ -55,15 +71,107 @@ __device__ __forceinline__ uint32_t root_any(const uint32_t *P, uint32_t x, cons
     return x;
 }
 
-// MODE 0: one thread per vertex; MODE 1: one warp per vertex.
-template <typename OffT, int MODE>
-__global__ void k_batched(const uint64_t *gv, uint32_t G, uint64_t V, const OffT *I, const uint32_t *A, uint64_t M,
-                          uint32_t *labels, uint32_t *queue, uint32_t smem_max, Dev d) {
-    extern __shared__ uint32_t Ps[];
-    __shared__ uint32_t g_cur;
+// Edge functor of the warp walk: each undirected edge once, from its larger
+// endpoint.
+template <typename T>
+struct BatchUnite {
+    T *P;
+    Dev d;
+    __device__ __forceinline__ void apply4(uint32_t u, const uint32_t (&v)[4], const bool (&ok)[4]) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (ok[j] && v[j] < u) unite_any(P, u, v[j], d);
+    }
+    __device__ __forceinline__ void apply4u(const uint32_t (&u)[4], const uint32_t (&v)[4], const bool (&ok)[4]) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (ok[j] && v[j] < u[j]) unite_any(P, u[j], v[j], d);
+    }
+};
+
+// Union-find over graph [vb, vb + ng) with parent array P (local ids).
+template <typename OffT, int MODE, typename T>
+__device__ __forceinline__ void batch_unions(const OffT *I, const uint32_t *A, uint64_t M, uint64_t vb, uint32_t ng,
+                                             T *P, const Dev &d) {
     const int lane = threadIdx.x & 31;
+    const uint32_t wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    if (MODE == 0) {
+        for (uint32_t i = threadIdx.x; i < ng; i += blockDim.x) {
+            uint64_t b, e;
+            clamp_range((uint64_t)ld_off(I + vb + i), (uint64_t)ld_off(I + vb + i + 1), M, b, e, d);
+            for (uint64_t x = b; x < e; ++x) {
+                const uint32_t v = ld_stream(A + x);
+                if (v >= ng) { atomicOr(d.err, ERR_BAD_EDGE); continue; }
+                if (v < i) unite_any(P, i, v, d);
+            }
+        }
+    } else if (MODE == 1) {
+        for (uint32_t i = wid; i < ng; i += nwarp) {
+            uint64_t b, e;
+            clamp_range((uint64_t)ld_off(I + vb + i), (uint64_t)ld_off(I + vb + i + 1), M, b, e, d);
+            for (uint64_t x = b + lane; x < e; x += 32) {
+                const uint32_t v = ld_stream(A + x);
+                if (v >= ng) { atomicOr(d.err, ERR_BAD_EDGE); continue; }
+                if (v < i) unite_any(P, i, v, d);
+            }
+        }
+    } else {
+        BatchUnite<T> f{P, d};
+        // every lane of the warp takes part in each step (shuffles)
+        for (uint32_t base = wid * 32; base < ng; base += nwarp * 32) {
+            const uint32_t i = base + lane;
+            uint64_t b = 0, e = 0;
+            if (i < ng) clamp_range((uint64_t)ld_off(I + vb + i), (uint64_t)ld_off(I + vb + i + 1), M, b, e, d);
+            const uint64_t dg = e - b;
+            warp_light_edges(i < ng ? i : 0, b, dg > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)dg, A, ng, f, d);
+        }
+    }
+}
+
+// Graph order for the queue: largest vertex count first, by size class
+// (four classes per octave; class 0 holds empty and malformed ranges).
+// One block; the order inside a class is arbitrary (results do not depend
+// on it).
+constexpr int NCLS = 4 * 33 + 1;
+
+__device__ __forceinline__ int size_class(uint64_t vb, uint64_t ve, uint64_t V) {
+    if (ve <= vb || ve > V || ve - vb > 0xFFFFFFFEull) return 0;
+    const uint32_t n = (uint32_t)(ve - vb);
+    const int l = 31 - __clz(n);
+    const int frac = l >= 2 ? (int)((n >> (l - 2)) & 3u) : 0;
+    return 1 + 4 * l + frac;
+}
+
+__global__ void __launch_bounds__(1024) k_batch_order(const uint64_t *gv, uint32_t G, uint64_t V, uint32_t *order) {
+    __shared__ uint32_t cnt[NCLS];
+    for (int c = threadIdx.x; c < NCLS; c += blockDim.x) cnt[c] = 0;
+    __syncthreads();
+    for (uint32_t g = threadIdx.x; g < G; g += blockDim.x) atomicAdd(&cnt[size_class(gv[g], gv[g + 1], V)], 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int c = NCLS - 1; c >= 0; --c) {   // descending classes
+            const uint32_t x = cnt[c];
+            cnt[c] = run;
+            run += x;
+        }
+    }
+    __syncthreads();
+    for (uint32_t g = threadIdx.x; g < G; g += blockDim.x)
+        order[atomicAdd(&cnt[size_class(gv[g], gv[g + 1], V)], 1u)] = g;
+}
+
+template <typename OffT, int MODE>
+__global__ void __launch_bounds__(1024) k_batched(const uint64_t *gv, const uint32_t *order, uint32_t G, uint64_t V,
+                                                  const OffT *I, const uint32_t *A, uint64_t M, uint32_t *labels,
+                                                  uint32_t *queue, uint32_t smem_max, Dev d) {
+    extern __shared__ uint16_t Ps[];
+    __shared__ uint32_t g_cur;
     for (;;) {
-        if (threadIdx.x == 0) g_cur = atomicAdd(queue, 1u);
+        if (threadIdx.x == 0) {
+            const uint32_t q = atomicAdd(queue, 1u);
+            g_cur = q < G ? order[q] : G;
+        }
         __syncthreads();
         const uint32_t g = g_cur;
         __syncthreads();
@@ -74,40 +182,21 @@ __global__ void k_batched(const uint64_t *gv, uint32_t G, uint64_t V, const OffT
             continue;
         }
         const uint32_t ng = (uint32_t)(ve - vb);
-        const bool local = ng <= smem_max;
-        uint32_t *P = local ? Ps : labels + vb;
         Dev dg = d;
         if (dg.cap == 0) dg.cap = 2ull * ng + 1024;
-        for (uint32_t i = threadIdx.x; i < ng; i += blockDim.x) P[i] = i;
-        __syncthreads();
-        // apply each undirected edge once, from its larger endpoint
-        if (MODE == 0) {
-            for (uint32_t i = threadIdx.x; i < ng; i += blockDim.x) {
-                uint64_t b, e;
-                clamp_range((uint64_t)ld_off(I + vb + i), (uint64_t)ld_off(I + vb + i + 1), M, b, e, d);
-                for (uint64_t x = b; x < e; ++x) {
-                    const uint32_t v = ld_stream(A + x);
-                    if (v >= ng) { atomicOr(d.err, ERR_BAD_EDGE); continue; }
-                    if (v < i) unite_any(P, i, v, dg);
-                }
-            }
+        if (ng <= smem_max) {
+            for (uint32_t i = threadIdx.x; i < ng; i += blockDim.x) Ps[i] = (uint16_t)i;
+            __syncthreads();
+            batch_unions<OffT, MODE, uint16_t>(I, A, M, vb, ng, Ps, dg);
+            __syncthreads();
+            // final shortcut: the root of each tree is its smallest vertex
+            for (uint32_t i = threadIdx.x; i < ng; i += blockDim.x) labels[vb + i] = root_any(Ps, i, dg);
         } else {
-            const uint32_t wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-            for (uint32_t i = wid; i < ng; i += nwarp) {
-                uint64_t b, e;
-                clamp_range((uint64_t)ld_off(I + vb + i), (uint64_t)ld_off(I + vb + i + 1), M, b, e, d);
-                for (uint64_t x = b + lane; x < e; x += 32) {
-                    const uint32_t v = ld_stream(A + x);
-                    if (v >= ng) { atomicOr(d.err, ERR_BAD_EDGE); continue; }
-                    if (v < i) unite_any(P, i, v, dg);
-                }
-            }
-        }
-        __syncthreads();
-        // final shortcut: the root of each tree is its smallest vertex
-        if (local) {
-            for (uint32_t i = threadIdx.x; i < ng; i += blockDim.x) labels[vb + i] = root_any(P, i, dg);
-        } else {
+            uint32_t *P = labels + vb;
+            for (uint32_t i = threadIdx.x; i < ng; i += blockDim.x) P[i] = i;
+            __syncthreads();
+            batch_unions<OffT, MODE, uint32_t>(I, A, M, vb, ng, P, dg);
+            __syncthreads();
             for (uint32_t i = threadIdx.x; i < ng; i += blockDim.x) P[i] = root_any(P, i, dg);
         }
         __syncthreads();
@@ -116,18 +205,25 @@ __global__ void k_batched(const uint64_t *gv, uint32_t G, uint64_t V, const OffT
 
 cc_status check_batch_opt(const cc_batch_opt &o) {
     if (o.threads != 128 && o.threads != 256 && o.threads != 512 && o.threads != 1024) return CC_ERR_INVALID;
-    if (o.smem_max_vertices > (200u * 1024u) / 4u) return CC_ERR_INVALID;
-    if (o.vertex_mode > 1 || o.reserved != 0) return CC_ERR_INVALID;
+    if (o.smem_max_vertices > 65536u) return CC_ERR_INVALID;
+    if (o.vertex_mode > 2 || o.reserved != 0) return CC_ERR_INVALID;
     return CC_OK;
 }
 
 template <typename OffT>
+const void *batched_fn(uint32_t mode) {
+    return mode == 2 ? (const void *)k_batched<OffT, 2>
+                     : mode == 1 ? (const void *)k_batched<OffT, 1> : (const void *)k_batched<OffT, 0>;
+}
+
+template <typename OffT>
 cc_status launch_batched(const uint64_t *gv, uint32_t G, uint64_t V, const void *offsets, const uint32_t *edges,
-                         uint64_t M, const cc_batch_opt &o, uint32_t *labels, uint32_t *queue, cudaStream_t s) {
+                         uint64_t M, const cc_batch_opt &o, uint32_t *labels, uint32_t *queue, uint32_t *order,
+                         cudaStream_t s) {
     const DeviceInfo *di = device_info();
     if (!di) return CC_ERR_CUDA;
-    const size_t smem = (size_t)o.smem_max_vertices * 4;
-    const void *fn = o.vertex_mode ? (const void *)k_batched<OffT, 1> : (const void *)k_batched<OffT, 0>;
+    const size_t smem = (size_t)o.smem_max_vertices * sizeof(uint16_t);
+    const void *fn = batched_fn<OffT>(o.vertex_mode);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return from_cuda(e);
@@ -144,13 +240,23 @@ cc_status launch_batched(const uint64_t *gv, uint32_t G, uint64_t V, const void 
     const Dev d = Dev{di->err, lc == 1024 ? 0 : lc};
     e = cudaMemsetAsync(queue, 0, 4, s);
     if (e != cudaSuccess) return from_cuda(e);
+    {
+        CC_PROF("k_batch_order", s);
+        k_batch_order<<<1, 1024, 0, s>>>(gv, G, V, order);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return from_cuda(e);
+    const OffT *I = static_cast<const OffT *>(offsets);
     CC_PROF("k_batched", s);
-    if (o.vertex_mode)
-        k_batched<OffT, 1><<<(unsigned)grid, o.threads, smem, s>>>(gv, G, V, static_cast<const OffT *>(offsets),
-                                                                    edges, M, labels, queue, o.smem_max_vertices, d);
+    if (o.vertex_mode == 2)
+        k_batched<OffT, 2><<<(unsigned)grid, o.threads, smem, s>>>(gv, order, G, V, I, edges, M, labels, queue,
+                                                                    o.smem_max_vertices, d);
+    else if (o.vertex_mode == 1)
+        k_batched<OffT, 1><<<(unsigned)grid, o.threads, smem, s>>>(gv, order, G, V, I, edges, M, labels, queue,
+                                                                    o.smem_max_vertices, d);
     else
-        k_batched<OffT, 0><<<(unsigned)grid, o.threads, smem, s>>>(gv, G, V, static_cast<const OffT *>(offsets),
-                                                                    edges, M, labels, queue, o.smem_max_vertices, d);
+        k_batched<OffT, 0><<<(unsigned)grid, o.threads, smem, s>>>(gv, order, G, V, I, edges, M, labels, queue,
+                                                                    o.smem_max_vertices, d);
     return from_cuda(cudaGetLastError());
 }
 
@@ -171,9 +277,9 @@ extern "C" {
 
 void cc_batch_default_opt(cc_batch_opt *o) {
     if (!o) return;
-    o->threads = 256;
-    o->smem_max_vertices = 12288;
-    o->vertex_mode = 0;
+    o->threads = 1024;
+    o->smem_max_vertices = 65536;
+    o->vertex_mode = 2;
     o->reserved = 0;
 }
 
@@ -187,10 +293,12 @@ cc_status cc_batched(const uint64_t *gv, uint32_t G, const void *offsets, int of
     if ((st = check_batch_opt(o)) != CC_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Scratch sc;
-    const size_t oq = sc.reserve(4);
+    const size_t oq = sc.reserve(4), oo = sc.reserve((size_t)G * 4);
     if ((st = sc.alloc(s)) != CC_OK) return st;
-    return offsets_u64 ? launch_batched<uint64_t>(gv, G, V, offsets, edges, M, o, labels_out, sc.at<uint32_t>(oq), s)
-                       : launch_batched<uint32_t>(gv, G, V, offsets, edges, M, o, labels_out, sc.at<uint32_t>(oq), s);
+    return offsets_u64 ? launch_batched<uint64_t>(gv, G, V, offsets, edges, M, o, labels_out, sc.at<uint32_t>(oq),
+                                                  sc.at<uint32_t>(oo), s)
+                       : launch_batched<uint32_t>(gv, G, V, offsets, edges, M, o, labels_out, sc.at<uint32_t>(oq),
+                                                  sc.at<uint32_t>(oo), s);
 }
 
 cc_status cc_batched_autotune(const uint64_t *gv, uint32_t G, const void *offsets, int offsets_u64,
@@ -204,9 +312,11 @@ cc_status cc_batched_autotune(const uint64_t *gv, uint32_t G, const void *offset
     if (G == 0 || V == 0) return CC_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     std::vector<cc_batch_opt> cands;
-    for (uint32_t mode : {0u, 1u})
-        for (uint32_t threads : {128u, 256u, 512u, 1024u})
-            for (uint32_t smem : {0u, 4096u, 12288u, 24576u, 49152u})
+    // shared-memory thresholds 16384 / 28672 / 57344 / 65536 vertices take
+    // 32 / 56 / 112 / 128 KB per CTA: 7, 4, 2 and 1 CTAs per SM
+    for (uint32_t mode : {0u, 1u, 2u})
+        for (uint32_t threads : {256u, 512u, 1024u})
+            for (uint32_t smem : {0u, 16384u, 28672u, 57344u, 65536u})
                 cands.push_back(cc_batch_opt{threads, smem, mode, 0});
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return CC_ERR_CUDA;

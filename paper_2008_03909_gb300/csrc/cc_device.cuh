@@ -804,4 +804,47 @@ struct LabelCounter {
     }
 };
 
+// LabelCounter that also tracks the arg-max as it counts: every atomicAdd
+// returns the count before it, so its issuer sees the count after it, and
+// the last increment of each label sees that label's final count.  The
+// largest (count << 32 | ~label) seen anywhere is therefore the arg-max with
+// ties to the smallest label, with no pass over the count array.
+struct LabelCounterArg {
+    uint32_t hot = NONE, hot_c = 0, cand = NONE, cand_c = 0;
+    unsigned long long best = 0;
+    __device__ __forceinline__ void bump(uint32_t *cnt, uint32_t l, uint32_t c) {
+        const uint32_t now = atomicAdd(cnt + l, c) + c;
+        const unsigned long long k = ((unsigned long long)now << 32) | (uint32_t)~l;
+        best = k > best ? k : best;
+    }
+    __device__ __forceinline__ void add(uint32_t *cnt, uint32_t l) {
+        if (l == hot) { ++hot_c; return; }
+        if (l == cand) {
+            if (++cand_c > hot_c) {
+                uint32_t t = hot; hot = cand; cand = t;
+                t = hot_c; hot_c = cand_c; cand_c = t;
+            }
+            return;
+        }
+        if (cand_c) bump(cnt, cand, cand_c);
+        cand = l;
+        cand_c = 1;
+    }
+    // every lane of the warp must call this; then the warp's best goes to
+    // *key (one atomicMax per warp; key may be null)
+    __device__ __forceinline__ void flush(uint32_t *cnt, unsigned long long *key) {
+        if (cand_c) bump(cnt, cand, cand_c);
+        const int lane = threadIdx.x & 31;
+        unsigned grp = __match_any_sync(0xFFFFFFFFu, hot);
+        uint32_t sum = __reduce_add_sync(grp, hot_c);
+        if (hot != NONE && sum && lane == __ffs(grp) - 1) bump(cnt, hot, sum);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long y = __shfl_xor_sync(0xFFFFFFFFu, best, o);
+            best = y > best ? y : best;
+        }
+        if (lane == 0 && best && key) atomicMax(key, best);
+    }
+};
+
 }  // namespace ccg

@@ -74,8 +74,13 @@ __device__ __forceinline__ void roots4(const uint32_t *P, uint32_t v0, uint32_t 
     }
 }
 
+// Full compression (FullShortcut).  COUNT: also count every non-root's
+// root into cnt (the labels are then a flat forest) and leave the arg-max
+// key (count << 32 | ~label, the largest count with ties to the smallest
+// label) in *key, which must start at 0.
 template <bool COUNT>
-__global__ void __launch_bounds__(256, 8) k_shortcut(uint32_t *P, uint32_t *prev, uint32_t n, uint32_t *cnt, Dev d) {
+__global__ void __launch_bounds__(256, 8) k_shortcut(uint32_t *P, uint32_t *prev, uint32_t n, uint32_t *cnt,
+                                                     Dev d, unsigned long long *key = nullptr) {
     // 16-byte vector accesses only when both arrays are 16-byte aligned (a
     // caller's label buffer may be any 4-byte-aligned slice)
     const bool vec = (reinterpret_cast<uintptr_t>(P) & 15) == 0 &&
@@ -83,7 +88,7 @@ __global__ void __launch_bounds__(256, 8) k_shortcut(uint32_t *P, uint32_t *prev
     const uint64_t n4 = vec ? n / 4 : 0;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    LabelCounter lc;
+    LabelCounterArg lc;
     for (uint64_t i = tid; i < n4; i += stride) {
         uint4 p = __ldcg(reinterpret_cast<const uint4 *>(P) + i);
         uint32_t x[4], px[4] = {p.x, p.y, p.z, p.w};
@@ -105,7 +110,7 @@ __global__ void __launch_bounds__(256, 8) k_shortcut(uint32_t *P, uint32_t *prev
         if (prev) prev[v] = r;
         if (COUNT && r != v) lc.add(cnt, r);
     }
-    if (COUNT) lc.flush(cnt);
+    if (COUNT) lc.flush(cnt, key);
 }
 
 // ---------------------------------------------------------------- k-out
@@ -281,12 +286,18 @@ k_kout_defer(uint32_t n, uint32_t *P, const uint2 *defer, const uint32_t *dcount
 }
 
 // Second round for k = 2: Union(v, pick1[v]) from the stash written in the
-// first pass (coalesced reads of the stash and of P[v]).
+// first pass (coalesced reads of the stash and of P[v]).  The trees of the
+// first round are not compressed first: the union's finds walk them (with
+// the engine's splicing), which costs less than a full compression pass
+// because first-edge chains are short (a vertex's first neighbour is its
+// smallest).  The stash is dead after its read, so it is zeroed on the way
+// and serves next as the label-count array.
 template <class E>
-__global__ void __launch_bounds__(256, 8) k_kout_apply_pick(const uint32_t *pick1, uint32_t n, uint32_t *P, Dev d) {
+__global__ void __launch_bounds__(256, 8) k_kout_apply_pick(uint32_t *pick1, uint32_t n, uint32_t *P, Dev d) {
     for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
          v += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t w = pick1[v];
+        pick1[v] = 0;
         uint32_t u1[1] = {(uint32_t)v}, w1[1] = {w};
         bool ok[1] = {w != NONE};
         unite_pairs<E, 1>(P, u1, w1, ok, d);
@@ -1722,22 +1733,26 @@ cc_status sample_phase(const Graph &g, const cc_sample_opt &so, const cc_finish_
             k_kout_defer<E><<<gv, TPB, 0, s>>>(g.n, P, defer, dcount, gv, (uint32_t)cap_blk, d);
         }
         if (so.k > 1) {
-            {
-                CC_PROF("k_compress_mid", s);
-                k_shortcut<false><<<gv, TPB, 0, s>>>(P, nullptr, g.n, nullptr, d);
-            }
             if (pick1) {
                 CC_PROF("k_kout_apply_pick", s);
                 k_kout_apply_pick<E><<<gv, TPB, 0, s>>>(pick1, g.n, P, d);
             } else {
+                {
+                    CC_PROF("k_compress_mid", s);
+                    k_shortcut<false><<<gv, TPB, 0, s>>>(P, nullptr, g.n, nullptr, d);
+                }
                 CC_PROF("k_kout_rest", s);
                 launch_kout<OffT, E>(gv, s, I, g.A, g.n, g.m, so.k, so.kout_rule, so.seed, P, d, 1u, so.k);
             }
         }
         if (count_into) {
-            CC_TRY(cudaMemsetAsync(count_into, 0, (size_t)g.n * 4, s));
+            // the arg-max key is taken as the compression counts (identify
+            // then only converts it); with k = 2 the zeroed stash counts
+            uint32_t *cnt = pick1 ? pick1 : count_into;
+            if (!pick1) CC_TRY(cudaMemsetAsync(cnt, 0, (size_t)g.n * 4, s));
+            CC_TRY(cudaMemsetAsync(&w.ctl()->key, 0, 8, s));
             CC_PROF("k_compress_count", s);
-            k_shortcut<true><<<gv, TPB, 0, s>>>(P, nullptr, g.n, count_into, d);
+            k_shortcut<true><<<gv, TPB, 0, s>>>(P, nullptr, g.n, cnt, d, &w.ctl()->key);
         } else {
             CC_PROF("k_compress", s);
             k_shortcut<false><<<gv, TPB, 0, s>>>(P, nullptr, g.n, nullptr, d);
@@ -1762,14 +1777,15 @@ cc_status identify_phase(const uint32_t *L, uint32_t n, uint32_t samples, uint64
     uint32_t *cnt = w.sc.at<uint32_t>(w.o_counts);
     Ctl *ctl = w.ctl();
     const unsigned gv = grid_for(di, n, TPB);
+    // counted: the compression that counted also left the arg-max key
     if (!counted) {
         CC_TRY(cudaMemsetAsync(cnt, 0, (size_t)n * 4, s));
-        CC_PROF("k_count_labels", s);
-        if (flat) k_count_labels<true><<<gv, TPB, 0, s>>>(L, n, cnt, d);
-        else k_count_labels<false><<<gv, TPB, 0, s>>>(L, n, cnt, d);
-    }
-    CC_TRY(cudaMemsetAsync(&ctl->key, 0, 8, s));
-    {
+        {
+            CC_PROF("k_count_labels", s);
+            if (flat) k_count_labels<true><<<gv, TPB, 0, s>>>(L, n, cnt, d);
+            else k_count_labels<false><<<gv, TPB, 0, s>>>(L, n, cnt, d);
+        }
+        CC_TRY(cudaMemsetAsync(&ctl->key, 0, 8, s));
         CC_PROF("k_argmax_counts", s);
         k_argmax_counts<<<gv, TPB, 0, s>>>(cnt, n, &ctl->key);
     }

@@ -18,7 +18,9 @@ def batch_with_edge_cases(count, seed):
     gs.insert(3, synth.empty(0))
     gs.insert(5, synth.empty(1))
     gs.insert(7, synth.counterexample())
-    gs.append(synth.rmat(15, 4, seed=seed))          # larger than every shared-memory threshold but one
+    gs.append(synth.rmat(15, 4, seed=seed))          # larger than every shared-memory threshold but two
+    gs.append(synth.grid2d(256, 256, 0.1, seed=seed))  # exactly 65536 vertices: the largest 16-bit local id
+    gs.append(synth.rmat(17, 2, seed=seed))          # above 65536: global parents under every schedule
     gs.append(synth.grid2d(260, 240, 0.3, seed=seed))
     return gs
 
@@ -34,9 +36,9 @@ def batch():
     return gs, gv.cuda(), off.cuda(), edg.cuda(), expected(gs)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 @pytest.mark.parametrize("threads", [128, 256, 1024])
-@pytest.mark.parametrize("smem", [0, 4096, 49152])
+@pytest.mark.parametrize("smem", [0, 4096, 57344, 65536])
 def test_batched_schedules(batch, mode, threads, smem):
     gs, gv, off, edg, want = batch
     lab = cc.cc_batched(gv, off, edg, cc.batch_opt(threads, smem, mode))
