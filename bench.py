@@ -71,6 +71,8 @@ def parse():
     p.add_argument("--minlabel", action="store_true",
                    help="also time the sixteen Liu-Tarjan variants, Stergiou and label propagation (none / k-out)")
     p.add_argument("--batched-graphs", type=int, default=10000)
+    p.add_argument("--batched-schedule", default="",
+                   help="threads,smem_max_vertices,mode: time this schedule instead of autotuning")
     p.add_argument("--sel-train", type=int, default=2000)
     p.add_argument("--sel-test", type=int, default=200)
     p.add_argument("--sel-scale-lo", type=int, default=14)
@@ -673,7 +675,12 @@ def bench_batched(args, cc, synth, dev):
         off = off.to(torch.int32)
     gv, off, edg = gv.to(dev), off.to(dev), edg.to(dev)
     ob = 4 if off.dtype == torch.int32 else 8
-    lab, best, tune_ms = cc.cc_batched_autotune(gv, off, edg)
+    if args.batched_schedule:
+        t, sm, md = (int(x) for x in args.batched_schedule.split(","))
+        best = cc.batch_opt(t, sm, md)
+        lab = cc.cc_batched(gv, off, edg, best)
+    else:
+        lab, best, tune_ms = cc.cc_batched_autotune(gv, off, edg)
     reps = 10
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
@@ -784,12 +791,12 @@ def bench_incremental(args, cc, synth, dev, qf):
     # rate (latency at the load the plain loop sustains)
     answers = [torch.empty(max(1, nq), dtype=torch.uint8).pin_memory() for (_, _, _, nq) in batches]
 
-    def served(interval_s):
+    def served(interval_s, zero_copy=False):
         base = synth.rmat(args.incr_scale, 16, seed=2, device=dev)
         inc2 = cc.Incremental(n, base.offsets, base.edges, finish=cc.finish_opt(args.incr_finish))
         del base
         torch.cuda.empty_cache()
-        srv = cc.Server(inc2, slots=4, slot_pairs=1 << 22)
+        srv = cc.Server(inc2, slots=4, slot_pairs=1 << 22, zero_copy=zero_copy)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         tickets = []
@@ -811,6 +818,7 @@ def bench_incremental(args, cc, synth, dev, qf):
 
     wall_srv, lat_srv, same_all = served(0.0)
     wall_pace, lat_pace, same_pace = served(wall / len(batches))
+    wall_zc, lat_zc, same_zc = served(0.0, zero_copy=True)
     return {"base": f"rmat{args.incr_scale}_ef16", "n": n, "finish": args.incr_finish, "batches": len(batches),
             "query_fraction": qf,
             "inserts": total_ins, "queries": total_q,
@@ -824,7 +832,12 @@ def bench_incremental(args, cc, synth, dev, qf):
                        "p50_ms": round(pct(lat_srv, 50), 4), "p99_ms": round(pct(lat_srv, 99), 4),
                        "wall_s": round(wall_srv, 4), "plain_wall_s": round(wall, 4),
                        "speedup_vs_plain": round(wall / wall_srv, 3),
-                       "answers_equal_plain_every_batch": same_all and same_pace,
+                       "answers_equal_plain_every_batch": same_all and same_pace and same_zc,
+                       "staging": "copy engines (requests staged through 4 device slots of 2^22 pairs)",
+                       "zero_copy": {"ops_per_s": round((total_ins + total_q) / wall_zc, 1),
+                                     "p50_ms": round(pct(lat_zc, 50), 4), "p99_ms": round(pct(lat_zc, 99), 4),
+                                     "wall_s": round(wall_zc, 4),
+                                     "note": "kernels read the pinned requests in place over the host link"},
                        "latency": "submit to answers in host memory, all batches submitted back to back",
                        "paced": {"interval_ms": round(1e3 * wall / len(batches), 4),
                                  "p50_ms": round(pct(lat_pace, 50), 4), "p99_ms": round(pct(lat_pace, 99), 4),

@@ -285,7 +285,8 @@ cc_status cc_random_sectors(const uint32_t *x, uint64_t words, uint64_t count, u
  *   memory as 16-bit local ids (2 bytes per vertex of the threshold per
  *   CTA), larger ones in their slice of labels_out; vertex_mode 0 = one
  *   thread per vertex, 1 = one warp per vertex, 2 = 32 vertices per warp,
- *   the warp walking their concatenated edge lists.  Graphs are taken
+ *   the warp walking their concatenated edge lists, 3 = mode 2 at two
+ *   1024-thread CTAs per SM (threads must be 1024).  Graphs are taken
  *   largest first.  Any schedule gives the same labels.  Scratch: 4 G + 4
  *   bytes (stream-ordered).
  * cc_batched_autotune times every candidate schedule on this batch (it
@@ -345,16 +346,20 @@ cc_status cc_incr_destroy(cc_incr *h);
  * cc_server_create: the server uses `h` exclusively until it is destroyed.
  * cc_server_submit: inserts (2k uint32) and queries (2q uint32) are HOST
  *   arrays, answers a HOST uint8[q] array; all three must stay valid until
- *   cc_server_wait returns.  When all three are pinned (device-mapped) host
- *   memory, the kernels read and write them in place (no staging copies, no
- *   slot); otherwise the request is staged through the slots.
+ *   cc_server_wait returns.  Requests are staged through the slots: the
+ *   copy engines move request r+1's pairs in while request r's kernels run
+ *   and request r-1's answers go out.  With CC_SERVER_ZERO_COPY in flags,
+ *   a request whose three arrays are all pinned (device-mapped) host memory
+ *   is instead read and written in place by the kernels (no copy, no slot),
+ *   which serialises its transfer with its compute.
  * cc_server_wait: blocks until the request's answers are in host memory;
  *   *latency_ms_out (may be NULL) gets submit-to-completion time.
  * cc_server_destroy: drains the queue, then frees the server (not h). */
 typedef struct cc_server cc_server;
+#define CC_SERVER_ZERO_COPY 1u
 typedef struct cc_server_opt {
     uint32_t slots;        /* device slots in flight (1..64; 4) */
-    uint32_t reserved;     /* must be 0 */
+    uint32_t flags;        /* 0 or CC_SERVER_ZERO_COPY (default 0) */
     uint64_t slot_pairs;   /* pairs per slot (1..2^30; 2^22) */
 } cc_server_opt;
 void cc_server_default_opt(cc_server_opt *opt);
@@ -391,16 +396,36 @@ cc_status cc_server_destroy(cc_server *s);
 #define CC_MLP_NPARAM (2 * CC_MLP_IN + CC_MLP_IN * CC_MLP_HID + CC_MLP_HID + CC_MLP_HID * CC_MLP_HID + \
                        CC_MLP_HID + CC_MLP_HID * CC_MLP_OUT + CC_MLP_OUT)
 /* Selector features of a graph (same conventions as cc_static; n >= 1):
- * feat_out (DEVICE float[16]) <- 0 log2(n+1), 1 log2(m+1), 2 m/n,
- * 3 log2(max degree + 1), 4 degree variance / mean^2, 5-7 fractions of
- * vertices of degree 0, 1, 2, 8 fraction of degree 3..16, 9 fraction of
- * degree > 64, 10 share of edges at vertices of degree > 64, 11 size of
- * the largest k-out (k = 2, `seed`) sampled cluster / n, 12 sampled
- * clusters / n, 13 edges left for the finish after k-out / m, 14 levels of
- * a BFS from the highest-degree vertex capped at 64, divided by 64, 15
- * vertices that BFS reached / n.  Synchronises the stream. */
+ * feat_out (DEVICE float[16]) <- the features the selected path
+ * (cc_select_static) computes on its way, from the k-out (k = 2, `seed`)
+ * sample it starts with: 0 log2(n+1), 1 log2(m+1), 2 m/n, 3 log2(max
+ * degree + 1), 4 degree variance / mean^2, 5-7 fractions of vertices of
+ * degree 0, 1, 2, 8 fraction of degree 3..16, 9 fraction of degree > 64,
+ * 10 share of edges at vertices of degree > 64, 11 size of the frequent
+ * sampled cluster L_max / n, 12 vertices outside their own singleton after
+ * sampling / n, 13 edges left for the finish (edges out of vertices not in
+ * L_max) / m, 14 light candidates of the finish (not in L_max, degree
+ * 1..32) / n, 15 parent steps walked per non-root by the sampling's last
+ * compression (how deep the sampled trees were).  Stream-ordered. */
 cc_status cc_features(const void *offsets, int offsets_u64, const uint32_t *edges, uint32_t n, uint64_t m,
                       uint64_t seed, float *feat_out, void *stream);
+/* The selected static path (the learned selector; no counterpart in the
+ * paper, whose Section 4.7 picks by a hand-made decision tree).  Labels
+ * exactly as cc_static, by one of 12 classes c = 4 * sampling + finish:
+ * sampling 0 k-out (k = 2), 1 BFS (3 tries), 2 LDD (beta 0.2); finish 0
+ * UF-Rem-CAS (FindNaive, SplitAtomicOne), 1 UF-Async (FindSplit), 2 SV,
+ * 3 Liu-Tarjan PRF.  The default class 0's k-out sample is computed first;
+ * the features (cc_features) come from it and the MLP `params` (DEVICE
+ * float[CC_MLP_NPARAM]) picks the class on the device.  The host waits
+ * for the choice only (not for the labels): class 0 and the other k-out
+ * classes continue on the same sample and candidate lists; BFS and LDD
+ * classes run the static path from scratch.  force_class in [0, 12)
+ * overrides the MLP (params may then be NULL); -1 uses it.  feat_out
+ * (DEVICE float[16], may be NULL) receives the features; *class_out (host,
+ * may be NULL) the class run.  The labels are stream-ordered on `stream`. */
+cc_status cc_select_static(const void *offsets, int offsets_u64, const uint32_t *edges, uint32_t n, uint64_t m,
+                           const float *params, int force_class, uint64_t seed, uint32_t *labels_out,
+                           float *feat_out, int32_t *class_out, void *stream);
 cc_status cc_mlp_init(float *params, uint64_t seed, void *stream);
 cc_status cc_mlp_set_norm(float *params, const float *X, uint32_t B, void *stream);
 cc_status cc_mlp_forward(const float *params, const float *X, uint32_t B, float *logits, float *acts, void *stream);

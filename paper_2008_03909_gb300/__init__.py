@@ -69,7 +69,7 @@ class BatchOpt(ctypes.Structure):
 
 
 class ServerOpt(ctypes.Structure):
-    _fields_ = [("slots", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("slot_pairs", ctypes.c_uint64)]
+    _fields_ = [("slots", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("slot_pairs", ctypes.c_uint64)]
 
 
 class Stats(ctypes.Structure):
@@ -142,6 +142,10 @@ _SIGS = {
                                          ctypes.c_void_p, ctypes.c_void_p]),
     "cc_features": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64,
                                    ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]),
+    "cc_select_static": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_uint32,
+                                        ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32),
+                                        ctypes.c_void_p]),
     "cc_mlp_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]),
     "cc_mlp_set_norm": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]),
     "cc_mlp_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p,
@@ -482,6 +486,22 @@ def cc_features(offsets, edges, seed: int = 1, out=None, stream=None) -> torch.T
     return out
 
 
+def cc_select_static(offsets, edges, params=None, force_class: int = -1, seed: int = 1, labels_out=None,
+                     feat_out=None, stream=None):
+    """The selected static path: labels (int32 view of uint32) and the class
+    run (see connectit_gb.h).  params: the MLP's parameter tensor (CUDA
+    float32), or None with force_class >= 0."""
+    Ip, u64, Ap, n, m = _graph_args(offsets, edges)
+    if labels_out is None:
+        labels_out = torch.empty(n, dtype=torch.int32, device=offsets.device)
+    cls = ctypes.c_int32(-1)
+    pp = ctypes.c_void_p(params.data_ptr()) if params is not None else None
+    fp = ctypes.c_void_p(feat_out.data_ptr()) if feat_out is not None else None
+    _check(lib().cc_select_static(Ip, u64, Ap, n, m, pp, force_class, seed, ctypes.c_void_p(labels_out.data_ptr()),
+                                  fp, ctypes.byref(cls), _stream(stream)), "cc_select_static")
+    return labels_out, cls.value
+
+
 MLP_IN, MLP_HID, MLP_OUT = 16, 64, 12
 MLP_NPARAM = 2 * MLP_IN + MLP_IN * MLP_HID + MLP_HID + MLP_HID * MLP_HID + MLP_HID + MLP_HID * MLP_OUT + MLP_OUT
 
@@ -575,12 +595,14 @@ class Server:
     """Continuous-batching request loop over an Incremental handle.  Host
     tensors (pinned for overlap) are kept alive until wait()."""
 
-    def __init__(self, inc: "Incremental", slots: int = 4, slot_pairs: int = 1 << 22):
+    ZERO_COPY = 1
+
+    def __init__(self, inc: "Incremental", slots: int = 4, slot_pairs: int = 1 << 22, zero_copy: bool = False):
         self._s = ctypes.c_void_p(0)
         self._keep = {}
         self.inc = inc
-        _check(lib().cc_server_create(inc._h, ctypes.byref(ServerOpt(slots, 0, slot_pairs)), ctypes.byref(self._s)),
-               "cc_server_create")
+        opt = ServerOpt(slots, self.ZERO_COPY if zero_copy else 0, slot_pairs)
+        _check(lib().cc_server_create(inc._h, ctypes.byref(opt), ctypes.byref(self._s)), "cc_server_create")
 
     def submit(self, inserts: torch.Tensor | None, queries: torch.Tensor | None, answers: torch.Tensor | None = None):
         for t, nm in ((inserts, "inserts"), (queries, "queries")):

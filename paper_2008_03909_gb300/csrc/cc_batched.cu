@@ -9,12 +9,14 @@
 // Each CTA then takes whole graphs from a global queue in that order.  A
 // graph of at most `smem_max_vertices` (<= 65536) vertices keeps its parent
 // array in shared memory as 16-bit local ids (block-local atomics, one
-// coalesced global write per vertex at the end); a larger one uses its own
-// slice of the output as a 32-bit parent array in global memory (L2).
+// coalesced global write per vertex at the end); a graph of at most 65536
+// vertices keeps ids below the threshold there and the rest in its slice of
+// the output; a larger one uses its slice of the output as a 32-bit parent
+// array in global memory (L2).
 // Vertices are mapped one per thread (mode 0), one per warp (mode 1), or 32
 // per warp with the warp walking the concatenation of their edge lists, 128
 // consecutive edge words per step (mode 2, the static path's light-vertex
-// walk).  cc_batched_autotune times the candidate schedules on the caller's
+// walk; mode 3 the same at two 1024-thread CTAs per SM).  cc_batched_autotune times the candidate schedules on the caller's
 // batch and returns the fastest.
 #include <vector>
 
@@ -24,20 +26,46 @@ using namespace ccg;
 
 namespace {
 
-__device__ __forceinline__ uint32_t cas_par(uint32_t *p, uint32_t cmp, uint32_t val) {
-    return atomicCAS(p, cmp, val);
-}
-__device__ __forceinline__ uint32_t cas_par(uint16_t *p, uint32_t cmp, uint32_t val) {
-    return atomicCAS(reinterpret_cast<unsigned short *>(p), (unsigned short)cmp, (unsigned short)val);
-}
+// A graph's parent array (local ids): 16-bit in shared memory (ParS), 32-bit
+// in the graph's slice of the output (ParG), or split (ParH): ids below S in
+// shared memory, the rest in the output slice, for graphs a little larger
+// than the shared-memory threshold.  Reads are volatile (coherent for the
+// block in shared memory, L2 in global memory).
+struct ParS {
+    uint16_t *s;
+    __device__ __forceinline__ uint32_t ld(uint32_t i) const { return reinterpret_cast<volatile uint16_t *>(s)[i]; }
+    __device__ __forceinline__ uint32_t cas(uint32_t i, uint32_t c, uint32_t v) const {
+        return atomicCAS(reinterpret_cast<unsigned short *>(s + i), (unsigned short)c, (unsigned short)v);
+    }
+    __device__ __forceinline__ void set(uint32_t i, uint32_t v) const { s[i] = (uint16_t)v; }
+};
+struct ParG {
+    uint32_t *g;
+    __device__ __forceinline__ uint32_t ld(uint32_t i) const { return reinterpret_cast<volatile uint32_t *>(g)[i]; }
+    __device__ __forceinline__ uint32_t cas(uint32_t i, uint32_t c, uint32_t v) const { return atomicCAS(g + i, c, v); }
+    __device__ __forceinline__ void set(uint32_t i, uint32_t v) const { g[i] = v; }
+};
+struct ParH {
+    uint16_t *s;
+    uint32_t *g;
+    uint32_t S;
+    __device__ __forceinline__ uint32_t ld(uint32_t i) const {
+        return i < S ? (uint32_t)reinterpret_cast<volatile uint16_t *>(s)[i] : reinterpret_cast<volatile uint32_t *>(g)[i];
+    }
+    __device__ __forceinline__ uint32_t cas(uint32_t i, uint32_t c, uint32_t v) const {
+        return i < S ? (uint32_t)atomicCAS(reinterpret_cast<unsigned short *>(s + i), (unsigned short)c, (unsigned short)v)
+                     : atomicCAS(g + i, c, v);
+    }
+    __device__ __forceinline__ void set(uint32_t i, uint32_t v) const {
+        if (i < S) s[i] = (uint16_t)v;
+        else g[i] = v;
+    }
+};
 
-// Rem-CAS union (Algorithm 14 with SplitAtomicOne) on a parent array of
-// 16-bit ids in shared memory or 32-bit ids in global memory, read through
-// volatile loads (coherent for the block in shared memory, L2 in global).
-template <typename T>
-__device__ __forceinline__ void unite_any(T *P, uint32_t u, uint32_t v, const Dev &d) {
-    volatile T *VP = P;
-    uint32_t ru = u, rv = v, pru = VP[ru], prv = VP[rv];
+// Rem-CAS union (Algorithm 14 with SplitAtomicOne) on a parent array.
+template <class Par>
+__device__ __forceinline__ void unite_any(const Par &P, uint32_t u, uint32_t v, const Dev &d) {
+    uint32_t ru = u, rv = v, pru = P.ld(ru), prv = P.ld(rv);
     Guard g;
     while (pru != prv) {
         if (pru < prv) {
@@ -45,12 +73,12 @@ __device__ __forceinline__ void unite_any(T *P, uint32_t u, uint32_t v, const De
             t = pru; pru = prv; prv = t;
         }
         if (ru == pru) {
-            uint32_t old = cas_par(P + ru, ru, prv);
+            uint32_t old = P.cas(ru, ru, prv);
             if (old == ru) return;
             pru = old;
         } else {
-            uint32_t w = VP[pru];
-            if (pru != w) cas_par(P + ru, pru, w);
+            uint32_t w = P.ld(pru);
+            if (pru != w) P.cas(ru, pru, w);
             ru = pru;
             pru = w;
         }
@@ -58,14 +86,13 @@ __device__ __forceinline__ void unite_any(T *P, uint32_t u, uint32_t v, const De
     }
 }
 
-template <typename T>
-__device__ __forceinline__ uint32_t root_any(const T *P, uint32_t x, const Dev &d) {
-    const volatile T *VP = P;
-    uint32_t p = VP[x];
+template <class Par>
+__device__ __forceinline__ uint32_t root_any(const Par &P, uint32_t x, const Dev &d) {
+    uint32_t p = P.ld(x);
     Guard g;
     while (p != x) {
         x = p;
-        p = VP[x];
+        p = P.ld(x);
         if (!g.step(d)) break;
     }
     return x;
@@ -73,9 +100,9 @@ __device__ __forceinline__ uint32_t root_any(const T *P, uint32_t x, const Dev &
 
 // Edge functor of the warp walk: each undirected edge once, from its larger
 // endpoint.
-template <typename T>
+template <class Par>
 struct BatchUnite {
-    T *P;
+    Par P;
     Dev d;
     __device__ __forceinline__ void apply4(uint32_t u, const uint32_t (&v)[4], const bool (&ok)[4]) {
 #pragma unroll
@@ -90,9 +117,9 @@ struct BatchUnite {
 };
 
 // Union-find over graph [vb, vb + ng) with parent array P (local ids).
-template <typename OffT, int MODE, typename T>
+template <typename OffT, int MODE, class Par>
 __device__ __forceinline__ void batch_unions(const OffT *I, const uint32_t *A, uint64_t M, uint64_t vb, uint32_t ng,
-                                             T *P, const Dev &d) {
+                                             const Par &P, const Dev &d) {
     const int lane = threadIdx.x & 31;
     const uint32_t wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     if (MODE == 0) {
@@ -116,14 +143,29 @@ __device__ __forceinline__ void batch_unions(const OffT *I, const uint32_t *A, u
             }
         }
     } else {
-        BatchUnite<T> f{P, d};
-        // every lane of the warp takes part in each step (shuffles)
-        for (uint32_t base = wid * 32; base < ng; base += nwarp * 32) {
+        BatchUnite<Par> f{P, d};
+        // every lane of the warp takes part in each step (shuffles); the next
+        // tile's offsets are loaded before this tile's edges are walked
+        uint32_t base = wid * 32;
+        uint64_t o0 = 0, o1 = 0;
+        if (base + lane < ng) {
+            o0 = (uint64_t)ld_off(I + vb + base + lane);
+            o1 = (uint64_t)ld_off(I + vb + base + lane + 1);
+        }
+        for (; base < ng; base += nwarp * 32) {
             const uint32_t i = base + lane;
+            const uint32_t nb = base + nwarp * 32;
+            uint64_t n0 = 0, n1 = 0;
+            if (nb + lane < ng) {
+                n0 = (uint64_t)ld_off(I + vb + nb + lane);
+                n1 = (uint64_t)ld_off(I + vb + nb + lane + 1);
+            }
             uint64_t b = 0, e = 0;
-            if (i < ng) clamp_range((uint64_t)ld_off(I + vb + i), (uint64_t)ld_off(I + vb + i + 1), M, b, e, d);
+            if (i < ng) clamp_range(o0, o1, M, b, e, d);
             const uint64_t dg = e - b;
             warp_light_edges(i < ng ? i : 0, b, dg > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)dg, A, ng, f, d);
+            o0 = n0;
+            o1 = n1;
         }
     }
 }
@@ -161,8 +203,10 @@ __global__ void __launch_bounds__(1024) k_batch_order(const uint64_t *gv, uint32
         order[atomicAdd(&cnt[size_class(gv[g], gv[g + 1], V)], 1u)] = g;
 }
 
+// MODE 3 is MODE 2 built for two 1024-thread CTAs per SM (64 warps, at most
+// 32 registers a thread): more tiles in flight per SM.
 template <typename OffT, int MODE>
-__global__ void __launch_bounds__(1024) k_batched(const uint64_t *gv, const uint32_t *order, uint32_t G, uint64_t V,
+__global__ void __launch_bounds__(1024, MODE == 3 ? 2 : 1) k_batched(const uint64_t *gv, const uint32_t *order, uint32_t G, uint64_t V,
                                                   const OffT *I, const uint32_t *A, uint64_t M, uint32_t *labels,
                                                   uint32_t *queue, uint32_t smem_max, Dev d) {
     extern __shared__ uint16_t Ps[];
@@ -184,20 +228,32 @@ __global__ void __launch_bounds__(1024) k_batched(const uint64_t *gv, const uint
         const uint32_t ng = (uint32_t)(ve - vb);
         Dev dg = d;
         if (dg.cap == 0) dg.cap = 2ull * ng + 1024;
+        constexpr int BM = MODE == 3 ? 2 : MODE;
         if (ng <= smem_max) {
-            for (uint32_t i = threadIdx.x; i < ng; i += blockDim.x) Ps[i] = (uint16_t)i;
+            const ParS P{Ps};
+            for (uint32_t i = threadIdx.x; i < ng; i += blockDim.x) P.set(i, i);
             __syncthreads();
-            batch_unions<OffT, MODE, uint16_t>(I, A, M, vb, ng, Ps, dg);
+            batch_unions<OffT, BM>(I, A, M, vb, ng, P, dg);
             __syncthreads();
             // final shortcut: the root of each tree is its smallest vertex
-            for (uint32_t i = threadIdx.x; i < ng; i += blockDim.x) labels[vb + i] = root_any(Ps, i, dg);
+            for (uint32_t i = threadIdx.x; i < ng; i += blockDim.x) labels[vb + i] = root_any(P, i, dg);
+        } else if (ng <= 65536u && smem_max > 0) {
+            // ids below smem_max in shared memory, the rest in the output
+            // slice; the final write of a vertex's root into its own slot
+            // there is a valid compression for concurrent readers
+            const ParH P{Ps, labels + vb, smem_max};
+            for (uint32_t i = threadIdx.x; i < ng; i += blockDim.x) P.set(i, i);
+            __syncthreads();
+            batch_unions<OffT, BM>(I, A, M, vb, ng, P, dg);
+            __syncthreads();
+            for (uint32_t i = threadIdx.x; i < ng; i += blockDim.x) labels[vb + i] = root_any(P, i, dg);
         } else {
-            uint32_t *P = labels + vb;
-            for (uint32_t i = threadIdx.x; i < ng; i += blockDim.x) P[i] = i;
+            const ParG P{labels + vb};
+            for (uint32_t i = threadIdx.x; i < ng; i += blockDim.x) P.set(i, i);
             __syncthreads();
-            batch_unions<OffT, MODE, uint32_t>(I, A, M, vb, ng, P, dg);
+            batch_unions<OffT, BM>(I, A, M, vb, ng, P, dg);
             __syncthreads();
-            for (uint32_t i = threadIdx.x; i < ng; i += blockDim.x) P[i] = root_any(P, i, dg);
+            for (uint32_t i = threadIdx.x; i < ng; i += blockDim.x) labels[vb + i] = root_any(P, i, dg);
         }
         __syncthreads();
     }
@@ -206,14 +262,17 @@ __global__ void __launch_bounds__(1024) k_batched(const uint64_t *gv, const uint
 cc_status check_batch_opt(const cc_batch_opt &o) {
     if (o.threads != 128 && o.threads != 256 && o.threads != 512 && o.threads != 1024) return CC_ERR_INVALID;
     if (o.smem_max_vertices > 65536u) return CC_ERR_INVALID;
-    if (o.vertex_mode > 2 || o.reserved != 0) return CC_ERR_INVALID;
+    if (o.vertex_mode > 3 || o.reserved != 0) return CC_ERR_INVALID;
+    if (o.vertex_mode == 3 && o.threads != 1024) return CC_ERR_INVALID;
     return CC_OK;
 }
 
 template <typename OffT>
 const void *batched_fn(uint32_t mode) {
-    return mode == 2 ? (const void *)k_batched<OffT, 2>
-                     : mode == 1 ? (const void *)k_batched<OffT, 1> : (const void *)k_batched<OffT, 0>;
+    return mode == 3   ? (const void *)k_batched<OffT, 3>
+           : mode == 2 ? (const void *)k_batched<OffT, 2>
+           : mode == 1 ? (const void *)k_batched<OffT, 1>
+                       : (const void *)k_batched<OffT, 0>;
 }
 
 template <typename OffT>
@@ -248,7 +307,10 @@ cc_status launch_batched(const uint64_t *gv, uint32_t G, uint64_t V, const void 
     if (e != cudaSuccess) return from_cuda(e);
     const OffT *I = static_cast<const OffT *>(offsets);
     CC_PROF("k_batched", s);
-    if (o.vertex_mode == 2)
+    if (o.vertex_mode == 3)
+        k_batched<OffT, 3><<<(unsigned)grid, o.threads, smem, s>>>(gv, order, G, V, I, edges, M, labels, queue,
+                                                                    o.smem_max_vertices, d);
+    else if (o.vertex_mode == 2)
         k_batched<OffT, 2><<<(unsigned)grid, o.threads, smem, s>>>(gv, order, G, V, I, edges, M, labels, queue,
                                                                     o.smem_max_vertices, d);
     else if (o.vertex_mode == 1)
@@ -314,10 +376,10 @@ cc_status cc_batched_autotune(const uint64_t *gv, uint32_t G, const void *offset
     std::vector<cc_batch_opt> cands;
     // shared-memory thresholds 16384 / 28672 / 57344 / 65536 vertices take
     // 32 / 56 / 112 / 128 KB per CTA: 7, 4, 2 and 1 CTAs per SM
-    for (uint32_t mode : {0u, 1u, 2u})
+    for (uint32_t mode : {0u, 1u, 2u, 3u})
         for (uint32_t threads : {256u, 512u, 1024u})
             for (uint32_t smem : {0u, 16384u, 28672u, 57344u, 65536u})
-                cands.push_back(cc_batch_opt{threads, smem, mode, 0});
+                if (mode != 3 || threads == 1024) cands.push_back(cc_batch_opt{threads, smem, mode, 0});
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return CC_ERR_CUDA;
     float best = -1.f;

@@ -703,8 +703,63 @@ __device__ __forceinline__ void write_chunks(ChunkRef *chunks, uint64_t cap, uin
     for (uint32_t c = 0; c < nc; ++c) chunks[slot + c] = ChunkRef{u, c};
 }
 
+// Chunk-list slots reserved by a warp in runs of at least WARP_RES: one
+// global atomic per run instead of one per warp step that has a heavy
+// vertex (a single counter hit by every warp step serialised at the L2).
+// Slots of a run that stay unused are filled with empty chunks (u = NONE)
+// when the warp takes a new run or finishes (close()), and the chunk pass
+// skips them.  A grid leaves at most WARP_RES - 1 empty slots per warp,
+// which CHUNK_SLACK covers (64 warps per SM, up to 256 SMs).
+constexpr uint32_t WARP_RES = 64;
+constexpr uint64_t CHUNK_SLACK = 64ull * 256 * WARP_RES;
+
+struct WarpSlots {
+    uint64_t cur = 0, end = 0;   // warp-uniform
+    // every lane calls with the same total; returns the warp's first slot
+    __device__ __forceinline__ uint64_t take(uint32_t *counter, uint32_t total, ChunkRef *chunks, uint64_t cap) {
+        if (cur + total > end) {
+            close(chunks, cap);
+            const uint32_t want = total > WARP_RES ? total : WARP_RES;
+            uint32_t b = 0;
+            if ((threadIdx.x & 31) == 0) b = atomicAdd(counter, want);
+            b = __shfl_sync(0xFFFFFFFFu, b, 0);
+            cur = b;
+            end = (uint64_t)b + want;
+        }
+        const uint64_t r = cur;
+        cur += total;
+        return r;
+    }
+    __device__ __forceinline__ void close(ChunkRef *chunks, uint64_t cap) {
+        for (uint64_t x = cur + (threadIdx.x & 31); x < end && x < cap; x += 32) chunks[x] = ChunkRef{NONE, 0};
+        cur = end;
+    }
+};
+
+// Binning of one warp step's vertices: each lane's nc chunks go to slots
+// from the warp's reservation.
+__device__ __forceinline__ void warp_bin_chunks(WarpSlots &ws, uint32_t *counter, ChunkRef *chunks, uint64_t cap,
+                                                uint32_t nc, uint32_t u, const Dev &d) {
+    const int lane = threadIdx.x & 31;
+    uint32_t incl = nc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    if (total == 0) return;   // warp-uniform
+    const uint64_t base = ws.take(counter, total, chunks, cap);
+    const uint64_t slot = base + incl - nc;
+    if (nc) {
+        if (slot + nc > cap) { atomicOr(d.err, ERR_NONCONVERGED); return; }
+        for (uint32_t c = 0; c < nc; ++c) chunks[slot + c] = ChunkRef{u, c};
+    }
+}
+
 // Warps of the grid walk the chunk list [0, min(*count, cap)) (the count
 // can pass the capacity only on malformed offsets, which is flagged).
+// Empty slots (u = NONE, left by warp reservations) are skipped.
 template <typename OffT, class F>
 __device__ __forceinline__ void run_chunks(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m,
                                            const ChunkRef *chunks, const uint32_t *count, uint64_t cap, F &f,
@@ -714,6 +769,7 @@ __device__ __forceinline__ void run_chunks(const OffT *I, const uint32_t *A, uin
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t i = warp; i < total; i += nwarps) {
         ChunkRef c = chunks[i];
+        if (c.u == NONE) continue;
         uint64_t b, e;
         vertex_range(I, c.u, m, b, e, d);
         uint64_t cb = b + (uint64_t)c.c * CHUNK;

@@ -30,22 +30,44 @@ __global__ void __launch_bounds__(256, 8) k_incr_iota(uint32_t *P, uint32_t n) {
         P[i] = (uint32_t)i;
 }
 
-// Insert(u, v) = Union(u, v) for every pair; four pairs per thread step so
-// their parent loads overlap.
-template <class E>
-__global__ void __launch_bounds__(256, 8) k_incr_insert(uint32_t *P, uint32_t n, const uint32_t *pairs, uint64_t k, Dev d) {
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i0 < k; i0 += 4 * stride) {
-        uint32_t u[4], v[4], pu[4], pv[4];
-        bool ok[4];
+// The four consecutive pairs [4g, 4g + 4) of a batch: two 16-byte loads
+// when the pair array is 16-byte aligned and the group is whole (adjacent
+// threads then read adjacent 32-byte sectors), else word loads.  ok[j] is
+// false past the end and for ids >= n (flagged).
+__device__ __forceinline__ void load_pairs4(const uint32_t *pairs, uint64_t g, uint64_t k, uint32_t n, bool vec,
+                                            uint32_t (&u)[4], uint32_t (&v)[4], bool (&ok)[4], const Dev &d) {
+    const uint64_t i0 = 4 * g;
+    if (vec && i0 + 4 <= k) {
+        const uint4 a = __ldcs(reinterpret_cast<const uint4 *>(pairs) + 2 * g);
+        const uint4 b = __ldcs(reinterpret_cast<const uint4 *>(pairs) + 2 * g + 1);
+        u[0] = a.x; v[0] = a.y; u[1] = a.z; v[1] = a.w;
+        u[2] = b.x; v[2] = b.y; u[3] = b.z; v[3] = b.w;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ok[j] = true;
+    } else {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            uint64_t i = i0 + j * stride;
-            ok[j] = i < k;
-            u[j] = ok[j] ? __ldcs(pairs + 2 * i) : 0;
-            v[j] = ok[j] ? __ldcs(pairs + 2 * i + 1) : 0;
-            if (ok[j] && (u[j] >= n || v[j] >= n)) { atomicOr(d.err, ERR_BAD_EDGE); ok[j] = false; }
+            ok[j] = i0 + j < k;
+            u[j] = ok[j] ? __ldcs(pairs + 2 * (i0 + j)) : 0;
+            v[j] = ok[j] ? __ldcs(pairs + 2 * (i0 + j) + 1) : 0;
         }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (ok[j] && (u[j] >= n || v[j] >= n)) { atomicOr(d.err, ERR_BAD_EDGE); ok[j] = false; }
+}
+
+// Insert(u, v) = Union(u, v) for every pair; four consecutive pairs per
+// thread step, their eight parent loads issued before any union.
+template <class E>
+__global__ void __launch_bounds__(256, 8) k_incr_insert(uint32_t *P, uint32_t n, const uint32_t *pairs, uint64_t k, Dev d) {
+    const bool vec = (reinterpret_cast<uintptr_t>(pairs) & 15) == 0;
+    const uint64_t groups = (k + 3) / 4;
+    for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < groups;
+         g += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t u[4], v[4], pu[4], pv[4];
+        bool ok[4];
+        load_pairs4(pairs, g, k, n, vec, u, v, ok, d);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             pu[j] = ok[j] ? ld_rel(P + u[j]) : 0;
@@ -96,19 +118,39 @@ __global__ void __launch_bounds__(256, 8) k_incr_shortcut(uint32_t *P, uint32_t 
 // IsConnected(u, v): Find(u) == Find(v) with the handle's find option.
 template <int FIND>
 __global__ void __launch_bounds__(256, 8) k_incr_query(uint32_t *P, uint32_t n, const uint32_t *pairs, uint64_t q, uint8_t *ans, Dev d) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < q;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t u = __ldcs(pairs + 2 * i), v = __ldcs(pairs + 2 * i + 1);
-        if (u >= n || v >= n) {
-            atomicOr(d.err, ERR_BAD_EDGE);
-            ans[i] = 0;
-            continue;
+    // four consecutive queries per thread step: pairs by two 16-byte loads,
+    // all eight parent loads in flight, answers written as one word when
+    // the answer array allows it
+    const bool vec = (reinterpret_cast<uintptr_t>(pairs) & 15) == 0;
+    const bool wvec = (reinterpret_cast<uintptr_t>(ans) & 3) == 0;
+    const uint64_t groups = (q + 3) / 4;
+    for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < groups;
+         g += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t u[4], v[4], pu[4], pv[4];
+        bool ok[4];
+        load_pairs4(pairs, g, q, n, vec, u, v, ok, d);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            pu[j] = ok[j] ? ld_rel(P + u[j]) : 0;
+            pv[j] = ok[j] ? ld_rel(P + v[j]) : 0;
         }
-        uint32_t pu = ld_rel(P + u), pv = ld_rel(P + v);
-        if (pu == pv) { ans[i] = 1; continue; }
-        uint32_t ru = find_from<FIND>(P, u, pu, d);
-        uint32_t rv = find_from<FIND>(P, v, pv, d);
-        ans[i] = ru == rv;
+        uint8_t a[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (!ok[j]) { a[j] = 0; continue; }
+            if (pu[j] == pv[j]) { a[j] = 1; continue; }
+            const uint32_t ru = find_from<FIND>(P, u[j], pu[j], d);
+            const uint32_t rv = find_from<FIND>(P, v[j], pv[j], d);
+            a[j] = ru == rv;
+        }
+        const uint64_t i0 = 4 * g;
+        if (wvec && i0 + 4 <= q) {
+            *reinterpret_cast<uchar4 *>(ans + i0) = make_uchar4(a[0], a[1], a[2], a[3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (i0 + j < q) ans[i0 + j] = a[j];
+        }
     }
 }
 
@@ -248,7 +290,7 @@ cc_status cc_incr_query_batch(cc_incr *h, const uint32_t *pairs, uint64_t q, uin
     if (!di) return CC_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const Dev d = make_dev(di, h->n);
-    const unsigned grid = grid_for(di, q, TPB);
+    const unsigned grid = grid_for(di, (q + 3) / 4, TPB);
     switch (h->fo.find) {
         case CC_FIND_SPLIT: { CC_PROF("k_incr_query", s); k_incr_query<FIND_SPLIT><<<grid, TPB, 0, s>>>(h->P, h->n, pairs, q, answers_out, d); } break;
         case CC_FIND_HALVE: { CC_PROF("k_incr_query", s); k_incr_query<FIND_HALVE><<<grid, TPB, 0, s>>>(h->P, h->n, pairs, q, answers_out, d); } break;

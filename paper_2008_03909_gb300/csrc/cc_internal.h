@@ -93,7 +93,13 @@ struct Ctl {
     uint32_t ldd_pull;                 // LDD: 1 while the rounds run bottom-up
     uint32_t ldd_push_nf;              // LDD: the frontier size the top-down kernels see (0 bottom-up)
     uint32_t ldd_done;                 // LDD: blocks of the frontier pass done (the last one decides)
-    uint32_t pad[10];
+    uint32_t guess;                    // k-out: sampled guess of L_max the fused binning used
+    uint32_t rebin;                    // 1 when the exact L_max differs from the guess
+    unsigned long long nonroots;       // k-out fused pass: vertices whose root is not themselves
+    unsigned long long steps;          // k-out fused pass: parent steps walked by its compression
+    uint32_t sel_class;                // selected path: the chosen class
+    uint32_t skip;                     // selected path: 1 when the default finish must not run
+    uint32_t pad[2];
 };
 
 // Launch accounting: one scope per kernel launch.  Counts every launch and,

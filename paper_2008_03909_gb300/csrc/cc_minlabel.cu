@@ -247,6 +247,7 @@ __global__ void __launch_bounds__(256, 8) k_pairs_at_positions(const OffT *I, co
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t c = warp; c < total; c += nwarps) {
         const ChunkRef cr = chunks[c];
+        if (cr.u == NONE) continue;   // an empty slot of a warp's reservation
         uint64_t b, e;
         vertex_range(I, cr.u, m, b, e, d);
         const uint64_t cb = b + (uint64_t)cr.c * CHUNK, ce = cb + CHUNK < e ? cb + CHUNK : e;

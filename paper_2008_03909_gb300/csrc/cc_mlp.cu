@@ -12,16 +12,15 @@
 // order, so a training step is deterministic.
 #include <cmath>
 
-#include "cc_internal.h"
+#include "cc_mlp.cuh"
 
 using namespace ccg;
 
 namespace {
 
-constexpr int IN = CC_MLP_IN, H = CC_MLP_HID, OUT = CC_MLP_OUT;
-constexpr int O_MU = 0, O_SIG = IN, O_W1 = 2 * IN, O_B1 = O_W1 + IN * H, O_W2 = O_B1 + H, O_B2 = O_W2 + H * H,
-              O_W3 = O_B2 + H, O_B3 = O_W3 + H * OUT, NP = O_B3 + OUT;
-static_assert(NP == CC_MLP_NPARAM, "parameter layout");
+constexpr int IN = MLP_IN, H = MLP_H, OUT = MLP_OUT;
+constexpr int O_MU = MLP_O_MU, O_SIG = MLP_O_SIG, O_W1 = MLP_O_W1, O_B1 = MLP_O_B1, O_W2 = MLP_O_W2,
+              O_B2 = MLP_O_B2, O_W3 = MLP_O_W3, O_B3 = MLP_O_B3, NP = MLP_NP;
 constexpr int O_TRAIN = O_W1;              // first trained parameter
 constexpr int NTRAIN = NP - O_TRAIN;
 
@@ -32,28 +31,10 @@ __global__ void k_mlp_forward(const float *__restrict__ p, const float *__restri
     const uint32_t s = blockIdx.x;
     if (s >= B) return;
     const int t = threadIdx.x;
-    if (t < IN) {
-        float sg = p[O_SIG + t];
-        sg = sg > 1e-6f ? sg : 1e-6f;
-        x[t] = (X[(size_t)s * IN + t] - p[O_MU + t]) / sg;
-    }
-    __syncthreads();
-    float a = p[O_B1 + t];
-    for (int i = 0; i < IN; ++i) a = fmaf(x[i], p[O_W1 + i * H + t], a);
-    h1[t] = a > 0.f ? a : 0.f;
-    __syncthreads();
-    a = p[O_B2 + t];
-    for (int i = 0; i < H; ++i) a = fmaf(h1[i], p[O_W2 + i * H + t], a);
-    h2[t] = a > 0.f ? a : 0.f;
-    __syncthreads();
+    mlp_forward_one(p, X + (size_t)s * IN, x, h1, h2, logits + (size_t)s * OUT);
     if (acts) {
         acts[(size_t)s * 2 * H + t] = h1[t];
         acts[(size_t)s * 2 * H + H + t] = h2[t];
-    }
-    if (t < OUT) {
-        a = p[O_B3 + t];
-        for (int i = 0; i < H; ++i) a = fmaf(h2[i], p[O_W3 + i * OUT + t], a);
-        logits[(size_t)s * OUT + t] = a;
     }
 }
 
@@ -202,11 +183,7 @@ __global__ void k_mlp_soft_targets(const float *times, uint32_t B, float tau, fl
 __global__ void k_mlp_argmax(const float *logits, uint32_t B, int32_t *cls) {
     const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= B) return;
-    const float *z = logits + (size_t)s * OUT;
-    int best = 0;
-    for (int k = 1; k < OUT; ++k)
-        if (z[k] > z[best]) best = k;
-    cls[s] = best;
+    cls[s] = mlp_argmax(logits + (size_t)s * OUT);
 }
 
 }  // namespace

@@ -13,11 +13,13 @@
 // by slots x slot_pairs x 17 bytes), and issues each piece of a request as
 // host->device copies (copy stream) -> insert and query kernels (compute
 // stream, ticket order) -> answers device->host (return stream).  Copies of
-// later requests overlap the kernels of earlier ones.  Requests whose host
-// buffers the device can address directly (pinned memory; over NVLink-C2C
-// on Grace-Blackwell) skip staging: their kernels read the pairs from host
-// memory and write the answers there.  A completion thread
-// waits on each request's last event in issue order and stamps its time.
+// later requests overlap the kernels of earlier ones, so the pipeline runs
+// at the slower of the host link and the kernels rather than their sum.
+// With CC_SERVER_ZERO_COPY, requests whose host buffers the device can
+// address directly (pinned memory; over NVLink-C2C on Grace-Blackwell) skip
+// staging instead: their kernels read the pairs from host memory and write
+// the answers there.  A completion thread waits on each request's last
+// event in issue order and stamps its time.
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -70,6 +72,7 @@ struct cc_server {
     cc_incr *h = nullptr;
     int device = 0;
     uint64_t cap = 0;
+    uint32_t flags = 0;
     cudaStream_t s_in = nullptr, s_comp = nullptr, s_out = nullptr;
     std::vector<Slot> slots;
     size_t next_slot = 0;
@@ -231,7 +234,7 @@ extern "C" {
 void cc_server_default_opt(cc_server_opt *o) {
     if (!o) return;
     o->slots = 4;
-    o->reserved = 0;
+    o->flags = 0;
     o->slot_pairs = 1ull << 22;
 }
 
@@ -241,7 +244,8 @@ cc_status cc_server_create(cc_incr *h, const cc_server_opt *opt, cc_server **out
     cc_server_opt o;
     cc_server_default_opt(&o);
     if (opt) o = *opt;
-    if (o.slots < 1 || o.slots > 64 || o.slot_pairs < 1 || o.slot_pairs > (1ull << 30) || o.reserved)
+    if (o.slots < 1 || o.slots > 64 || o.slot_pairs < 1 || o.slot_pairs > (1ull << 30) ||
+        (o.flags & ~CC_SERVER_ZERO_COPY))
         return CC_ERR_INVALID;
     const DeviceInfo *di = device_info();
     if (!di) return CC_ERR_CUDA;
@@ -249,6 +253,7 @@ cc_status cc_server_create(cc_incr *h, const cc_server_opt *opt, cc_server **out
     s->h = h;
     s->device = di->device;
     s->cap = o.slot_pairs;
+    s->flags = o.flags;
     s->slots.resize(o.slots);
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->s_in, cudaStreamNonBlocking);
@@ -278,7 +283,8 @@ cc_status cc_server_submit(cc_server *s, const uint32_t *inserts, uint64_t k, co
     if (!s || !ticket_out) return CC_ERR_INVALID;
     if ((k && !inserts) || (q && (!queries || !answers))) return CC_ERR_INVALID;
     auto r = std::make_shared<Request>();
-    r->direct = (k == 0 || device_view(inserts)) && (q == 0 || (device_view(queries) && device_view(answers)));
+    r->direct = (s->flags & CC_SERVER_ZERO_COPY) && (k == 0 || device_view(inserts)) &&
+                (q == 0 || (device_view(queries) && device_view(answers)));
     if (r->direct) {
         r->pieces.push_back(Piece{inserts, k, queries, q, answers});
     } else {

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "cc_internal.h"
+#include "cc_mlp.cuh"
 
 using namespace ccg;
 
@@ -53,7 +54,7 @@ __global__ void __launch_bounds__(256, 8) k_check_forest(uint32_t *P, uint32_t n
 // vertex also counts one for its root (IdentifyFrequent on flat labels, see
 // identify_phase).
 __device__ __forceinline__ void roots4(const uint32_t *P, uint32_t v0, uint32_t (&x)[4], uint32_t (&px)[4],
-                                       const Dev &d) {
+                                       const Dev &d, uint32_t *steps = nullptr) {
     bool act[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -70,6 +71,7 @@ __device__ __forceinline__ void roots4(const uint32_t *P, uint32_t v0, uint32_t 
             }
 #pragma unroll
         for (int j = 0; j < 4; ++j) act[j] = act[j] && px[j] != x[j];
+        if (steps) *steps += (uint32_t)act[0] + act[1] + act[2] + act[3];
         if (!g.step(d)) break;
     }
 }
@@ -79,12 +81,18 @@ __device__ __forceinline__ void roots4(const uint32_t *P, uint32_t v0, uint32_t 
 // key (count << 32 | ~label, the largest count with ties to the smallest
 // label) in *key, which must start at 0.
 template <bool COUNT>
+// zero (may be null, 16-byte aligned): an n-word array this pass also
+// clears (the count array of the next pass, cleared without a pass of its
+// own while this one waits on its parent walks).
 __global__ void __launch_bounds__(256, 8) k_shortcut(uint32_t *P, uint32_t *prev, uint32_t n, uint32_t *cnt,
-                                                     Dev d, unsigned long long *key = nullptr) {
+                                                     Dev d, unsigned long long *key = nullptr,
+                                                     const uint32_t *skip = nullptr, uint32_t *zero = nullptr) {
+    if (skip && *skip) return;   // the selected path chose another finish
     // 16-byte vector accesses only when both arrays are 16-byte aligned (a
     // caller's label buffer may be any 4-byte-aligned slice)
     const bool vec = (reinterpret_cast<uintptr_t>(P) & 15) == 0 &&
-                     (prev == nullptr || (reinterpret_cast<uintptr_t>(prev) & 15) == 0);
+                     (prev == nullptr || (reinterpret_cast<uintptr_t>(prev) & 15) == 0) &&
+                     (zero == nullptr || (reinterpret_cast<uintptr_t>(zero) & 15) == 0);
     const uint64_t n4 = vec ? n / 4 : 0;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
@@ -97,6 +105,7 @@ __global__ void __launch_bounds__(256, 8) k_shortcut(uint32_t *P, uint32_t *prev
         uint4 r = make_uint4(x[0], x[1], x[2], x[3]);
         if (r.x != p.x || r.y != p.y || r.z != p.z || r.w != p.w) __stcg(reinterpret_cast<uint4 *>(P) + i, r);
         if (prev) __stcg(reinterpret_cast<uint4 *>(prev) + i, r);
+        if (zero) __stcg(reinterpret_cast<uint4 *>(zero) + i, make_uint4(0, 0, 0, 0));
         if (COUNT) {
 #pragma unroll
             for (int j = 0; j < 4; ++j)
@@ -108,10 +117,57 @@ __global__ void __launch_bounds__(256, 8) k_shortcut(uint32_t *P, uint32_t *prev
         uint32_t r = find_from<FIND_NAIVE>(P, (uint32_t)v, p, d);
         if (r != p) P[v] = r;
         if (prev) prev[v] = r;
+        if (zero) zero[v] = 0;
         if (COUNT && r != v) lc.add(cnt, r);
     }
     if (COUNT) lc.flush(cnt, key);
 }
+
+// ---------------------------------------------------------------- degree statistics
+// Degree statistics of the graph for the selector's features, gathered by
+// a pass that reads every vertex's offsets anyway (the first k-out pass, or
+// a pass of their own): sum and sum of squares of the degrees, counts of
+// degree 0, 1, 2, 3..16 and > 64, the edges at vertices of degree > 64, and
+// the highest degree (key deg << 32 | ~v: ties to the smallest vertex).
+struct FeatStats {
+    unsigned long long sum_deg, cnt[5], edges_gt64, maxkey;
+    double sum_deg2;
+};
+
+struct DegStats {
+    unsigned long long sd = 0, sd2 = 0, c0 = 0, c1 = 0, c2 = 0, c3 = 0, c4 = 0, e64 = 0, mk = 0;
+    __device__ __forceinline__ void add(uint64_t deg, uint32_t v) {
+        sd += deg;
+        sd2 += deg * deg;
+        c0 += deg == 0;
+        c1 += deg == 1;
+        c2 += deg == 2;
+        c3 += deg >= 3 && deg <= 16;
+        c4 += deg > 64;
+        if (deg > 64) e64 += deg;
+        const unsigned long long key = ((deg < 0xFFFFFFFFull ? deg : 0xFFFFFFFFull) << 32) | (uint32_t)~v;
+        mk = key > mk ? key : mk;
+    }
+    // every lane of the warp calls this; one set of atomics per warp
+    __device__ __forceinline__ void flush(FeatStats *st) {
+        unsigned long long c[5] = {c0, c1, c2, c3, c4};
+        for (int o = 16; o > 0; o >>= 1) {
+            sd += __shfl_xor_sync(0xFFFFFFFFu, sd, o);
+            sd2 += __shfl_xor_sync(0xFFFFFFFFu, sd2, o);
+            e64 += __shfl_xor_sync(0xFFFFFFFFu, e64, o);
+            for (int j = 0; j < 5; ++j) c[j] += __shfl_xor_sync(0xFFFFFFFFu, c[j], o);
+            const unsigned long long y = __shfl_xor_sync(0xFFFFFFFFu, mk, o);
+            mk = y > mk ? y : mk;
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(&st->sum_deg, sd);
+            atomicAdd(&st->sum_deg2, (double)sd2);
+            atomicAdd(&st->edges_gt64, e64);
+            for (int j = 0; j < 5; ++j) atomicAdd(&st->cnt[j], c[j]);
+            atomicMax(&st->maxkey, mk);
+        }
+    }
+};
 
 // ---------------------------------------------------------------- k-out
 // Algorithm 4: each vertex of degree > 0 picks its first edge and k-1
@@ -188,11 +244,15 @@ void launch_kout(unsigned grid, cudaStream_t s, const OffT *I, const uint32_t *A
 // serialised (about 2 ns each, 0.5M of them at RMAT-26: most of the
 // kernel's time).  A block's warp steps hold at most cap_blk vertices, so
 // its region cannot overflow (checked, flagged).
-template <typename OffT>
+// STATS: also gather the degree statistics into *fs (the selector's
+// features; the offsets are read here anyway).
+template <typename OffT, bool STATS = false>
 __global__ void __launch_bounds__(256, 8) k_kout_hook_first(const OffT *I, const uint32_t *A, uint32_t n,
                                                             uint64_t m, uint32_t *P, uint2 *defer,
                                                             uint32_t *dcount, uint32_t cap_blk, uint32_t *pick1,
-                                                            uint32_t k, uint32_t rule, uint64_t seed, Dev d) {
+                                                            uint32_t k, uint32_t rule, uint64_t seed, uint32_t *nz,
+                                                            Dev d, FeatStats *fs = nullptr) {
+    DegStats ds;
     __shared__ uint32_t nblk;
     if (threadIdx.x == 0) nblk = 0;
     __syncthreads();
@@ -229,6 +289,12 @@ __global__ void __launch_bounds__(256, 8) k_kout_hook_first(const OffT *I, const
             const uint64_t v = base + 32 * j + lane;
             uint64_t b = 0, e = 0;
             if (v < n) clamp_range(beg[j], end[j], m, b, e, d);
+            // nz (optional): bit v set iff v has an edge, one word per 32
+            // consecutive vertices (the later binning skips isolated vertices
+            // without reading their offsets)
+            const unsigned has = __ballot_sync(0xFFFFFFFFu, e > b);
+            if (nz && lane == 0 && base + 32 * j < n) nz[(base >> 5) + j] = has;
+            if (STATS && v < n) ds.add(e - b, (uint32_t)v);
             // pick 0 (the first edge, or a uniform pick under the pure rule)
             w[j] = e > b ? ld_stream(A + b + kout_offset(rule, seed, v, k, 0, e - b)) : NONE;
             // with k = 2 pick 1 is read here too and kept for the second
@@ -263,6 +329,7 @@ __global__ void __launch_bounds__(256, 8) k_kout_hook_first(const OffT *I, const
                 ++slot;
             }
     }
+    if (STATS) ds.flush(fs);
     __syncthreads();
     if (threadIdx.x == 0) dcount[blockIdx.x] = nblk < cap_blk ? nblk : cap_blk;
 }
@@ -286,18 +353,15 @@ k_kout_defer(uint32_t n, uint32_t *P, const uint2 *defer, const uint32_t *dcount
 }
 
 // Second round for k = 2: Union(v, pick1[v]) from the stash written in the
-// first pass (coalesced reads of the stash and of P[v]).  The trees of the
-// first round are not compressed first: the union's finds walk them (with
-// the engine's splicing), which costs less than a full compression pass
-// because first-edge chains are short (a vertex's first neighbour is its
-// smallest).  The stash is dead after its read, so it is zeroed on the way
-// and serves next as the label-count array.
+// first pass (coalesced reads of the stash and of P[v]).  (Zeroing the
+// stash here, to reuse it as the count array, made this kernel 12x slower:
+// 2.93 against 0.24 ms at R-MAT scale 26; the count array is cleared by the
+// mid-round compression instead.)
 template <class E>
-__global__ void __launch_bounds__(256, 8) k_kout_apply_pick(uint32_t *pick1, uint32_t n, uint32_t *P, Dev d) {
+__global__ void __launch_bounds__(256, 8) k_kout_apply_pick(const uint32_t *pick1, uint32_t n, uint32_t *P, Dev d) {
     for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
          v += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t w = pick1[v];
-        pick1[v] = 0;
         uint32_t u1[1] = {(uint32_t)v}, w1[1] = {w};
         bool ok[1] = {w != NONE};
         unite_pairs<E, 1>(P, u1, w1, ok, d);
@@ -409,6 +473,261 @@ __global__ void k_freq_sampled(const uint32_t *L, uint32_t n, uint32_t S, uint64
     }
 }
 
+// ---------------------------------------------------------------- fused k-out binning
+// A guess of L_max before the exact count: the most frequent root among 256
+// seeded vertices that have an edge (ties to the smallest root), each root
+// found by walking the not yet compressed forest (at most 64 steps; a walk
+// that stops early just gives a worse guess).  One block of 256 threads.
+// The guess only decides which vertices the fused binning treats as
+// candidates; the exact L_max is checked against it afterwards.
+constexpr uint64_t TAG_GUESS = 0x67756573ull;
+__global__ void __launch_bounds__(256) k_guess_lmax(const uint32_t *P, const uint32_t *nz, uint32_t n, uint64_t seed,
+                                                    Ctl *ctl) {
+    // the fused pass appends and counts from zero
+    if (threadIdx.x == 0) {
+        ctl->nlight = 0;
+        ctl->nchunks = 0;
+        ctl->edges = 0;
+        ctl->key = 0;
+        ctl->rebin = 0;
+        ctl->nonroots = 0;
+        ctl->steps = 0;
+    }
+    __shared__ uint32_t lab[256];
+    __shared__ unsigned long long red[8];
+    const uint32_t t = threadIdx.x;
+    const uint32_t v = (uint32_t)(draw64(seed ^ TAG_GUESS, t) % n);
+    uint32_t r = NONE;
+    if ((nz[v >> 5] >> (v & 31)) & 1u) {
+        r = v;
+        for (int step = 0; step < 64; ++step) {
+            const uint32_t p = ld_rel(P + r);
+            if (p == r || p >= n) break;
+            r = p;
+        }
+    }
+    lab[t] = r;
+    __syncthreads();
+    unsigned long long best = 0;
+    if (r != NONE) {
+        uint32_t c = 0;
+        for (int j = 0; j < 256; ++j) c += lab[j] == r;
+        best = ((unsigned long long)c << 32) | (uint32_t)~r;
+    }
+    best = warp_max_u64(best);
+    if ((t & 31) == 0) red[t >> 5] = best;
+    __syncthreads();
+    if (t == 0) {
+        for (int w = 1; w < 8; ++w) best = red[w] > best ? red[w] : best;
+        best = best > red[0] ? best : red[0];
+        ctl->guess = best ? ~(uint32_t)(best & 0xFFFFFFFFull) : NONE;
+    }
+}
+
+// The k-out sampling's last full compression, fused with IdentifyFrequent's
+// count (non-roots counted into cnt, the arg-max key left in ctl->key) and
+// with the finish's candidate binning (Algorithm 7's filter) against the
+// guessed L_max: a vertex whose root differs from the guess and that has an
+// edge (nz bit) is binned, light (degree <= LIGHT_MAX) to the light list,
+// heavier as chunks.  Only candidates read offsets, so on a graph with a
+// giant cluster this pass replaces the binning pass's read of every offset
+// and label.  When the exact L_max differs from the guess (k_lmax_check)
+// the lists are rebuilt by k_cand_bin.
+template <typename OffT>
+__global__ void __launch_bounds__(256, 6) k_compress_count_bin(uint32_t *P, uint32_t n, uint32_t *cnt, const OffT *I,
+                                                               uint64_t m, const uint32_t *nz, Ctl *ctl,
+                                                               uint32_t *light, ChunkRef *chunks, uint64_t cap,
+                                                               Dev d) {
+    const bool vec = (reinterpret_cast<uintptr_t>(P) & 15) == 0;
+    const uint64_t n4 = vec ? n / 4 : 0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const uint32_t guess = ctl->guess;
+    const int lane = threadIdx.x & 31;
+    LabelCounterArg lc;
+    WarpSlots ws;
+    unsigned long long my_edges = 0, my_nonroots = 0;
+    uint32_t my_steps = 0;
+    // whole warps iterate together (the binning's appends are warp-collective)
+    const uint64_t n4w = (n4 + 31) / 32 * 32;
+    for (uint64_t i = tid; i < n4w; i += stride) {
+        const bool act = i < n4;
+        uint32_t x[4], px[4];
+        const uint32_t v0 = (uint32_t)(4 * i);
+        uint32_t nc[4] = {0, 0, 0, 0}, isl[4] = {0, 0, 0, 0};
+        if (act) {
+            uint4 p = __ldcg(reinterpret_cast<const uint4 *>(P) + i);
+            px[0] = p.x; px[1] = p.y; px[2] = p.z; px[3] = p.w;
+            roots4(P, v0, x, px, d, &my_steps);
+            uint4 r = make_uint4(x[0], x[1], x[2], x[3]);
+            if (r.x != p.x || r.y != p.y || r.z != p.z || r.w != p.w) __stcg(reinterpret_cast<uint4 *>(P) + i, r);
+            const uint32_t bits = (nz[v0 >> 5] >> (v0 & 31)) & 15u;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (x[j] != v0 + j) {
+                    lc.add(cnt, x[j]);
+                    ++my_nonroots;
+                }
+                if (x[j] != guess && ((bits >> j) & 1u)) {
+                    uint64_t b, e;
+                    vertex_range(I, v0 + j, m, b, e, d);
+                    const uint64_t deg = e - b;
+                    my_edges += deg;
+                    isl[j] = deg > 0 && deg <= LIGHT_MAX;
+                    nc[j] = deg > LIGHT_MAX ? (uint32_t)((deg + CHUNK - 1) / CHUNK) : 0;
+                }
+            }
+        }
+        const uint32_t nls = isl[0] + isl[1] + isl[2] + isl[3], ncs = nc[0] + nc[1] + nc[2] + nc[3];
+        // most warp steps of a graph with a giant cluster have no candidate
+        if (!__any_sync(0xFFFFFFFFu, nls | ncs)) continue;   // warp-uniform
+        uint32_t sl = warp_append_full(&ctl->nlight, nls);
+        uint32_t incl = ncs;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const uint32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        uint64_t sc = tot ? ws.take(&ctl->nchunks, tot, chunks, cap) + incl - ncs : 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (isl[j]) light[sl++] = v0 + j;
+            if (nc[j]) {
+                if (sc + nc[j] > cap) atomicOr(d.err, ERR_NONCONVERGED);
+                else
+                    for (uint32_t c = 0; c < nc[j]; ++c) chunks[sc + c] = ChunkRef{v0 + j, c};
+                sc += nc[j];
+            }
+        }
+    }
+    // the last n % 4 vertices (all of them when P is not 16-byte aligned),
+    // one per thread: single appends
+    for (uint64_t v = 4 * n4 + tid; v < n; v += stride) {
+        uint32_t p = ld_rel(P + v);
+        uint32_t r = find_from<FIND_NAIVE>(P, (uint32_t)v, p, d);
+        if (r != p) P[v] = r;
+        if (r != v) {
+            lc.add(cnt, r);
+            ++my_nonroots;
+        }
+        if (r != guess && ((nz[v >> 5] >> (v & 31)) & 1u)) {
+            uint64_t b, e;
+            vertex_range(I, (uint32_t)v, m, b, e, d);
+            const uint64_t deg = e - b;
+            my_edges += deg;
+            if (deg > 0 && deg <= LIGHT_MAX) {
+                light[atomicAdd(&ctl->nlight, 1u)] = (uint32_t)v;
+            } else if (deg > LIGHT_MAX) {
+                const uint32_t ncv = (uint32_t)((deg + CHUNK - 1) / CHUNK);
+                const uint64_t sc = atomicAdd(&ctl->nchunks, ncv);
+                if (sc + ncv > cap) atomicOr(d.err, ERR_NONCONVERGED);
+                else
+                    for (uint32_t c = 0; c < ncv; ++c) chunks[sc + c] = ChunkRef{(uint32_t)v, c};
+            }
+        }
+    }
+    ws.close(chunks, cap);
+    lc.flush(cnt, &ctl->key);
+    unsigned long long my_st = my_steps;
+    for (int o = 16; o > 0; o >>= 1) {
+        my_edges += __shfl_xor_sync(0xFFFFFFFFu, my_edges, o);
+        my_nonroots += __shfl_xor_sync(0xFFFFFFFFu, my_nonroots, o);
+        my_st += __shfl_xor_sync(0xFFFFFFFFu, my_st, o);
+    }
+    if (lane == 0) {
+        if (my_edges) atomicAdd(&ctl->edges, my_edges);
+        if (my_nonroots) atomicAdd(&ctl->nonroots, my_nonroots);
+        if (my_st) atomicAdd(&ctl->steps, my_st);
+    }
+}
+
+// L_max from the arg-max key; when it is not the guess the fused binning
+// used, the lists are cleared and rebin is set (k_cand_bin then rebuilds
+// them against the exact L_max).
+__global__ void k_lmax_check(Ctl *ctl, uint32_t *lmax) {
+    const unsigned long long k = ctl->key;
+    const uint32_t l = k ? ~(uint32_t)(k & 0xFFFFFFFFull) : 0u;
+    *lmax = l;
+    const bool re = l != ctl->guess;
+    ctl->rebin = re;
+    if (re) {
+        ctl->nlight = 0;
+        ctl->nchunks = 0;
+        ctl->edges = 0;
+    }
+}
+
+// The selector's choice inside the default path (k-out + UF-Rem-CAS): the
+// L_max check of k_lmax_check, then the 16 features from what the default
+// path already computed, then the MLP's class, all in one block of 64
+// threads.  Features (floats): 0 log2(n+1), 1 log2(m+1), 2 m/n, 3
+// log2(max degree+1), 4 degree variance / mean^2, 5-7 fractions of vertices
+// of degree 0, 1, 2, 8 fraction of degree 3..16, 9 fraction of degree > 64,
+// 10 share of edges at vertices of degree > 64, 11 size of L_max's k-out
+// cluster / n, 12 vertices outside their own singleton after k-out / n, 13
+// edges left for the finish / m, 14 light candidate vertices of the finish
+// / n, 15 parent steps per non-root in the last compression (how deep the
+// k-out trees were, a cheap stand-in for the graph's depth).  params null:
+// features only, class 0 (the default).  force >= 0 overrides the class.
+// The class goes to ctl->sel_class and, with rebin in bit 8, to *host_word
+// (mapped host memory, may be null); ctl->skip = class != 0.
+__global__ void __launch_bounds__(64) k_lmax_select(Ctl *ctl, uint32_t *lmax, const FeatStats *fs, uint32_t n,
+                                                    uint64_t m, const float *params, int force, float *feat_out,
+                                                    volatile int *host_word) {
+    __shared__ float xin[MLP_IN], x[MLP_IN], h1[MLP_H], h2[MLP_H], z[MLP_OUT];
+    __shared__ uint32_t re_s;
+    const int t = threadIdx.x;
+    if (t == 0) {
+        const unsigned long long k = ctl->key;
+        const uint32_t l = k ? ~(uint32_t)(k & 0xFFFFFFFFull) : 0u;
+        *lmax = l;
+        const double nn = (double)n, mm = m ? (double)m : 1.0;
+        const double mean = (double)fs->sum_deg / nn;
+        const double var = fs->sum_deg2 / nn - mean * mean;
+        const double nonroots = (double)ctl->nonroots;
+        xin[0] = (float)log2(nn + 1.0);
+        xin[1] = (float)log2((double)m + 1.0);
+        xin[2] = (float)mean;
+        xin[3] = (float)log2((double)(fs->maxkey >> 32) + 1.0);
+        xin[4] = (float)(mean > 0 ? var / (mean * mean) : 0.0);
+        for (int j = 0; j < 3; ++j) xin[5 + j] = (float)(fs->cnt[j] / nn);
+        xin[8] = (float)(fs->cnt[3] / nn);
+        xin[9] = (float)(fs->cnt[4] / nn);
+        xin[10] = (float)(fs->edges_gt64 / mm);
+        xin[11] = (float)(((double)(k >> 32) + 1.0) / nn);
+        xin[12] = (float)(nonroots / nn);
+        xin[13] = (float)((double)ctl->edges / mm);
+        xin[14] = (float)((double)ctl->nlight / nn);
+        xin[15] = (float)((double)ctl->steps / (nonroots > 1.0 ? nonroots : 1.0));
+        const bool re = l != ctl->guess;
+        ctl->rebin = re;
+        re_s = re;
+        if (re) {
+            ctl->nlight = 0;
+            ctl->nchunks = 0;
+            ctl->edges = 0;
+        }
+    }
+    __syncthreads();
+    if (feat_out && t < MLP_IN) feat_out[t] = xin[t];
+    int cls = 0;
+    if (params) {
+        mlp_forward_one(params, xin, x, h1, h2, z);
+        __syncthreads();
+        cls = mlp_argmax(z);
+    }
+    if (force >= 0) cls = force;
+    if (t == 0) {
+        ctl->sel_class = (uint32_t)cls;
+        ctl->skip = cls != 0;
+        if (host_word) {
+            *host_word = cls | ((int)re_s << 8);
+            __threadfence_system();
+        }
+    }
+}
+
 // ---------------------------------------------------------------- edge passes
 // Edge pass over a vertex range (union-find finish with nothing skipped, or
 // a skip test on P[u] == L_max): light vertices run in the calling thread;
@@ -422,6 +741,7 @@ __global__ void __launch_bounds__(256, 8) k_range_bin(const OffT *I, const uint3
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint32_t lmax = lmax_p ? *lmax_p : NONE;
     unsigned long long my_edges = 0;
+    WarpSlots ws;
     for (uint64_t base = warp * 32; base < n; base += nw * 32) {
         uint32_t u = (uint32_t)(base + lane);
         bool act = base + lane < n;
@@ -431,10 +751,10 @@ __global__ void __launch_bounds__(256, 8) k_range_bin(const OffT *I, const uint3
         uint64_t deg = e - b;
         my_edges += deg;
         uint32_t nc = deg > LIGHT_MAX ? (uint32_t)((deg + CHUNK - 1) / CHUNK) : 0;
-        uint32_t slot = warp_append_full(nchunks, nc);
-        if (nc) write_chunks(chunks, cap, slot, nc, u, d);
+        warp_bin_chunks(ws, nchunks, chunks, cap, nc, u, d);
         warp_light_edges(u, b, nc ? 0u : (uint32_t)deg, A, n, f, d);
     }
+    ws.close(chunks, cap);
     f.flush();
     for (int o = 16; o > 0; o >>= 1) my_edges += __shfl_xor_sync(0xFFFFFFFFu, my_edges, o);
     if (lane == 0 && edges && my_edges) atomicAdd(edges, my_edges);
@@ -442,7 +762,8 @@ __global__ void __launch_bounds__(256, 8) k_range_bin(const OffT *I, const uint3
 
 template <typename OffT, class F>
 __global__ void __launch_bounds__(256, 8) k_chunks(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, const ChunkRef *chunks,
-                         const uint32_t *nchunks, uint64_t cap, F f, Dev d) {
+                         const uint32_t *nchunks, uint64_t cap, F f, Dev d, const uint32_t *skip = nullptr) {
+    if (skip && *skip) return;
     run_chunks(I, A, n, m, chunks, nchunks, cap, f, d);
     f.flush();
 }
@@ -457,6 +778,7 @@ __global__ void __launch_bounds__(256, 8) k_list_bin(const OffT *I, const uint32
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint32_t total = *count;
+    WarpSlots ws;
     for (uint64_t base = warp * 32; base < total; base += nw * 32) {
         bool act = base + lane < total;
         uint32_t u = act ? list[base + lane] : 0;
@@ -464,10 +786,10 @@ __global__ void __launch_bounds__(256, 8) k_list_bin(const OffT *I, const uint32
         if (act) vertex_range(I, u, m, b, e, d);
         uint64_t deg = e - b;
         uint32_t nc = deg > LIGHT_MAX ? (uint32_t)((deg + CHUNK - 1) / CHUNK) : 0;
-        uint32_t slot = warp_append_full(nchunks, nc);
-        if (nc) write_chunks(chunks, cap, slot, nc, u, d);
+        warp_bin_chunks(ws, nchunks, chunks, cap, nc, u, d);
         warp_light_edges(u, b, nc ? 0u : (uint32_t)deg, A, n, f, d);
     }
+    ws.close(chunks, cap);
     f.flush();
 }
 
@@ -477,12 +799,18 @@ __global__ void __launch_bounds__(256, 8) k_list_bin(const OffT *I, const uint32
 template <typename OffT>
 __global__ void __launch_bounds__(256, 8) k_cand_bin(const OffT *I, uint32_t n, uint64_t m, const uint32_t *P, const uint32_t *lmax_p,
                            uint32_t *light, uint32_t *nlight, ChunkRef *chunks, uint32_t *nchunks, uint64_t cap,
-                           unsigned long long *edges, Dev d) {
+                           unsigned long long *edges, Dev d, const uint32_t *only_if = nullptr,
+                           const uint32_t *skip = nullptr) {
+    // only_if: the lists were built by the fused k-out pass; rebuild them
+    // only when that pass's L_max guess was wrong.  skip: the selected path
+    // chose another finish (which rebuilds them itself if needed)
+    if ((only_if && *only_if == 0) || (skip && *skip)) return;
     const int lane = threadIdx.x & 31;
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint32_t lmax = lmax_p ? *lmax_p : NONE;
     unsigned long long my_edges = 0;
+    WarpSlots ws;
     // a warp step covers 128 vertices, four per lane, read with vector loads
     for (uint64_t base = warp * 128; base < n; base += nw * 128) {
         const uint64_t v0 = base + 4 * lane;
@@ -505,23 +833,35 @@ __global__ void __launch_bounds__(256, 8) k_cand_bin(const OffT *I, uint32_t n, 
             ncs += nc[j];
         }
         uint32_t sl = warp_append_full(nlight, nl);
-        uint32_t sc = warp_append_full(nchunks, ncs);
+        // the lane's chunks, in vertex order, from the warp's reservation
+        uint32_t incl = ncs;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const uint32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        uint64_t sc = tot ? ws.take(nchunks, tot, chunks, cap) + incl - ncs : 0;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             if (bb[j] > 0 && bb[j] <= LIGHT_MAX) light[sl++] = (uint32_t)(v0 + j);
             if (nc[j]) {
-                write_chunks(chunks, cap, sc, nc[j], (uint32_t)(v0 + j), d);
+                if (sc + nc[j] > cap) atomicOr(d.err, ERR_NONCONVERGED);
+                else
+                    for (uint32_t c = 0; c < nc[j]; ++c) chunks[sc + c] = ChunkRef{(uint32_t)(v0 + j), c};
                 sc += nc[j];
             }
         }
     }
+    ws.close(chunks, cap);
     for (int o = 16; o > 0; o >>= 1) my_edges += __shfl_xor_sync(0xFFFFFFFFu, my_edges, o);
     if (lane == 0 && edges && my_edges) atomicAdd(edges, my_edges);
 }
 
 template <typename OffT, class F>
 __global__ void __launch_bounds__(256, 8) k_light_list(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, const uint32_t *list,
-                             const uint32_t *count, F f, Dev d) {
+                             const uint32_t *count, F f, Dev d, const uint32_t *skip = nullptr) {
+    if (skip && *skip) return;
     const int lane = threadIdx.x & 31;
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -1089,6 +1429,7 @@ __global__ void __launch_bounds__(256, 8) k_ldd_bin(const OffT *I, const uint32_
     const int lane = threadIdx.x & 31;
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    WarpSlots ws;
     if (!ctl->ldd_pull) {
         const uint32_t total = ctl->ldd_push_nf;
         for (uint64_t base = warp * 32; base < total; base += nw * 32) {
@@ -1098,10 +1439,10 @@ __global__ void __launch_bounds__(256, 8) k_ldd_bin(const OffT *I, const uint32_
             if (act) vertex_range(I, u, m, b, e, d);
             const uint64_t deg = e - b;
             const uint32_t nc = deg > LIGHT_MAX ? (uint32_t)((deg + CHUNK - 1) / CHUNK) : 0;
-            const uint32_t slot = warp_append_full(nchunks, nc);
-            if (nc) write_chunks(chunks, cap, slot, nc, u, d);
+            warp_bin_chunks(ws, nchunks, chunks, cap, nc, u, d);
             warp_light_edges(u, b, nc ? 0u : (uint32_t)deg, A, n, fpush, d);
         }
+        ws.close(chunks, cap);
         return;
     }
     for (uint64_t base = warp * 32; base < n; base += nw * 32) {
@@ -1112,10 +1453,10 @@ __global__ void __launch_bounds__(256, 8) k_ldd_bin(const OffT *I, const uint32_
         if (w < n && !((vword >> lane) & 1u)) vertex_range(I, (uint32_t)w, m, b, e, d);
         const uint64_t deg = e - b;
         const uint32_t nc = deg > LIGHT_MAX ? (uint32_t)((deg + CHUNK - 1) / CHUNK) : 0;
-        const uint32_t slot = warp_append_full(nchunks, nc);
-        if (nc) write_chunks(chunks, cap, slot, nc, (uint32_t)w, d);
+        warp_bin_chunks(ws, nchunks, chunks, cap, nc, (uint32_t)w, d);
         warp_light_edges((uint32_t)w, b, nc ? 0u : (uint32_t)deg, A, n, fpull, d);
     }
+    ws.close(chunks, cap);
 }
 
 template <typename OffT>
@@ -1178,82 +1519,6 @@ __global__ void __launch_bounds__(256, 8) k_apply_cluster_min(uint32_t *P, uint3
         P[i] = cmin[P[i]];
 }
 
-// ---------------------------------------------------------------- selector features
-struct FeatStats {
-    unsigned long long sum_deg, cnt[5], edges_gt64, maxkey;   // maxkey = deg << 32 | ~v
-    double sum_deg2;
-    unsigned long long roots, lmax_count, edges_nonlmax;
-};
-
-// Degree statistics in one pass over the offsets.
-template <typename OffT>
-__global__ void __launch_bounds__(256, 8) k_degree_stats(const OffT *I, uint32_t n, uint64_t m, FeatStats *st, Dev d) {
-    unsigned long long sd = 0, c[5] = {0, 0, 0, 0, 0}, e64 = 0, mk = 0;
-    double sd2 = 0;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        uint64_t b, e;
-        vertex_range(I, (uint32_t)i, m, b, e, d);
-        const uint64_t deg = e - b;
-        sd += deg;
-        sd2 += (double)deg * (double)deg;
-        c[0] += deg == 0;
-        c[1] += deg == 1;
-        c[2] += deg == 2;
-        c[3] += deg >= 3 && deg <= 16;
-        c[4] += deg > 64;
-        if (deg > 64) e64 += deg;
-        const unsigned long long key = ((deg < 0xFFFFFFFFull ? deg : 0xFFFFFFFFull) << 32) | (uint32_t)~(uint32_t)i;
-        mk = key > mk ? key : mk;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        sd += __shfl_xor_sync(0xFFFFFFFFu, sd, o);
-        sd2 += __shfl_xor_sync(0xFFFFFFFFu, sd2, o);
-        e64 += __shfl_xor_sync(0xFFFFFFFFu, e64, o);
-        for (int j = 0; j < 5; ++j) c[j] += __shfl_xor_sync(0xFFFFFFFFu, c[j], o);
-        unsigned long long y = __shfl_xor_sync(0xFFFFFFFFu, mk, o);
-        mk = y > mk ? y : mk;
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&st->sum_deg, sd);
-        atomicAdd(&st->sum_deg2, sd2);
-        atomicAdd(&st->edges_gt64, e64);
-        for (int j = 0; j < 5; ++j) atomicAdd(&st->cnt[j], c[j]);
-        atomicMax(&st->maxkey, mk);
-    }
-}
-
-// On flat sampled labels: roots (= sampled components), the size of L_max's
-// cluster, and the edges out of vertices outside it (left for the finish).
-template <typename OffT>
-__global__ void __launch_bounds__(256, 8) k_label_stats(const OffT *I, uint32_t n, uint64_t m, const uint32_t *P,
-                                                         const uint32_t *lmax_p, FeatStats *st, Dev d) {
-    const uint32_t lmax = *lmax_p;
-    unsigned long long r = 0, c = 0, e = 0;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t l = P[i];
-        r += l == i;
-        if (l == lmax) {
-            ++c;
-        } else {
-            uint64_t b, t;
-            vertex_range(I, (uint32_t)i, m, b, t, d);
-            e += t - b;
-        }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        r += __shfl_xor_sync(0xFFFFFFFFu, r, o);
-        c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
-        e += __shfl_xor_sync(0xFFFFFFFFu, e, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&st->roots, r);
-        atomicAdd(&st->lmax_count, c);
-        atomicAdd(&st->edges_nonlmax, e);
-    }
-}
-
 // ================================================================ host side
 struct Graph {
     const void *I;
@@ -1272,6 +1537,19 @@ struct Work {
            o_hooks = 0;
     bool has_hooks = false;
     bool has_counts = false, has_sv = false, has_bfs = false, has_ldd = false;
+    // k-out with a finish: the nonzero-degree bitmap, and whether the fused
+    // compression already built the finish's candidate lists
+    bool has_nz = false, lists_built = false;
+    size_t o_nz = 0;
+    // the selected path: degree statistics gathered by the first k-out pass
+    // and the choice made where L_max is checked (k_lmax_select)
+    FeatStats *fs = nullptr;
+    bool select = false;
+    const float *sel_params = nullptr;
+    int sel_force = -1;
+    float *sel_feat = nullptr;
+    volatile int *sel_host = nullptr;
+    uint64_t sel_m = 0;
     uint64_t chunk_cap = 0;
     Ctl *ctl() const { return sc.at<Ctl>(o_ctl); }
 };
@@ -1292,7 +1570,7 @@ void plan(Work &w, const Graph &g, int sample_kind, uint32_t freq_samples, int f
         if (sample_kind == CC_SAMPLE_LDD) w.o_stamp = w.sc.reserve(n * 4);
     }
     w.o_ctl = w.sc.reserve(sizeof(Ctl));
-    w.chunk_cap = chunk_capacity(n, g.m);
+    w.chunk_cap = chunk_capacity(n, g.m) + CHUNK_SLACK;
     w.o_chunks = w.sc.reserve(w.chunk_cap * sizeof(ChunkRef));
     if (sample_kind == CC_SAMPLE_KOUT) {
         // per-block regions of the first-edge queue: n pairs plus one warp
@@ -1306,6 +1584,10 @@ void plan(Work &w, const Graph &g, int sample_kind, uint32_t freq_samples, int f
         w.o_counts = w.sc.reserve(n * 4);
     }
     if (finish_phase) w.o_light = w.sc.reserve(n * 4);
+    if (finish_phase && sample_kind == CC_SAMPLE_KOUT && freq_samples == 0) {
+        w.has_nz = true;
+        w.o_nz = w.sc.reserve(((n + 31) / 32 + 4) * 4);
+    }
     if (finish_phase && (finish_kind == CC_FINISH_SV || finish_kind == CC_FINISH_LT_PRF)) {
         w.has_sv = true;
         w.o_prev = w.sc.reserve(n * 4);
@@ -1723,33 +2005,58 @@ cc_status sample_phase(const Graph &g, const cc_sample_opt &so, const cc_finish_
         if (gv > KOUT_MAX_BLOCKS || (uint64_t)gv * cap_blk > kout_defer_entries(g.n) || cap_blk > 0xFFFFFFFFull)
             return CC_ERR_INVALID;   // not reached: grids have at most 8 blocks per SM
         uint32_t *pick1 = so.k == 2 ? w.sc.at<uint32_t>(w.o_pick) : nullptr;
+        // the fused binning (k = 2, exact IdentifyFrequent, a finish to follow)
+        const bool fuse = count_into && pick1 && w.has_nz;
+        uint32_t *nz = fuse ? w.sc.at<uint32_t>(w.o_nz) : nullptr;
         {
             CC_PROF("k_kout_hook_first", s);
-            k_kout_hook_first<OffT><<<gv, TPB, 0, s>>>(I, g.A, g.n, g.m, P, defer, dcount, (uint32_t)cap_blk, pick1,
-                                                       so.k, so.kout_rule, so.seed, d);
+            if (w.fs)
+                k_kout_hook_first<OffT, true><<<gv, TPB, 0, s>>>(I, g.A, g.n, g.m, P, defer, dcount, (uint32_t)cap_blk,
+                                                                 pick1, so.k, so.kout_rule, so.seed, nz, d, w.fs);
+            else
+                k_kout_hook_first<OffT><<<gv, TPB, 0, s>>>(I, g.A, g.n, g.m, P, defer, dcount, (uint32_t)cap_blk,
+                                                           pick1, so.k, so.kout_rule, so.seed, nz, d);
         }
         {
             CC_PROF("k_kout_defer", s);
             k_kout_defer<E><<<gv, TPB, 0, s>>>(g.n, P, defer, dcount, gv, (uint32_t)cap_blk, d);
         }
         if (so.k > 1) {
+            // full compression between the rounds: without it the second
+            // round's unions walk the first round's uncompressed chains, which
+            // measured 20x slower than this pass (5.3 against 0.25 ms at
+            // R-MAT scale 26)
+            {
+                CC_PROF("k_compress_mid", s);
+                k_shortcut<false><<<gv, TPB, 0, s>>>(P, nullptr, g.n, nullptr, d, nullptr, nullptr, count_into);
+            }
             if (pick1) {
                 CC_PROF("k_kout_apply_pick", s);
                 k_kout_apply_pick<E><<<gv, TPB, 0, s>>>(pick1, g.n, P, d);
             } else {
-                {
-                    CC_PROF("k_compress_mid", s);
-                    k_shortcut<false><<<gv, TPB, 0, s>>>(P, nullptr, g.n, nullptr, d);
-                }
                 CC_PROF("k_kout_rest", s);
                 launch_kout<OffT, E>(gv, s, I, g.A, g.n, g.m, so.k, so.kout_rule, so.seed, P, d, 1u, so.k);
             }
         }
-        if (count_into) {
+        if (fuse) {
+            // compression + count + arg-max key + the finish's candidate
+            // lists against a sampled guess of L_max (checked in identify)
+            Ctl *ctl = w.ctl();
+            {
+                CC_PROF("k_guess_lmax", s);
+                k_guess_lmax<<<1, 256, 0, s>>>(P, nz, g.n, so.seed, ctl);
+            }
+            CC_PROF("k_compress_count", s);
+            k_compress_count_bin<OffT><<<grid_for(di, g.n, TPB, 6), TPB, 0, s>>>(
+                P, g.n, count_into, I, g.m, nz, ctl, w.sc.at<uint32_t>(w.o_light),
+                                                          w.sc.at<ChunkRef>(w.o_chunks), w.chunk_cap, d);
+            w.lists_built = true;
+        } else if (count_into) {
             // the arg-max key is taken as the compression counts (identify
-            // then only converts it); with k = 2 the zeroed stash counts
-            uint32_t *cnt = pick1 ? pick1 : count_into;
-            if (!pick1) CC_TRY(cudaMemsetAsync(cnt, 0, (size_t)g.n * 4, s));
+            // then only converts it); with k > 1 the mid-round compression
+            // cleared the count array
+            uint32_t *cnt = count_into;
+            if (so.k <= 1) CC_TRY(cudaMemsetAsync(cnt, 0, (size_t)g.n * 4, s));
             CC_TRY(cudaMemsetAsync(&w.ctl()->key, 0, 8, s));
             CC_PROF("k_compress_count", s);
             k_shortcut<true><<<gv, TPB, 0, s>>>(P, nullptr, g.n, cnt, d, &w.ctl()->key);
@@ -1789,7 +2096,16 @@ cc_status identify_phase(const uint32_t *L, uint32_t n, uint32_t samples, uint64
         CC_PROF("k_argmax_counts", s);
         k_argmax_counts<<<gv, TPB, 0, s>>>(cnt, n, &ctl->key);
     }
-    {
+    if (w.lists_built && w.select) {
+        // the check plus the selector's features and choice
+        CC_PROF("k_lmax_select", s);
+        k_lmax_select<<<1, MLP_H, 0, s>>>(ctl, lmax_out, w.fs, n, w.sel_m, w.sel_params, w.sel_force, w.sel_feat,
+                                          w.sel_host);
+    } else if (w.lists_built) {
+        // the fused k-out pass binned against a guess: check it
+        CC_PROF("k_lmax_check", s);
+        k_lmax_check<<<1, 1, 0, s>>>(ctl, lmax_out);
+    } else {
         CC_PROF("k_key_to_label", s);
         k_key_to_label<<<1, 1, 0, s>>>(&ctl->key, lmax_out);
     }
@@ -1798,9 +2114,13 @@ cc_status identify_phase(const uint32_t *L, uint32_t n, uint32_t samples, uint64
 }
 
 // lmax_p: device pointer to L_max, or nullptr for "skip nothing".
+// skip (device word, may be null; union-find finishes only): when it reads
+// 1 the finish's kernels return at once (the selected path chose another
+// finish after these kernels were enqueued).
 template <typename OffT>
 cc_status finish_phase(const Graph &g, const cc_finish_opt &fo, const uint32_t *lmax_p, uint32_t *P, Work &w,
-                       const DeviceInfo *di, const Dev &d, cudaStream_t s, uint32_t *rounds_out) {
+                       const DeviceInfo *di, const Dev &d, cudaStream_t s, uint32_t *rounds_out,
+                       const uint32_t *skip = nullptr) {
     const OffT *I = static_cast<const OffT *>(g.I);
     const uint32_t n = g.n;
     Ctl *ctl = w.ctl();
@@ -1808,8 +2128,14 @@ cc_status finish_phase(const Graph &g, const cc_finish_opt &fo, const uint32_t *
     const unsigned gv = grid_for(di, n, TPB);
     const unsigned gc = grid_for(di, (uint64_t)1 << 40, TPB);
     if (rounds_out) *rounds_out = 0;
-    CC_TRY(cudaMemsetAsync(&ctl->nchunks, 0, 4, s));
-    CC_TRY(cudaMemsetAsync(&ctl->edges, 0, 8, s));
+    // lists built by the fused k-out pass (against the exact L_max, or
+    // cleared by k_lmax_check and rebuilt by the guarded k_cand_bin below)
+    const bool built = w.lists_built && lmax_p != nullptr;
+    const uint32_t *only_if = built ? &ctl->rebin : nullptr;
+    if (!built) {
+        CC_TRY(cudaMemsetAsync(&ctl->nchunks, 0, 4, s));
+        CC_TRY(cudaMemsetAsync(&ctl->edges, 0, 8, s));
+    }
     uint32_t *light = w.sc.at<uint32_t>(w.o_light);
     if (fo.kind == CC_FINISH_UF_REM_CAS || fo.kind == CC_FINISH_UF_ASYNC || fo.kind == CC_FINISH_UF_HOOKS ||
         fo.kind == CC_FINISH_UF_EARLY) {
@@ -1819,11 +2145,11 @@ cc_status finish_phase(const Graph &g, const cc_finish_opt &fo, const uint32_t *
         // then its edges are applied.
         const bool lower_only = (lmax_p == nullptr);
         if (!lower_only) {
-            CC_TRY(cudaMemsetAsync(&ctl->nlight, 0, 4, s));
+            if (!built) CC_TRY(cudaMemsetAsync(&ctl->nlight, 0, 4, s));
             {
                 CC_PROF("k_cand_bin", s);
                 k_cand_bin<OffT><<<gv, TPB, 0, s>>>(I, n, g.m, P, lmax_p, light, &ctl->nlight, chunks, &ctl->nchunks,
-                                                    w.chunk_cap, &ctl->edges, d);
+                                                    w.chunk_cap, &ctl->edges, d, only_if, skip);
             }
             CC_LAUNCH();
         }
@@ -1839,11 +2165,13 @@ cc_status finish_phase(const Graph &g, const cc_finish_opt &fo, const uint32_t *
             else
                 {
                     CC_PROF("k_light_list", s);
-                    k_light_list<OffT, UnionEdge<E>><<<gv, TPB, 0, s>>>(I, g.A, n, g.m, light, &ctl->nlight, f, d);
+                    k_light_list<OffT, UnionEdge<E>><<<gv, TPB, 0, s>>>(I, g.A, n, g.m, light, &ctl->nlight, f, d,
+                                                                         skip);
                 }
             {
                 CC_PROF("k_chunks", s);
-                k_chunks<OffT, UnionEdge<E>><<<gc, TPB, 0, s>>>(I, g.A, n, g.m, chunks, &ctl->nchunks, w.chunk_cap, f, d);
+                k_chunks<OffT, UnionEdge<E>><<<gc, TPB, 0, s>>>(I, g.A, n, g.m, chunks, &ctl->nchunks, w.chunk_cap, f, d,
+                                                                skip);
             }
             CC_LAUNCH();
             return CC_OK;
@@ -1851,18 +2179,18 @@ cc_status finish_phase(const Graph &g, const cc_finish_opt &fo, const uint32_t *
         if (st != CC_OK) return st;
         {
             CC_PROF("k_final_shortcut", s);
-            k_shortcut<false><<<gv, TPB, 0, s>>>(P, nullptr, n, nullptr, d);
+            k_shortcut<false><<<gv, TPB, 0, s>>>(P, nullptr, n, nullptr, d, nullptr, skip);
         }
         CC_LAUNCH();
         return CC_OK;
     }
     // SV / LT-PRF and the other min-label finishes: candidate lists once,
     // then rounds until nothing changes.
-    CC_TRY(cudaMemsetAsync(&ctl->nlight, 0, 4, s));
+    if (!built) CC_TRY(cudaMemsetAsync(&ctl->nlight, 0, 4, s));
     {
         CC_PROF("k_cand_bin", s);
         k_cand_bin<OffT><<<gv, TPB, 0, s>>>(I, n, g.m, P, lmax_p, light, &ctl->nlight, chunks, &ctl->nchunks,
-                                            w.chunk_cap, &ctl->edges, d);
+                                            w.chunk_cap, &ctl->edges, d, only_if);
     }
     CC_LAUNCH();
     if (fo.kind != CC_FINISH_SV && fo.kind != CC_FINISH_LT_PRF) {
@@ -2141,124 +2469,114 @@ const void *host_device_view(const void *p, size_t bytes) {
     return a.devicePointer;
 }
 
-// Capped BFS (push only, at most `cap` levels) from src: levels run and
-// vertices reached.  Uses the BFS sampling's kernels and scratch.
-template <typename OffT>
-cc_status bfs_capped(const Graph &g, uint32_t src, uint32_t cap, uint32_t *P, Work &w, const DeviceInfo *di,
-                     const Dev &d, cudaStream_t s, uint32_t *levels, uint64_t *reached) {
-    const OffT *I = static_cast<const OffT *>(g.I);
-    const uint32_t n = g.n;
-    const uint64_t words = (n + 31) / 32;
-    Ctl *ctl = w.ctl();
-    uint32_t *vis = w.sc.at<uint32_t>(w.o_vis);
-    uint32_t *q[2] = {w.sc.at<uint32_t>(w.o_q0), w.sc.at<uint32_t>(w.o_q1)};
-    ChunkRef *chunks = w.sc.at<ChunkRef>(w.o_chunks);
-    const unsigned gv = grid_for(di, n, TPB);
-    CC_TRY(cudaMemsetAsync(vis, 0, words * 4, s));
-    CC_TRY(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
-    k_set_u32<<<1, 1, 0, s>>>(q[0], src);
-    k_set_u32<<<1, 1, 0, s>>>(&ctl->nfront[0], 1);
-    k_set_u32<<<1, 1, 0, s>>>(&ctl->minv, src);
-    k_list_to_bitmap<<<1, 32, 0, s>>>(q[0], &ctl->nfront[0], vis);
-    CC_LAUNCH();
-    uint64_t tot = 1;
-    uint32_t lv = 0;
-    int cur = 0;
-    for (; lv < cap; ++lv) {
-        const int nx = cur ^ 1;
-        CC_TRY(cudaMemsetAsync(&ctl->nfront[nx], 0, 4, s));
-        CC_TRY(cudaMemsetAsync(&ctl->nchunks, 0, 4, s));
-        BFSEdge f{P, vis, q[nx], &ctl->nfront[nx], &ctl->minv, src, NONE, d.forest};
-        {
-            CC_PROF("k_list_bin", s);
-            k_list_bin<OffT, BFSEdge><<<gv, TPB, 0, s>>>(I, g.A, n, g.m, q[cur], &ctl->nfront[cur], f, chunks,
-                                                         &ctl->nchunks, w.chunk_cap, d);
-        }
-        {
-            CC_PROF("k_chunks", s);
-            k_chunks<OffT, BFSEdge><<<grid_for(di, (uint64_t)1 << 40, TPB), TPB, 0, s>>>(
-                I, g.A, n, g.m, chunks, &ctl->nchunks, w.chunk_cap, f, d);
-        }
-        CC_LAUNCH();
-        uint32_t nf = 0;
-        CC_TRY(cudaMemcpyAsync(&nf, &ctl->nfront[nx], 4, cudaMemcpyDeviceToHost, s));
-        CC_TRY(cudaStreamSynchronize(s));
-        cur = nx;
-        if (nf == 0) break;
-        tot += nf;
+// ---------------------------------------------------------------- the selected path
+// The learned selector's run (no counterpart in the paper, which picks by a
+// hand-made decision tree, Section 4.7).  The default path (k-out k = 2 +
+// UF-Rem-CAS) runs as usual; the first k-out pass also gathers the degree
+// statistics, and the kernel that checks L_max also forms the 16 features
+// and runs the MLP (k_lmax_select).  The default finish is enqueued right
+// behind it, guarded by a device word; the host waits only for the choice
+// (an event), while the GPU goes on.  If the choice is the default, the
+// call returns with the finish in flight.  Otherwise the guarded kernels
+// return at once and the host enqueues the chosen path: another finish on
+// the same k-out sample and candidate lists, or (BFS / LDD sampling) the
+// whole static path.  Every class computes the same labels.
+//
+// Classes: c = 4 * sampling + finish, sampling 0 k-out, 1 BFS, 2 LDD;
+// finish 0 UF-Rem-CAS (FindNaive, SplitAtomicOne), 1 UF-Async (FindSplit),
+// 2 SV, 3 Liu-Tarjan PRF.
+void class_opts(int c, const cc_sample_opt &base, cc_sample_opt &so, cc_finish_opt &fo) {
+    so = base;
+    cc_default_opts(nullptr, &fo);
+    const int sm = c / 4, fin = c % 4;
+    so.kind = sm == 0 ? CC_SAMPLE_KOUT : sm == 1 ? CC_SAMPLE_BFS : CC_SAMPLE_LDD;
+    fo.kind = fin == 0 ? CC_FINISH_UF_REM_CAS : fin == 1 ? CC_FINISH_UF_ASYNC : fin == 2 ? CC_FINISH_SV
+                                                                                       : CC_FINISH_LT_PRF;
+    fo.find = fin == 1 ? CC_FIND_SPLIT : CC_FIND_NAIVE;
+}
+
+// Per host thread and device: a word of mapped host memory the choosing
+// kernel writes, and the event after that kernel.  (Kept until exit.)
+struct SelHost {
+    int device = -1;
+    int *word = nullptr;
+    int *dword = nullptr;
+    cudaEvent_t ev = nullptr;
+};
+
+cc_status sel_host(const DeviceInfo *di, SelHost **out) {
+    thread_local SelHost h;
+    if (h.device != di->device) {
+        SelHost x;
+        CC_TRY(cudaHostAlloc(reinterpret_cast<void **>(&x.word), 64, cudaHostAllocMapped | cudaHostAllocPortable));
+        CC_TRY(cudaHostGetDevicePointer(reinterpret_cast<void **>(&x.dword), x.word, 0));
+        CC_TRY(cudaEventCreateWithFlags(&x.ev, cudaEventDisableTiming));
+        x.device = di->device;
+        h = x;
     }
-    *levels = lv;
-    *reached = tot;
+    *out = &h;
     return CC_OK;
 }
 
+// features_only: stop after the features (class 0, nothing else runs; P
+// holds the k-out sample).  force >= 0: run that class whatever the MLP
+// says (the selector's training times each class this way).
 template <typename OffT>
-cc_status run_features(const Graph &g, uint64_t seed, float *feat_out, cudaStream_t s) {
+cc_status run_select(const Graph &g, const float *params, int force, uint64_t seed, uint32_t *P, float *feat_out,
+                     int32_t *class_out, bool features_only, cudaStream_t s) {
     const DeviceInfo *di = device_info();
     if (!di) return CC_ERR_CUDA;
-    const Dev d = make_dev(di, g.n);
-    const uint32_t n = g.n;
-    const unsigned gv = grid_for(di, n, TPB);
-    Work w;
-    plan(w, g, CC_SAMPLE_KOUT, 0, CC_FINISH_UF_REM_CAS, false);
-    const uint64_t words = (n + 31) / 32;
-    w.o_vis = w.sc.reserve(words * 4);
-    w.o_q0 = w.sc.reserve((size_t)n * 4);
-    w.o_q1 = w.sc.reserve((size_t)n * 4);
-    const size_t o_lab = w.sc.reserve((size_t)n * 4), o_st = w.sc.reserve(sizeof(FeatStats));
-    cc_status st = w.sc.alloc(s);
-    if (st != CC_OK) return st;
-    uint32_t *P = w.sc.at<uint32_t>(o_lab);
-    FeatStats *fs = w.sc.at<FeatStats>(o_st);
-    CC_TRY(cudaMemsetAsync(fs, 0, sizeof(FeatStats), s));
-    CC_TRY(cudaMemsetAsync(w.ctl(), 0, sizeof(Ctl), s));
-    {
-        CC_PROF("k_degree_stats", s);
-        k_degree_stats<OffT><<<gv, TPB, 0, s>>>(static_cast<const OffT *>(g.I), n, g.m, fs, d);
-    }
-    CC_LAUNCH();
-    // k-out sample (k = 2) and its frequent cluster
+    Dev d = make_dev(di, g.n);
     cc_sample_opt so;
     cc_finish_opt fo;
     cc_default_opts(&so, &fo);
     so.seed = seed;
+    Work w;
+    plan(w, g, CC_SAMPLE_KOUT, 0, CC_FINISH_UF_REM_CAS, true);
+    // SV / LT-PRF on the same sample need the round-start copy
+    w.has_sv = true;
+    w.o_prev = w.sc.reserve((size_t)g.n * 4);
+    const size_t o_fs = w.sc.reserve(sizeof(FeatStats));
+    cc_status st = w.sc.alloc(s);
+    if (st != CC_OK) return st;
+    SelHost *h = nullptr;
+    if (!features_only && (st = sel_host(di, &h)) != CC_OK) return st;
+    w.fs = w.sc.at<FeatStats>(o_fs);
+    w.select = true;
+    w.sel_params = features_only ? nullptr : params;
+    w.sel_force = features_only ? -1 : force;
+    w.sel_feat = feat_out;
+    w.sel_host = h ? h->dword : nullptr;
+    w.sel_m = g.m;
+    CC_TRY(cudaMemsetAsync(w.ctl(), 0, sizeof(Ctl), s));
+    CC_TRY(cudaMemsetAsync(w.fs, 0, sizeof(FeatStats), s));
     int32_t info = 0;
-    if ((st = sample_phase<OffT>(g, so, fo, P, w, di, d, s, &info, w.sc.at<uint32_t>(w.o_counts))) != CC_OK) return st;
-    if ((st = identify_phase(P, n, 0, seed, &w.ctl()->lmax, w, di, d, s, true, true)) != CC_OK) return st;
-    {
-        CC_PROF("k_label_stats", s);
-        k_label_stats<OffT><<<gv, TPB, 0, s>>>(static_cast<const OffT *>(g.I), n, g.m, P, &w.ctl()->lmax, fs, d);
+    if ((st = sample_phase<OffT>(g, so, fo, P, w, di, d, s, &info, w.sc.at<uint32_t>(w.o_counts))) != CC_OK)
+        return st;
+    if (!w.lists_built) return CC_ERR_INVALID;   // not reached: k = 2 with a finish always fuses
+    if ((st = identify_phase(P, g.n, 0, seed, &w.ctl()->lmax, w, di, d, s, true, true)) != CC_OK) return st;
+    if (features_only) {
+        if (class_out) *class_out = 0;
+        return CC_OK;
     }
-    CC_LAUNCH();
-    FeatStats h;
-    CC_TRY(cudaMemcpyAsync(&h, fs, sizeof(h), cudaMemcpyDeviceToHost, s));
-    CC_TRY(cudaStreamSynchronize(s));
-    // capped BFS from the highest-degree vertex (ties: smallest id)
-    const uint32_t src = ~(uint32_t)(h.maxkey & 0xFFFFFFFFull);
-    uint32_t levels = 0;
-    uint64_t reached = 0;
-    if ((st = bfs_capped<OffT>(g, src, 64, P, w, di, d, s, &levels, &reached)) != CC_OK) return st;
-    const double nn = (double)n, mm = (double)g.m > 0 ? (double)g.m : 1.0;
-    const double mean = (double)h.sum_deg / nn;
-    const double var = h.sum_deg2 / nn - mean * mean;
-    float f[CC_MLP_IN];
-    f[0] = (float)std::log2(nn + 1.0);
-    f[1] = (float)std::log2((double)g.m + 1.0);
-    f[2] = (float)mean;
-    f[3] = (float)std::log2((double)(h.maxkey >> 32) + 1.0);
-    f[4] = (float)(mean > 0 ? var / (mean * mean) : 0.0);
-    for (int j = 0; j < 3; ++j) f[5 + j] = (float)(h.cnt[j] / nn);
-    f[8] = (float)(h.cnt[3] / nn);
-    f[9] = (float)(h.cnt[4] / nn);
-    f[10] = (float)(h.edges_gt64 / mm);
-    f[11] = (float)(h.lmax_count / nn);
-    f[12] = (float)(h.roots / nn);
-    f[13] = (float)(h.edges_nonlmax / mm);
-    f[14] = (float)(levels / 64.0);
-    f[15] = (float)(reached / nn);
-    CC_TRY(cudaMemcpyAsync(feat_out, f, sizeof(f), cudaMemcpyHostToDevice, s));
-    CC_TRY(cudaStreamSynchronize(s));
-    return CC_OK;
+    CC_TRY(cudaEventRecord(h->ev, s));
+    const uint32_t *lmax_p = &w.ctl()->lmax;
+    if ((st = finish_phase<OffT>(g, fo, lmax_p, P, w, di, d, s, nullptr, &w.ctl()->skip)) != CC_OK) return st;
+    CC_TRY(cudaEventSynchronize(h->ev));
+    const int cls = *h->word & 0xFF;
+    if (class_out) *class_out = cls;
+    if (cls == 0) return CC_OK;
+    cc_sample_opt so2;
+    cc_finish_opt fo2;
+    class_opts(cls, so, so2, fo2);
+    if (so2.kind == CC_SAMPLE_KOUT) {
+        // another finish on the same sample (the lists are rebuilt first if
+        // the L_max guess was wrong)
+        uint32_t rounds = 0;
+        return finish_phase<OffT>(g, fo2, lmax_p, P, w, di, d, s, &rounds);
+    }
+    w.sc.release();
+    return run_static<OffT>(g, so2, fo2, P, nullptr, s);
 }
 
 }  // namespace
@@ -2457,5 +2775,28 @@ extern "C" cc_status cc_features(const void *offsets, int offsets_u64, const uin
     if (n == 0 || !feat_out || !aligned(feat_out, 4)) return CC_ERR_INVALID;
     Graph g{offsets, offsets_u64 != 0, edges, n, m};
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    return offsets_u64 ? run_features<uint64_t>(g, seed, feat_out, s) : run_features<uint32_t>(g, seed, feat_out, s);
+    Scratch sc;
+    const size_t op = sc.reserve((size_t)n * 4);
+    if ((st = sc.alloc(s)) != CC_OK) return st;
+    uint32_t *P = sc.at<uint32_t>(op);
+    return offsets_u64 ? run_select<uint64_t>(g, nullptr, -1, seed, P, feat_out, nullptr, true, s)
+                       : run_select<uint32_t>(g, nullptr, -1, seed, P, feat_out, nullptr, true, s);
+}
+
+extern "C" cc_status cc_select_static(const void *offsets, int offsets_u64, const uint32_t *edges, uint32_t n,
+                                      uint64_t m, const float *params, int force_class, uint64_t seed,
+                                      uint32_t *labels_out, float *feat_out, int32_t *class_out, void *stream) {
+    cc_status st = check_graph(offsets, offsets_u64, edges, n, m);
+    if (st != CC_OK) return st;
+    if (!labels_out || !aligned(labels_out, 4) || (feat_out && !aligned(feat_out, 4))) return CC_ERR_INVALID;
+    if (force_class >= CC_MLP_OUT || (force_class < 0 && !params)) return CC_ERR_INVALID;
+    if (params && !aligned(params, 4)) return CC_ERR_INVALID;
+    if (n == 0) {
+        if (class_out) *class_out = force_class >= 0 ? force_class : 0;
+        return CC_OK;
+    }
+    Graph g{offsets, offsets_u64 != 0, edges, n, m};
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    return offsets_u64 ? run_select<uint64_t>(g, params, force_class, seed, labels_out, feat_out, class_out, false, s)
+                       : run_select<uint32_t>(g, params, force_class, seed, labels_out, feat_out, class_out, false, s);
 }

@@ -4,69 +4,90 @@ library's own kernels (cc_mlp_*).  It never changes labels: every class
 runs the same exact connectivity, only faster or slower; if anything goes
 wrong it falls back to k-out + UF-Rem-CAS.
 
-The paper chooses by a hand-made decision tree (Section 4.7):
-UF-Rem-CAS with FindNaive; no sampling when m/n < 3; BFS (or LDD) sampling
-for dense, low-diameter graphs; k-out otherwise.  `paper_decision_tree`
-restates it on this library's features (low diameter: a BFS from the
-highest-degree vertex finishes within 64 levels and reaches at least half
-of the vertices).
+Classes: {k-out (k = 2), BFS (3 tries), LDD (beta 0.2)} x {UF-Rem-CAS,
+UF-Async, SV, Liu-Tarjan PRF}, class 0 (k-out + UF-Rem-CAS) the default.
+The choice is made inside the selected path (cc_select_static): the
+default's k-out sample is computed first, the features come from it, and a
+k-out class continues on it, so the features cost little and the sample is
+not redone.
+
+The paper chooses by a hand-made decision tree (Section 4.7): UF-Rem-CAS
+with FindNaive; no sampling when m/n < 3; BFS (or LDD) sampling for dense,
+low-diameter graphs; k-out otherwise.  `paper_decision_tree` restates it on
+this library's features; its no-sampling branch lies outside the twelve
+classes, so it returns (sampling, finish) names rather than a class index.
 """
 from __future__ import annotations
 
 import torch
 
-from . import (MLP_IN, MLP_NPARAM, MLP_OUT, cc_features, cc_static, finish_opt, mlp_adam, mlp_backward,
-               mlp_forward, mlp_init, mlp_predict, mlp_set_norm, mlp_soft_targets, sample_opt)
+from . import (MLP_IN, MLP_NPARAM, MLP_OUT, cc_features, cc_select_static, cc_static, finish_opt, mlp_adam,
+               mlp_backward, mlp_forward, mlp_init, mlp_predict, mlp_set_norm, mlp_soft_targets, sample_opt)
 
-SAMPLES = ("none", "kout", "bfs", "ldd")
-FINISHES = ("uf_rem_cas", "uf_async", "sv")
+SAMPLES = ("kout", "bfs", "ldd")
+FINISHES = ("uf_rem_cas", "uf_async", "sv", "lt_prf")
 CLASSES = [(s, f) for s in SAMPLES for f in FINISHES]
 assert len(CLASSES) == MLP_OUT
 DEFAULT = CLASSES.index(("kout", "uf_rem_cas"))
+assert DEFAULT == 0
 
 
 def class_opts(c: int):
+    """cc_static options of class c (the same combination cc_select_static
+    runs for c)."""
     s, f = CLASSES[c]
     return sample_opt(s), finish_opt(f, "split" if f == "uf_async" else "naive")
 
 
-def paper_decision_tree(feat: torch.Tensor) -> int:
-    """The paper's rule on one feature vector (host floats)."""
+def paper_decision_tree(feat: torch.Tensor) -> tuple:
+    """The paper's rule on one feature vector (host floats): (sampling,
+    finish).  Dense means m/n >= 3; low diameter means the k-out trees were
+    shallow (at most 1.5 parent steps per non-root in the sampling's last
+    compression) and the frequent cluster holds at least half the vertices."""
     f = [float(x) for x in feat]
-    avg_deg, bfs_levels, bfs_reached = f[2], f[14], f[15]
+    avg_deg, l_max_frac, depth = f[2], f[11], f[15]
     if avg_deg < 3.0:
-        return CLASSES.index(("none", "uf_rem_cas"))
-    # low diameter: the capped BFS finished AND it covered most of the graph
-    # (a hub inside a small component finishes early on any graph)
-    if bfs_levels < 1.0 and bfs_reached >= 0.5:
-        return CLASSES.index(("bfs", "uf_rem_cas"))
-    return DEFAULT
+        return ("none", "uf_rem_cas")
+    if depth <= 1.5 and l_max_frac >= 0.5:
+        return ("bfs", "uf_rem_cas")
+    return ("kout", "uf_rem_cas")
 
 
-def time_classes(offsets, edges, reps: int = 3, labels=None) -> torch.Tensor:
+def _timed(fn, reps: int) -> float:
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fn()
+    best = float("inf")
+    for _ in range(reps):
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return best
+
+
+def time_classes(offsets, edges, reps: int = 3, labels=None, realized: bool = True) -> torch.Tensor:
     """Milliseconds of every class on one graph (best of `reps` after one
-    untimed run), with CUDA events on the current stream."""
+    untimed run), with CUDA events on the current stream.  realized: each
+    class as the selected path runs it (cc_select_static with the class
+    forced: features and the default's k-out sample included, the sample
+    reused by k-out classes); else as a plain cc_static call."""
     n = offsets.numel() - 1
     if labels is None:
         labels = torch.empty(n, dtype=torch.int32, device=offsets.device)
     out = torch.empty(MLP_OUT, dtype=torch.float32)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for c in range(MLP_OUT):
-        so, fo = class_opts(c)
-        cc_static(offsets, edges, so, fo, labels)
-        best = float("inf")
-        for _ in range(reps):
-            e0.record()
-            cc_static(offsets, edges, so, fo, labels)
-            e1.record()
-            e1.synchronize()
-            best = min(best, e0.elapsed_time(e1))
-        out[c] = best
+        if realized:
+            out[c] = _timed(lambda: cc_select_static(offsets, edges, None, c, labels_out=labels), reps)
+        else:
+            so, fo = class_opts(c)
+            out[c] = _timed(lambda: cc_static(offsets, edges, so, fo, labels), reps)
     return out
 
 
 class Selector:
-    """MLP 16 -> 64 -> 64 -> 12 over cc_features, trained on measured times."""
+    """MLP 16 -> 64 -> 64 -> 12 over the selected path's features, trained
+    on measured times."""
 
     def __init__(self, device="cuda", seed: int = 1):
         self.device = torch.device(device)
@@ -110,12 +131,11 @@ class Selector:
             return DEFAULT
 
     def run(self, offsets, edges, labels_out=None):
-        """Labels of the graph with the chosen combination (k-out + UF-Rem-CAS
-        if the choice cannot run)."""
-        c = self.choose(offsets, edges)
-        so, fo = class_opts(c)
+        """Labels of the graph by the selected path (features, choice and run
+        in one call), and the class it ran; k-out + UF-Rem-CAS if the
+        selected path cannot run."""
         try:
-            return cc_static(offsets, edges, so, fo, labels_out), c
+            return cc_select_static(offsets, edges, self.params, -1, labels_out=labels_out)
         except Exception:
             so, fo = class_opts(DEFAULT)
             return cc_static(offsets, edges, so, fo, labels_out), DEFAULT

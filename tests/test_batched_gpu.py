@@ -46,6 +46,17 @@ def test_batched_schedules(batch, mode, threads, smem):
     assert cc.device_error() == 0
 
 
+@pytest.mark.parametrize("smem", [0, 28672, 57344])
+def test_batched_two_ctas_per_sm(batch, smem):
+    # mode 3: the tile walk at two 1024-thread CTAs per SM (1024 threads only)
+    gs, gv, off, edg, want = batch
+    lab = cc.cc_batched(gv, off, edg, cc.batch_opt(1024, smem, 3))
+    assert np.array_equal(lab.cpu().numpy().view(np.uint32), want)
+    with pytest.raises(cc.CCError):
+        cc.cc_batched(gv, off, edg, cc.batch_opt(512, smem, 3))
+    assert cc.device_error() == 0
+
+
 def test_batched_u32_offsets_and_autotune(batch):
     gs, gv, off, edg, want = batch
     lab, best, ms = cc.cc_batched_autotune(gv, off.to(torch.int32), edg)

@@ -83,38 +83,81 @@ def test_training_learns_a_rule():
 
 
 def test_features_closed_form_path():
+    # path 0 - 1 - ... - (n-1): two vertices of degree 1, the rest degree 2;
+    # k-out joins everything into the cluster of vertex 0, nothing is left
+    # for the finish
     n = 1000
     g = synth.path(n)
     f = cc.cc_features(g.offsets.cuda(), g.edges.cuda()).cpu().numpy()
     assert abs(f[0] - np.log2(n + 1)) < 1e-5 and abs(f[1] - np.log2(2 * (n - 1) + 1)) < 1e-5
     assert abs(f[2] - 2 * (n - 1) / n) < 1e-6 and abs(f[3] - np.log2(3)) < 1e-6
     assert f[5] == 0 and abs(f[6] - 2 / n) < 1e-7 and abs(f[7] - (n - 2) / n) < 1e-6
-    assert f[11] == 1.0 and abs(f[12] - 1 / n) < 1e-7 and f[13] == 0.0
-    # BFS from vertex 1 (the smallest of the degree-2 vertices) for 64 levels
-    assert f[14] == 1.0 and abs(f[15] - (1 + 1 + 64) / n) < 1e-6
+    assert f[11] == 1.0 and abs(f[12] - (n - 1) / n) < 1e-6 and f[13] == 0.0 and f[14] == 0.0
+    assert f[15] >= 0.0
+
+
+def _check_features(g, seed):
+    off, edg = g.numpy()
+    f = cc.cc_features(g.offsets.cuda(), g.edges.cuda(), seed=seed).cpu().numpy()
+    deg = np.diff(off).astype(np.float64)
+    n, m = g.n, max(1.0, deg.sum())
+    assert abs(f[2] - deg.mean()) < 1e-4 * max(deg.mean(), 1e-9)
+    if deg.mean() > 0:
+        assert abs(f[4] - deg.var() / deg.mean() ** 2) < 1e-3 * max(deg.var() / deg.mean() ** 2, 1e-9)
+    assert abs(f[3] - np.log2(deg.max() + 1)) < 1e-5
+    assert abs(f[5] - (deg == 0).mean()) < 1e-6 and abs(f[9] - (deg > 64).mean()) < 1e-6
+    assert abs(f[10] - deg[deg > 64].sum() / m) < 1e-5
+    # from the k-out sample (the oracle's, same seed) and its IdentifyFrequent
+    lab = oracle.kout_sample(off, edg, 2, seed)
+    lm, cnt = oracle.identify_frequent(lab)
+    out = lab != lm
+    assert abs(f[11] - cnt / n) < 1e-6
+    assert abs(f[12] - (lab != np.arange(n)).mean()) < 1e-6
+    assert abs(f[13] - deg[out].sum() / m) < 1e-6
+    assert abs(f[14] - (out & (deg > 0) & (deg <= 32)).mean()) < 1e-6
+    return f
 
 
 def test_features_match_numpy_and_oracle():
-    g = synth.rmat(16, 8, seed=4)
-    off, edg = g.numpy()
-    f = cc.cc_features(g.offsets.cuda(), g.edges.cuda(), seed=9).cpu().numpy()
-    deg = np.diff(off).astype(np.float64)
-    assert abs(f[2] - deg.mean()) < 1e-4 * deg.mean()
-    assert abs(f[4] - deg.var() / deg.mean() ** 2) < 1e-3 * (deg.var() / deg.mean() ** 2)
-    assert abs(f[5] - (deg == 0).mean()) < 1e-6 and abs(f[9] - (deg > 64).mean()) < 1e-6
-    assert abs(f[10] - deg[deg > 64].sum() / deg.sum()) < 1e-5
-    lab = oracle.kout_sample(off, edg, 2, 9)
-    lm, cnt = oracle.identify_frequent(lab)
-    assert abs(f[11] - cnt / g.n) < 1e-6
-    assert abs(f[12] - len(np.unique(lab)) / g.n) < 1e-6
-    assert abs(f[13] - deg[lab != lm].sum() / deg.sum()) < 1e-6
+    f1 = _check_features(synth.rmat(16, 8, seed=4), 9)
+    f2 = _check_features(synth.grid2d(200, 150, 0.2, seed=3), 2)
+    _check_features(synth.erdos_renyi(40000, 1.5, seed=5), 4)
+    _check_features(synth.cliques([7, 30, 2, 64, 5] * 20), 1)
+    # the depth stand-in separates a power-law graph from a grid
+    assert f2[15] > f1[15]
+
+
+def test_selected_path_every_class_exact():
+    """Every class the selected path can run (forced) gives the oracle's
+    labels and reports the class it ran."""
+    for i, g in enumerate((synth.rmat(13, 8, seed=2), synth.grid2d(90, 80, 0.3, seed=1),
+                           synth.erdos_renyi(20000, 1.2, seed=3), synth.path(3000))):
+        want, _ = oracle.cc_uf(*g.numpy())
+        off, edg = g.offsets.cuda(), g.edges.cuda()
+        for c in range(12):
+            lab, ran = cc.cc_select_static(off, edg, None, c)
+            assert ran == c
+            assert np.array_equal(lab.cpu().numpy().view(np.uint32), want), (i, c)
+    assert cc.device_error() == 0
+
+
+def test_selected_path_features_equal_cc_features():
+    g = synth.rmat(14, 8, seed=6)
+    off, edg = g.offsets.cuda(), g.edges.cuda()
+    feat = torch.empty(16, device="cuda")
+    sel = selector.Selector(seed=4)
+    lab, c = cc.cc_select_static(off, edg, sel.params, -1, feat_out=feat)
+    assert torch.equal(feat, cc.cc_features(off, edg))
+    # the class the network picks in the path is the one cc_mlp_predict picks
+    assert c == int(sel.predict(feat).item())
 
 
 def test_selector_never_changes_labels():
-    sel = selector.Selector(seed=2)
-    for i in range(8):
-        g = synth.selector_graph(i, seed=3, scale_lo=10, scale_hi=13)
-        want, _ = oracle.cc_uf(*g.numpy())
-        lab, c = sel.run(g.offsets.cuda(), g.edges.cuda())
-        assert 0 <= c < 12
-        assert np.array_equal(lab.cpu().numpy().view(np.uint32), want)
+    for seed in (2, 3, 4):
+        sel = selector.Selector(seed=seed)
+        for i in range(8):
+            g = synth.selector_graph(i, seed=3, scale_lo=10, scale_hi=13)
+            want, _ = oracle.cc_uf(*g.numpy())
+            lab, c = sel.run(g.offsets.cuda(), g.edges.cuda())
+            assert 0 <= c < 12
+            assert np.array_equal(lab.cpu().numpy().view(np.uint32), want)
