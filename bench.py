@@ -213,7 +213,7 @@ def algorithmic_bytes(kernel, n, m, m_finish, n_nz, k, off_bytes):
         # parents
         "k_kout_rest": ob * (n + 1) + n_nz * (k - 1) * (SECTOR + 4) + 4 * n,
         "k_compress_mid": 8 * n,                                    # read + write P
-        "k_compress_count": 8 * n,
+        "k_compress_count": 8 * n + n // 8,                         # read + write P, the degree bitmap
         "k_compress": 8 * n,
         "k_final_shortcut": 8 * n,
         "k_count_labels": 4 * n,
@@ -607,54 +607,88 @@ def bench_matrix(args, cc, synth, dev, grid=True, er=True):
 
 
 def bench_selector(args, cc, synth, dev):
-    """Learned selector: features and exhaustive timings of the 12 classes on
-    seeded graphs, train on the first part with the library's MLP kernels,
-    and score the held-out part by regret (t_pick - t_best) / t_best against
-    always k-out + UF-Rem-CAS and against the paper's decision tree."""
+    """Learned selector on seeded graphs (R-MAT, grids, G(n, M), cliques):
+    features and every class's time, training on the first part with the
+    library's MLP kernels, and the held-out part scored.  Class times are
+    realized: each class as the selected path runs it (features and the
+    default's k-out sample included, the sample reused by k-out classes),
+    so regret includes the cost of choosing.  The selected path itself
+    (features, choice, run in one call) is then timed on every held-out
+    graph and compared with plain k-out + UF-Rem-CAS calls.  Regret against
+    the plain class times (the twelve combinations as cc_static runs them)
+    is reported too, and the paper's decision tree (Section 4.7), whose
+    no-sampling branch is timed as plain no-sampling + UF-Rem-CAS."""
     import torch
     from paper_2008_03909_gb300 import selector
     N = args.sel_train + args.sel_test
     X = torch.empty(N, 16, dtype=torch.float32)
-    T = torch.empty(N, 12, dtype=torch.float32)
-    fam = []
+    TR = torch.empty(N, 12, dtype=torch.float32)
+    TP = torch.empty(N, 12, dtype=torch.float32)
+    TN = torch.empty(N, dtype=torch.float32)
     t0 = time.time()
     feat_ms = []
     for i in range(N):
         g = synth.selector_graph(i, seed=7, scale_lo=args.sel_scale_lo, scale_hi=args.sel_scale_hi, device=dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        X[i] = cc.cc_features(g.offsets, g.edges, seed=1).cpu()
-        e1.record()
-        e1.synchronize()
-        feat_ms.append(e0.elapsed_time(e1))
-        T[i] = selector.time_classes(g.offsets, g.edges, reps=2)
-        fam.append(i % 4)
-        del g
+        lab = torch.empty(g.n, dtype=torch.int32, device=dev)
+        feat_ms.append(selector._timed(lambda: cc.cc_features(g.offsets, g.edges), 2))
+        X[i] = cc.cc_features(g.offsets, g.edges).cpu()
+        TR[i] = selector.time_classes(g.offsets, g.edges, reps=2, labels=lab, realized=True)
+        if i >= args.sel_train:   # scoring only
+            TP[i] = selector.time_classes(g.offsets, g.edges, reps=2, labels=lab, realized=False)
+            TN[i] = selector._timed(lambda: cc.cc_static(g.offsets, g.edges, cc.sample_opt("none"),
+                                                         cc.finish_opt("uf_rem_cas"), lab), 2)
+        del g, lab
     collect_s = time.time() - t0
     sel = selector.Selector(device=dev, seed=1)
     t1 = time.time()
-    hist = sel.fit(X[: args.sel_train].to(dev), T[: args.sel_train].to(dev), epochs=800, lr=3e-3)
+    hist = sel.fit(X[: args.sel_train].to(dev), TR[: args.sel_train].to(dev), epochs=800, lr=3e-3)
     train_s = time.time() - t1
-    Xt, Tt = X[args.sel_train:], T[args.sel_train:]
+    Xt, Tr, Tp, Tn = X[args.sel_train:], TR[args.sel_train:], TP[args.sel_train:], TN[args.sel_train:]
     pick = sel.predict(Xt.to(dev)).cpu()
-    tree = torch.tensor([selector.paper_decision_tree(x) for x in Xt], dtype=torch.int32)
+    # the selected path end to end on each held-out graph, and plain default
+    sel_ms, def_ms, exact, ran = [], [], True, []
+    so0, fo0 = selector.class_opts(selector.DEFAULT)
+    for j, i in enumerate(range(args.sel_train, N)):
+        g = synth.selector_graph(i, seed=7, scale_lo=args.sel_scale_lo, scale_hi=args.sel_scale_hi, device=dev)
+        lab = torch.empty(g.n, dtype=torch.int32, device=dev)
+        ref = torch.empty(g.n, dtype=torch.int32, device=dev)
+        cc.cc_static(g.offsets, g.edges, so0, fo0, ref)
+        _, c = sel.run(g.offsets, g.edges, lab)
+        torch.cuda.synchronize()
+        exact = exact and bool(torch.equal(lab, ref))
+        ran.append(c)
+        sel_ms.append(selector._timed(lambda: sel.run(g.offsets, g.edges, lab), 3))
+        def_ms.append(selector._timed(lambda: cc.cc_static(g.offsets, g.edges, so0, fo0, lab), 3))
+        del g, lab, ref
     dflt = torch.full((args.sel_test,), selector.DEFAULT, dtype=torch.int32)
 
-    def score(ch):
-        r = selector.regret(Tt, ch)
+    def score(T, ch):
+        r = selector.regret(T, ch)
         return {"mean_regret": round(float(r.mean()), 4), "median_regret": round(float(r.median()), 4),
                 "p90_regret": round(float(r.quantile(0.9)), 4),
-                "total_ms": round(float(Tt.gather(1, ch.long()[:, None]).sum()), 3)}
+                "total_ms": round(float(T.gather(1, ch.long()[:, None]).sum()), 3)}
 
-    best_ms = float(Tt.min(dim=1).values.sum())
+    tree = [selector.paper_decision_tree(x) for x in Xt]
+    tree_ms = sum(float(Tn[j]) if s == "none" else float(Tp[j, selector.CLASSES.index((s, f))])
+                  for j, (s, f) in enumerate(tree))
     res = {"train_graphs": args.sel_train, "heldout_graphs": args.sel_test,
            "scales": [args.sel_scale_lo, args.sel_scale_hi],
            "classes": [f"{s}+{f}" for s, f in selector.CLASSES],
-           "mlp": score(pick), "always_kout_uf_rem_cas": score(dflt), "paper_decision_tree": score(tree),
-           "oracle_best_total_ms": round(best_ms, 3), "train_loss": [round(hist[0], 4), round(hist[-1], 4)],
+           "selected_path": {"total_ms": round(sum(sel_ms), 3), "labels_exact": exact,
+                             "classes_run": torch.bincount(torch.tensor(ran), minlength=12).tolist(),
+                             "note": "cc_select_static with the trained network: features, choice and run"},
+           "default_plain": {"total_ms": round(sum(def_ms), 3), "note": "cc_static k-out + UF-Rem-CAS"},
+           "selected_vs_default_time": round(sum(def_ms) / max(sum(sel_ms), 1e-9), 4),
+           "realized": {"mlp": score(Tr, pick), "always_default": score(Tr, dflt),
+                        "best_total_ms": round(float(Tr.min(dim=1).values.sum()), 3)},
+           "plain": {"mlp": score(Tp, pick), "always_default": score(Tp, dflt),
+                     "best_total_ms": round(float(Tp.min(dim=1).values.sum()), 3)},
+           "paper_decision_tree": {"total_ms": round(tree_ms, 3),
+                                   "picks": {k: sum(1 for t in tree if t == k) for k in set(tree)}},
+           "train_loss": [round(hist[0], 4), round(hist[-1], 4)],
            "collect_s": round(collect_s, 1), "train_s": round(train_s, 2),
            "features_ms_median": round(float(torch.tensor(feat_ms).median()), 4)}
-    res["mlp_vs_default_time"] = round(res["always_kout_uf_rem_cas"]["total_ms"] / res["mlp"]["total_ms"], 3)
+    res["paper_decision_tree"]["picks"] = {f"{a}+{b}": v for (a, b), v in res["paper_decision_tree"]["picks"].items()}
     return res
 
 
@@ -791,12 +825,12 @@ def bench_incremental(args, cc, synth, dev, qf):
     # rate (latency at the load the plain loop sustains)
     answers = [torch.empty(max(1, nq), dtype=torch.uint8).pin_memory() for (_, _, _, nq) in batches]
 
-    def served(interval_s, zero_copy=False):
+    def served(interval_s, stage=False):
         base = synth.rmat(args.incr_scale, 16, seed=2, device=dev)
         inc2 = cc.Incremental(n, base.offsets, base.edges, finish=cc.finish_opt(args.incr_finish))
         del base
         torch.cuda.empty_cache()
-        srv = cc.Server(inc2, slots=4, slot_pairs=1 << 22, zero_copy=zero_copy)
+        srv = cc.Server(inc2, slots=4, slot_pairs=1 << 22, stage=stage)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         tickets = []
@@ -818,7 +852,7 @@ def bench_incremental(args, cc, synth, dev, qf):
 
     wall_srv, lat_srv, same_all = served(0.0)
     wall_pace, lat_pace, same_pace = served(wall / len(batches))
-    wall_zc, lat_zc, same_zc = served(0.0, zero_copy=True)
+    wall_st, lat_st, same_st = served(0.0, stage=True)
     return {"base": f"rmat{args.incr_scale}_ef16", "n": n, "finish": args.incr_finish, "batches": len(batches),
             "query_fraction": qf,
             "inserts": total_ins, "queries": total_q,
@@ -832,12 +866,13 @@ def bench_incremental(args, cc, synth, dev, qf):
                        "p50_ms": round(pct(lat_srv, 50), 4), "p99_ms": round(pct(lat_srv, 99), 4),
                        "wall_s": round(wall_srv, 4), "plain_wall_s": round(wall, 4),
                        "speedup_vs_plain": round(wall / wall_srv, 3),
-                       "answers_equal_plain_every_batch": same_all and same_pace and same_zc,
-                       "staging": "copy engines (requests staged through 4 device slots of 2^22 pairs)",
-                       "zero_copy": {"ops_per_s": round((total_ins + total_q) / wall_zc, 1),
-                                     "p50_ms": round(pct(lat_zc, 50), 4), "p99_ms": round(pct(lat_zc, 99), 4),
-                                     "wall_s": round(wall_zc, 4),
-                                     "note": "kernels read the pinned requests in place over the host link"},
+                       "answers_equal_plain_every_batch": same_all and same_pace and same_st,
+                       "transfer": "kernels read the pinned requests in place over the host link",
+                       "staged": {"ops_per_s": round((total_ins + total_q) / wall_st, 1),
+                                  "p50_ms": round(pct(lat_st, 50), 4), "p99_ms": round(pct(lat_st, 99), 4),
+                                  "wall_s": round(wall_st, 4),
+                                  "note": "every request copied through 4 device slots of 2^22 pairs by the copy "
+                                          "engines (CC_SERVER_STAGE)"},
                        "latency": "submit to answers in host memory, all batches submitted back to back",
                        "paced": {"interval_ms": round(1e3 * wall / len(batches), 4),
                                  "p50_ms": round(pct(lat_pace, 50), 4), "p99_ms": round(pct(lat_pace, 99), 4),

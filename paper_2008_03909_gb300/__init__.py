@@ -595,13 +595,13 @@ class Server:
     """Continuous-batching request loop over an Incremental handle.  Host
     tensors (pinned for overlap) are kept alive until wait()."""
 
-    ZERO_COPY = 1
+    STAGE = 1
 
-    def __init__(self, inc: "Incremental", slots: int = 4, slot_pairs: int = 1 << 22, zero_copy: bool = False):
+    def __init__(self, inc: "Incremental", slots: int = 4, slot_pairs: int = 1 << 22, stage: bool = False):
         self._s = ctypes.c_void_p(0)
         self._keep = {}
         self.inc = inc
-        opt = ServerOpt(slots, self.ZERO_COPY if zero_copy else 0, slot_pairs)
+        opt = ServerOpt(slots, self.STAGE if stage else 0, slot_pairs)
         _check(lib().cc_server_create(inc._h, ctypes.byref(opt), ctypes.byref(self._s)), "cc_server_create")
 
     def submit(self, inserts: torch.Tensor | None, queries: torch.Tensor | None, answers: torch.Tensor | None = None):

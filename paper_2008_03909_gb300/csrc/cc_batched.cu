@@ -37,13 +37,15 @@ struct ParS {
     __device__ __forceinline__ uint32_t cas(uint32_t i, uint32_t c, uint32_t v) const {
         return atomicCAS(reinterpret_cast<unsigned short *>(s + i), (unsigned short)c, (unsigned short)v);
     }
-    __device__ __forceinline__ void set(uint32_t i, uint32_t v) const { s[i] = (uint16_t)v; }
+    __device__ __forceinline__ void set(uint32_t i, uint32_t v) const {
+        reinterpret_cast<volatile uint16_t *>(s)[i] = (uint16_t)v;
+    }
 };
 struct ParG {
     uint32_t *g;
     __device__ __forceinline__ uint32_t ld(uint32_t i) const { return reinterpret_cast<volatile uint32_t *>(g)[i]; }
     __device__ __forceinline__ uint32_t cas(uint32_t i, uint32_t c, uint32_t v) const { return atomicCAS(g + i, c, v); }
-    __device__ __forceinline__ void set(uint32_t i, uint32_t v) const { g[i] = v; }
+    __device__ __forceinline__ void set(uint32_t i, uint32_t v) const { reinterpret_cast<volatile uint32_t *>(g)[i] = v; }
 };
 struct ParH {
     uint16_t *s;
@@ -57,12 +59,18 @@ struct ParH {
                      : atomicCAS(g + i, c, v);
     }
     __device__ __forceinline__ void set(uint32_t i, uint32_t v) const {
-        if (i < S) s[i] = (uint16_t)v;
-        else g[i] = v;
+        if (i < S) reinterpret_cast<volatile uint16_t *>(s)[i] = (uint16_t)v;
+        else reinterpret_cast<volatile uint32_t *>(g)[i] = v;
     }
 };
 
-// Rem-CAS union (Algorithm 14 with SplitAtomicOne) on a parent array.
+// Rem-CAS union (Algorithm 14) on a parent array, splitting the walked
+// path as it goes (SplitOne).  The root link is a CAS; a split is a plain
+// store: it writes into a non-root an ancestor of it, and a non-root only
+// ever gains ancestors, so any interleaving of such stores leaves a valid
+// forest over the same sets (the CAS of SplitAtomicOne is needed only
+// where a root may be overwritten).  Plain stores keep the shared-memory
+// atomics to the links alone.
 template <class Par>
 __device__ __forceinline__ void unite_any(const Par &P, uint32_t u, uint32_t v, const Dev &d) {
     uint32_t ru = u, rv = v, pru = P.ld(ru), prv = P.ld(rv);
@@ -78,7 +86,7 @@ __device__ __forceinline__ void unite_any(const Par &P, uint32_t u, uint32_t v, 
             pru = old;
         } else {
             uint32_t w = P.ld(pru);
-            if (pru != w) P.cas(ru, pru, w);
+            if (pru != w) P.set(ru, w);
             ru = pru;
             pru = w;
         }

@@ -703,23 +703,29 @@ __device__ __forceinline__ void write_chunks(ChunkRef *chunks, uint64_t cap, uin
     for (uint32_t c = 0; c < nc; ++c) chunks[slot + c] = ChunkRef{u, c};
 }
 
-// Chunk-list slots reserved by a warp in runs of at least WARP_RES: one
-// global atomic per run instead of one per warp step that has a heavy
-// vertex (a single counter hit by every warp step serialised at the L2).
-// Slots of a run that stay unused are filled with empty chunks (u = NONE)
-// when the warp takes a new run or finishes (close()), and the chunk pass
-// skips them.  A grid leaves at most WARP_RES - 1 empty slots per warp,
-// which CHUNK_SLACK covers (64 warps per SM, up to 256 SMs).
+// Chunk-list slots reserved by a warp in runs: one global atomic per run
+// instead of one per warp step that has a heavy vertex (a single counter
+// hit by every warp step serialised at the L2).  A warp's first run is
+// exactly what it needs; each later run doubles, up to WARP_RES, so a warp
+// that appends once leaves no gap and one that appends often takes few
+// atomics.  Slots of a run that stay unused are filled with empty chunks
+// (u = NONE) when the warp takes a new run or finishes (close()), and the
+// chunk pass skips them.  A grid leaves at most WARP_RES - 1 empty slots
+// per warp, which CHUNK_SLACK covers (64 warps per SM, up to 256 SMs).
 constexpr uint32_t WARP_RES = 64;
 constexpr uint64_t CHUNK_SLACK = 64ull * 256 * WARP_RES;
 
 struct WarpSlots {
     uint64_t cur = 0, end = 0;   // warp-uniform
+    uint32_t run = 0;            // size of the last run (warp-uniform)
     // every lane calls with the same total; returns the warp's first slot
     __device__ __forceinline__ uint64_t take(uint32_t *counter, uint32_t total, ChunkRef *chunks, uint64_t cap) {
         if (cur + total > end) {
             close(chunks, cap);
-            const uint32_t want = total > WARP_RES ? total : WARP_RES;
+            uint32_t grow = run ? 2 * run : 0;
+            grow = grow > WARP_RES ? WARP_RES : grow;
+            const uint32_t want = total > grow ? total : grow;
+            run = want;
             uint32_t b = 0;
             if ((threadIdx.x & 31) == 0) b = atomicAdd(counter, want);
             b = __shfl_sync(0xFFFFFFFFu, b, 0);

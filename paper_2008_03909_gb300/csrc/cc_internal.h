@@ -76,6 +76,15 @@ class Scratch {
     cudaStream_t stream_ = nullptr;
 };
 
+// Degree statistics of a graph for the selector's features: sum and sum
+// of squares of the degrees, counts of degree 0, 1, 2, 3..16 and > 64, the
+// edges at vertices of degree > 64, and the highest degree (key
+// deg << 32 | ~v: ties to the smallest vertex).
+struct FeatStats {
+    unsigned long long sum_deg, cnt[5], edges_gt64, maxkey;
+    double sum_deg2;
+};
+
 // Control block of one call, in device memory.
 struct Ctl {
     uint32_t nchunks;
@@ -99,7 +108,7 @@ struct Ctl {
     unsigned long long steps;          // k-out fused pass: parent steps walked by its compression
     uint32_t sel_class;                // selected path: the chosen class
     uint32_t skip;                     // selected path: 1 when the default finish must not run
-    uint32_t pad[2];
+    FeatStats fs;                      // selected path: degree statistics (first k-out pass)
 };
 
 // Launch accounting: one scope per kernel launch.  Counts every launch and,

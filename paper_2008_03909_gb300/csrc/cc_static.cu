@@ -124,16 +124,8 @@ __global__ void __launch_bounds__(256, 8) k_shortcut(uint32_t *P, uint32_t *prev
 }
 
 // ---------------------------------------------------------------- degree statistics
-// Degree statistics of the graph for the selector's features, gathered by
-// a pass that reads every vertex's offsets anyway (the first k-out pass, or
-// a pass of their own): sum and sum of squares of the degrees, counts of
-// degree 0, 1, 2, 3..16 and > 64, the edges at vertices of degree > 64, and
-// the highest degree (key deg << 32 | ~v: ties to the smallest vertex).
-struct FeatStats {
-    unsigned long long sum_deg, cnt[5], edges_gt64, maxkey;
-    double sum_deg2;
-};
-
+// The degree statistics (FeatStats) gathered by the first k-out pass,
+// which reads every vertex's offsets anyway.
 struct DegStats {
     unsigned long long sd = 0, sd2 = 0, c0 = 0, c1 = 0, c2 = 0, c3 = 0, c4 = 0, e64 = 0, mk = 0;
     __device__ __forceinline__ void add(uint64_t deg, uint32_t v) {
@@ -148,8 +140,14 @@ struct DegStats {
         const unsigned long long key = ((deg < 0xFFFFFFFFull ? deg : 0xFFFFFFFFull) << 32) | (uint32_t)~v;
         mk = key > mk ? key : mk;
     }
-    // every lane of the warp calls this; one set of atomics per warp
+    // every thread of the block calls this once (it synchronises): warp
+    // sums, then block sums in shared memory, then one set of global
+    // atomics per block (one set per warp on the same nine words serialised
+    // at the L2 and cost more than the pass itself on small graphs)
     __device__ __forceinline__ void flush(FeatStats *st) {
+        __shared__ unsigned long long bs[9];
+        if (threadIdx.x < 9) bs[threadIdx.x] = 0;
+        __syncthreads();
         unsigned long long c[5] = {c0, c1, c2, c3, c4};
         for (int o = 16; o > 0; o >>= 1) {
             sd += __shfl_xor_sync(0xFFFFFFFFu, sd, o);
@@ -160,11 +158,19 @@ struct DegStats {
             mk = y > mk ? y : mk;
         }
         if ((threadIdx.x & 31) == 0) {
-            atomicAdd(&st->sum_deg, sd);
-            atomicAdd(&st->sum_deg2, (double)sd2);
-            atomicAdd(&st->edges_gt64, e64);
-            for (int j = 0; j < 5; ++j) atomicAdd(&st->cnt[j], c[j]);
-            atomicMax(&st->maxkey, mk);
+            atomicAdd(&bs[0], sd);
+            atomicAdd(&bs[1], sd2);
+            atomicAdd(&bs[2], e64);
+            for (int j = 0; j < 5; ++j) atomicAdd(&bs[3 + j], c[j]);
+            atomicMax(&bs[8], mk);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            atomicAdd(&st->sum_deg, bs[0]);
+            atomicAdd(&st->sum_deg2, (double)bs[1]);
+            atomicAdd(&st->edges_gt64, bs[2]);
+            for (int j = 0; j < 5; ++j) atomicAdd(&st->cnt[j], bs[3 + j]);
+            atomicMax(&st->maxkey, bs[8]);
         }
     }
 };
@@ -329,7 +335,7 @@ __global__ void __launch_bounds__(256, 8) k_kout_hook_first(const OffT *I, const
                 ++slot;
             }
     }
-    if (STATS) ds.flush(fs);
+    if (STATS) ds.flush(fs);   // block-wide (every thread reaches it)
     __syncthreads();
     if (threadIdx.x == 0) dcount[blockIdx.x] = nblk < cap_blk ? nblk : cap_blk;
 }
@@ -2023,9 +2029,10 @@ cc_status sample_phase(const Graph &g, const cc_sample_opt &so, const cc_finish_
         }
         if (so.k > 1) {
             // full compression between the rounds: without it the second
-            // round's unions walk the first round's uncompressed chains, which
-            // measured 20x slower than this pass (5.3 against 0.25 ms at
-            // R-MAT scale 26)
+            // round's unions walk the first round's uncompressed chains
+            // through L2 (folding the compression into the second round's
+            // pass measured 2.4 against 0.5 ms for the two at R-MAT scale
+            // 26); it also clears the count array
             {
                 CC_PROF("k_compress_mid", s);
                 k_shortcut<false><<<gv, TPB, 0, s>>>(P, nullptr, g.n, nullptr, d, nullptr, nullptr, count_into);
@@ -2536,20 +2543,18 @@ cc_status run_select(const Graph &g, const float *params, int force, uint64_t se
     // SV / LT-PRF on the same sample need the round-start copy
     w.has_sv = true;
     w.o_prev = w.sc.reserve((size_t)g.n * 4);
-    const size_t o_fs = w.sc.reserve(sizeof(FeatStats));
     cc_status st = w.sc.alloc(s);
     if (st != CC_OK) return st;
     SelHost *h = nullptr;
     if (!features_only && (st = sel_host(di, &h)) != CC_OK) return st;
-    w.fs = w.sc.at<FeatStats>(o_fs);
+    w.fs = &w.ctl()->fs;
     w.select = true;
     w.sel_params = features_only ? nullptr : params;
     w.sel_force = features_only ? -1 : force;
     w.sel_feat = feat_out;
     w.sel_host = h ? h->dword : nullptr;
     w.sel_m = g.m;
-    CC_TRY(cudaMemsetAsync(w.ctl(), 0, sizeof(Ctl), s));
-    CC_TRY(cudaMemsetAsync(w.fs, 0, sizeof(FeatStats), s));
+    CC_TRY(cudaMemsetAsync(w.ctl(), 0, sizeof(Ctl), s));   // the degree statistics too
     int32_t info = 0;
     if ((st = sample_phase<OffT>(g, so, fo, P, w, di, d, s, &info, w.sc.at<uint32_t>(w.o_counts))) != CC_OK)
         return st;

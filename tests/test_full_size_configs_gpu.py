@@ -101,11 +101,11 @@ def test_served_workload_plain_handle_equals_oracle(served):
     assert cc.device_error() == 0
 
 
-@pytest.mark.parametrize("pinned,zero_copy", [(True, False), (True, True), (False, False)])
-def test_served_workload_request_loop_equals_oracle(served, pinned, zero_copy):
+@pytest.mark.parametrize("pinned,stage", [(True, False), (True, True), (False, False)])
+def test_served_workload_request_loop_equals_oracle(served, pinned, stage):
     base, batches, want, want_labels = served
     inc = cc.Incremental(base.n, base.offsets, base.edges)
-    srv = cc.Server(inc, slots=4, slot_pairs=1 << 22, zero_copy=zero_copy)
+    srv = cc.Server(inc, slots=4, slot_pairs=1 << 22, stage=stage)
     reqs = [(i.pin_memory(), q.pin_memory()) if pinned else (i, q) for i, q in batches]
     outs = [torch.empty(max(1, q.numel() // 2), dtype=torch.uint8) for _, q in reqs]
     if pinned:

@@ -39,9 +39,9 @@ def oracle_replay(base, reqs):
     return out, inc.labels()
 
 
-def new_server(base, slots, slot_pairs, zero_copy=False):
+def new_server(base, slots, slot_pairs, stage=False):
     inc = cc.Incremental(base.n, base.offsets.cuda(), base.edges.cuda())
-    return inc, cc.Server(inc, slots=slots, slot_pairs=slot_pairs, zero_copy=zero_copy)
+    return inc, cc.Server(inc, slots=slots, slot_pairs=slot_pairs, stage=stage)
 
 
 @pytest.fixture(scope="module")
@@ -52,11 +52,11 @@ def setup():
     return base, reqs, want, want_labels
 
 
-@pytest.mark.parametrize("zero_copy", [False, True])
+@pytest.mark.parametrize("stage", [False, True])
 @pytest.mark.parametrize("slots,slot_pairs", [(1, 1 << 20), (3, 4096), (8, 777)])
-def test_all_at_once_matches_oracle(setup, slots, slot_pairs, zero_copy):
+def test_all_at_once_matches_oracle(setup, slots, slot_pairs, stage):
     base, reqs, want, want_labels = setup
-    inc, srv = new_server(base, slots, slot_pairs, zero_copy)
+    inc, srv = new_server(base, slots, slot_pairs, stage)
     tickets = [srv.submit(i, q) for i, q in reqs]
     for t, w in zip(tickets, want):
         ans, lat = srv.wait(t)
