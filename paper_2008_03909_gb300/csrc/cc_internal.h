@@ -108,7 +108,9 @@ struct Ctl {
     unsigned long long steps;          // k-out fused pass: parent steps walked by its compression
     uint32_t sel_class;                // selected path: the chosen class
     uint32_t skip;                     // selected path: 1 when the default finish must not run
-    FeatStats fs;                      // selected path: degree statistics (first k-out pass)
+    unsigned long long gcount;         // k-out fused pass: non-roots under the L_max guess
+    uint32_t fallback;                 // 1 when the guess holds no majority (labels counted in full)
+    uint32_t pad[1];
 };
 
 // Launch accounting: one scope per kernel launch.  Counts every launch and,

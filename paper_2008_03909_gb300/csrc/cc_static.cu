@@ -141,10 +141,11 @@ struct DegStats {
         mk = key > mk ? key : mk;
     }
     // every thread of the block calls this once (it synchronises): warp
-    // sums, then block sums in shared memory, then one set of global
-    // atomics per block (one set per warp on the same nine words serialised
-    // at the L2 and cost more than the pass itself on small graphs)
-    __device__ __forceinline__ void flush(FeatStats *st) {
+    // sums, then block sums in shared memory, written with plain stores to
+    // this block's slot of part[] (the consumer adds the slots up; global
+    // atomics from every block on the same nine words serialised at the L2
+    // and cost more than the pass itself)
+    __device__ __forceinline__ void flush(FeatStats *part) {
         __shared__ unsigned long long bs[9];
         if (threadIdx.x < 9) bs[threadIdx.x] = 0;
         __syncthreads();
@@ -166,11 +167,12 @@ struct DegStats {
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            atomicAdd(&st->sum_deg, bs[0]);
-            atomicAdd(&st->sum_deg2, (double)bs[1]);
-            atomicAdd(&st->edges_gt64, bs[2]);
-            for (int j = 0; j < 5; ++j) atomicAdd(&st->cnt[j], bs[3 + j]);
-            atomicMax(&st->maxkey, bs[8]);
+            FeatStats &f = part[blockIdx.x];
+            f.sum_deg = bs[0];
+            f.sum_deg2 = (double)bs[1];
+            f.edges_gt64 = bs[2];
+            for (int j = 0; j < 5; ++j) f.cnt[j] = bs[3 + j];
+            f.maxkey = bs[8];
         }
     }
 };
@@ -385,7 +387,9 @@ __global__ void __launch_bounds__(256, 8) k_kout_apply_pick(const uint32_t *pick
 // (ties to the smallest) is unchanged when only non-root vertices are
 // counted; with none, every root ties at 1 and the answer is root 0.
 template <bool FLAT>
-__global__ void __launch_bounds__(256, 8) k_count_labels(const uint32_t *L, uint32_t n, uint32_t *cnt, Dev d) {
+__global__ void __launch_bounds__(256, 8) k_count_labels(const uint32_t *L, uint32_t n, uint32_t *cnt, Dev d,
+                                                          const uint32_t *only_if = nullptr) {
+    if (only_if && *only_if == 0) return;
     const uint64_t n4 = (reinterpret_cast<uintptr_t>(L) & 15) == 0 ? n / 4 : 0;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
@@ -423,7 +427,9 @@ __device__ __forceinline__ void keep_max(unsigned long long &best, uint32_t c, u
     }
 }
 
-__global__ void __launch_bounds__(256, 8) k_argmax_counts(const uint32_t *cnt, uint32_t n, unsigned long long *key) {
+__global__ void __launch_bounds__(256, 8) k_argmax_counts(const uint32_t *cnt, uint32_t n, unsigned long long *key,
+                                                           const uint32_t *only_if = nullptr) {
+    if (only_if && *only_if == 0) return;
     __shared__ unsigned long long s[32];
     unsigned long long best = 0;
     const uint64_t n4 = (reinterpret_cast<uintptr_t>(cnt) & 15) == 0 ? n / 4 : 0;
@@ -480,14 +486,14 @@ __global__ void k_freq_sampled(const uint32_t *L, uint32_t n, uint32_t S, uint64
 }
 
 // ---------------------------------------------------------------- fused k-out binning
-// A guess of L_max before the exact count: the most frequent root among 256
+// A guess of L_max before the exact count: the most frequent root among 128
 // seeded vertices that have an edge (ties to the smallest root), each root
 // found by walking the not yet compressed forest (at most 64 steps; a walk
-// that stops early just gives a worse guess).  One block of 256 threads.
+// that stops early just gives a worse guess).  One block of 128 threads.
 // The guess only decides which vertices the fused binning treats as
 // candidates; the exact L_max is checked against it afterwards.
 constexpr uint64_t TAG_GUESS = 0x67756573ull;
-__global__ void __launch_bounds__(256) k_guess_lmax(const uint32_t *P, const uint32_t *nz, uint32_t n, uint64_t seed,
+__global__ void __launch_bounds__(128) k_guess_lmax(const uint32_t *P, const uint32_t *nz, uint32_t n, uint64_t seed,
                                                     Ctl *ctl) {
     // the fused pass appends and counts from zero
     if (threadIdx.x == 0) {
@@ -498,9 +504,10 @@ __global__ void __launch_bounds__(256) k_guess_lmax(const uint32_t *P, const uin
         ctl->rebin = 0;
         ctl->nonroots = 0;
         ctl->steps = 0;
+        ctl->gcount = 0;
     }
-    __shared__ uint32_t lab[256];
-    __shared__ unsigned long long red[8];
+    __shared__ uint32_t lab[128];
+    __shared__ unsigned long long red[4];
     const uint32_t t = threadIdx.x;
     const uint32_t v = (uint32_t)(draw64(seed ^ TAG_GUESS, t) % n);
     uint32_t r = NONE;
@@ -517,14 +524,14 @@ __global__ void __launch_bounds__(256) k_guess_lmax(const uint32_t *P, const uin
     unsigned long long best = 0;
     if (r != NONE) {
         uint32_t c = 0;
-        for (int j = 0; j < 256; ++j) c += lab[j] == r;
+        for (int j = 0; j < 128; ++j) c += lab[j] == r;
         best = ((unsigned long long)c << 32) | (uint32_t)~r;
     }
     best = warp_max_u64(best);
     if ((t & 31) == 0) red[t >> 5] = best;
     __syncthreads();
     if (t == 0) {
-        for (int w = 1; w < 8; ++w) best = red[w] > best ? red[w] : best;
+        for (int w = 1; w < 4; ++w) best = red[w] > best ? red[w] : best;
         best = best > red[0] ? best : red[0];
         ctl->guess = best ? ~(uint32_t)(best & 0xFFFFFFFFull) : NONE;
     }
@@ -540,7 +547,7 @@ __global__ void __launch_bounds__(256) k_guess_lmax(const uint32_t *P, const uin
 // and label.  When the exact L_max differs from the guess (k_lmax_check)
 // the lists are rebuilt by k_cand_bin.
 template <typename OffT>
-__global__ void __launch_bounds__(256, 6) k_compress_count_bin(uint32_t *P, uint32_t n, uint32_t *cnt, const OffT *I,
+__global__ void __launch_bounds__(256, 6) k_compress_count_bin(uint32_t *P, uint32_t n, const OffT *I,
                                                                uint64_t m, const uint32_t *nz, Ctl *ctl,
                                                                uint32_t *light, ChunkRef *chunks, uint64_t cap,
                                                                Dev d) {
@@ -550,9 +557,8 @@ __global__ void __launch_bounds__(256, 6) k_compress_count_bin(uint32_t *P, uint
     const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     const uint32_t guess = ctl->guess;
     const int lane = threadIdx.x & 31;
-    LabelCounterArg lc;
     WarpSlots ws;
-    unsigned long long my_edges = 0, my_nonroots = 0;
+    unsigned long long my_edges = 0, my_nonroots = 0, my_guess = 0;
     uint32_t my_steps = 0;
     // whole warps iterate together (the binning's appends are warp-collective)
     const uint64_t n4w = (n4 + 31) / 32 * 32;
@@ -571,8 +577,8 @@ __global__ void __launch_bounds__(256, 6) k_compress_count_bin(uint32_t *P, uint
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 if (x[j] != v0 + j) {
-                    lc.add(cnt, x[j]);
                     ++my_nonroots;
+                    my_guess += x[j] == guess;
                 }
                 if (x[j] != guess && ((bits >> j) & 1u)) {
                     uint64_t b, e;
@@ -614,8 +620,8 @@ __global__ void __launch_bounds__(256, 6) k_compress_count_bin(uint32_t *P, uint
         uint32_t r = find_from<FIND_NAIVE>(P, (uint32_t)v, p, d);
         if (r != p) P[v] = r;
         if (r != v) {
-            lc.add(cnt, r);
             ++my_nonroots;
+            my_guess += r == guess;
         }
         if (r != guess && ((nz[v >> 5] >> (v & 31)) & 1u)) {
             uint64_t b, e;
@@ -634,18 +640,38 @@ __global__ void __launch_bounds__(256, 6) k_compress_count_bin(uint32_t *P, uint
         }
     }
     ws.close(chunks, cap);
-    lc.flush(cnt, &ctl->key);
     unsigned long long my_st = my_steps;
     for (int o = 16; o > 0; o >>= 1) {
         my_edges += __shfl_xor_sync(0xFFFFFFFFu, my_edges, o);
         my_nonroots += __shfl_xor_sync(0xFFFFFFFFu, my_nonroots, o);
+        my_guess += __shfl_xor_sync(0xFFFFFFFFu, my_guess, o);
         my_st += __shfl_xor_sync(0xFFFFFFFFu, my_st, o);
     }
     if (lane == 0) {
         if (my_edges) atomicAdd(&ctl->edges, my_edges);
         if (my_nonroots) atomicAdd(&ctl->nonroots, my_nonroots);
+        if (my_guess) atomicAdd(&ctl->gcount, my_guess);
         if (my_st) atomicAdd(&ctl->steps, my_st);
     }
+}
+
+// Exact L_max without counting every label, when possible: the fused pass
+// counted the non-root vertices under the guess (gcount) and all non-root
+// vertices.  If the guess holds more than half of them, every other root
+// counts less, so the guess is the arg-max (no tie possible) and its key is
+// written; otherwise `fallback` is set and the guarded count kernels
+// (k_zero_if, k_count_labels, k_argmax_counts) find the key.
+__global__ void k_lmax_majority(Ctl *ctl) {
+    const unsigned long long gc = ctl->gcount, nr = ctl->nonroots;
+    const bool maj = ctl->guess != NONE && 2 * gc > nr;
+    ctl->fallback = !maj;
+    ctl->key = maj ? ((gc << 32) | (uint32_t)~ctl->guess) : 0ull;
+}
+
+__global__ void __launch_bounds__(256, 8) k_zero_if(uint32_t *a, uint32_t n, const uint32_t *only_if) {
+    if (*only_if == 0) return;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        a[i] = 0;
 }
 
 // L_max from the arg-max key; when it is not the guess the fused binning
@@ -667,45 +693,58 @@ __global__ void k_lmax_check(Ctl *ctl, uint32_t *lmax) {
 // The selector's choice inside the default path (k-out + UF-Rem-CAS): the
 // L_max check of k_lmax_check, then the 16 features from what the default
 // path already computed, then the MLP's class, all in one block of 64
-// threads.  Features (floats): 0 log2(n+1), 1 log2(m+1), 2 m/n, 3
-// log2(max degree+1), 4 degree variance / mean^2, 5-7 fractions of vertices
-// of degree 0, 1, 2, 8 fraction of degree 3..16, 9 fraction of degree > 64,
-// 10 share of edges at vertices of degree > 64, 11 size of L_max's k-out
-// cluster / n, 12 vertices outside their own singleton after k-out / n, 13
-// edges left for the finish / m, 14 light candidate vertices of the finish
-// / n, 15 parent steps per non-root in the last compression (how deep the
-// k-out trees were, a cheap stand-in for the graph's depth).  params null:
-// features only, class 0 (the default).  force >= 0 overrides the class.
-// The class goes to ctl->sel_class and, with rebin in bit 8, to *host_word
-// (mapped host memory, may be null); ctl->skip = class != 0.
-__global__ void __launch_bounds__(64) k_lmax_select(Ctl *ctl, uint32_t *lmax, const FeatStats *fs, uint32_t n,
-                                                    uint64_t m, const float *params, int force, float *feat_out,
-                                                    volatile int *host_word) {
+// threads.  The degree statistics arrive as one partial sum per block of
+// the first k-out pass (part[0..nparts)), added up here in a fixed order.
+// Features (floats): 0 log2(n+1), 1 log2(m+1), 2 m/n, 3 log2(max degree+1),
+// 4 degree variance / mean^2, 5-7 fractions of vertices of degree 0, 1, 2,
+// 8 fraction of degree 3..16, 9 fraction of degree > 64, 10 share of edges
+// at vertices of degree > 64, 11 size of L_max's k-out cluster / n, 12
+// vertices outside their own singleton after k-out / n, 13 edges left for
+// the finish / m, 14 light candidate vertices of the finish / n, 15 parent
+// steps per non-root in the last compression (how deep the k-out trees
+// were, a cheap stand-in for the graph's depth).  params null: features
+// only, class 0 (the default).  force >= 0 overrides the class.  The class
+// goes to ctl->sel_class and, with rebin in bit 8, to *host_word (mapped
+// host memory, may be null); ctl->skip = class != 0.
+__global__ void __launch_bounds__(64) k_lmax_select(Ctl *ctl, uint32_t *lmax, const FeatStats *part,
+                                                    uint32_t nparts, uint32_t n, uint64_t m, const float *params,
+                                                    int force, float *feat_out, volatile int *host_word) {
     __shared__ float xin[MLP_IN], x[MLP_IN], h1[MLP_H], h2[MLP_H], z[MLP_OUT];
+    __shared__ unsigned long long red[2][8];
+    __shared__ double red2[2];
+    __shared__ unsigned long long k_s, nonroots_s, edges_s, nlight_s, steps_s;
     __shared__ uint32_t re_s;
     const int t = threadIdx.x;
+    // degree statistics: thread-strided sums, then the two warps, then smem
+    unsigned long long a[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // sum, cnt[5], e64, max key
+    double a2 = 0.0;
+    for (uint32_t b = t; b < nparts; b += blockDim.x) {
+        const FeatStats &f = part[b];
+        a[0] += f.sum_deg;
+        for (int j = 0; j < 5; ++j) a[1 + j] += f.cnt[j];
+        a[6] += f.edges_gt64;
+        a[7] = f.maxkey > a[7] ? f.maxkey : a[7];
+        a2 += f.sum_deg2;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        for (int j = 0; j < 7; ++j) a[j] += __shfl_xor_sync(0xFFFFFFFFu, a[j], o);
+        const unsigned long long y = __shfl_xor_sync(0xFFFFFFFFu, a[7], o);
+        a[7] = y > a[7] ? y : a[7];
+        a2 += __shfl_xor_sync(0xFFFFFFFFu, a2, o);
+    }
+    if ((t & 31) == 0) {
+        for (int j = 0; j < 8; ++j) red[t >> 5][j] = a[j];
+        red2[t >> 5] = a2;
+    }
     if (t == 0) {
         const unsigned long long k = ctl->key;
         const uint32_t l = k ? ~(uint32_t)(k & 0xFFFFFFFFull) : 0u;
         *lmax = l;
-        const double nn = (double)n, mm = m ? (double)m : 1.0;
-        const double mean = (double)fs->sum_deg / nn;
-        const double var = fs->sum_deg2 / nn - mean * mean;
-        const double nonroots = (double)ctl->nonroots;
-        xin[0] = (float)log2(nn + 1.0);
-        xin[1] = (float)log2((double)m + 1.0);
-        xin[2] = (float)mean;
-        xin[3] = (float)log2((double)(fs->maxkey >> 32) + 1.0);
-        xin[4] = (float)(mean > 0 ? var / (mean * mean) : 0.0);
-        for (int j = 0; j < 3; ++j) xin[5 + j] = (float)(fs->cnt[j] / nn);
-        xin[8] = (float)(fs->cnt[3] / nn);
-        xin[9] = (float)(fs->cnt[4] / nn);
-        xin[10] = (float)(fs->edges_gt64 / mm);
-        xin[11] = (float)(((double)(k >> 32) + 1.0) / nn);
-        xin[12] = (float)(nonroots / nn);
-        xin[13] = (float)((double)ctl->edges / mm);
-        xin[14] = (float)((double)ctl->nlight / nn);
-        xin[15] = (float)((double)ctl->steps / (nonroots > 1.0 ? nonroots : 1.0));
+        k_s = k;
+        nonroots_s = ctl->nonroots;
+        edges_s = ctl->edges;
+        nlight_s = ctl->nlight;
+        steps_s = ctl->steps;
         const bool re = l != ctl->guess;
         ctl->rebin = re;
         re_s = re;
@@ -716,7 +755,38 @@ __global__ void __launch_bounds__(64) k_lmax_select(Ctl *ctl, uint32_t *lmax, co
         }
     }
     __syncthreads();
-    if (feat_out && t < MLP_IN) feat_out[t] = xin[t];
+    if (t < MLP_IN) {
+        const float nn = (float)n, mm = m ? (float)m : 1.f;
+        const unsigned long long sd = red[0][0] + red[1][0];
+        const float mean = (float)sd / nn;
+        float v = 0.f;
+        switch (t) {
+            case 0: v = log2f(nn + 1.f); break;
+            case 1: v = log2f((float)m + 1.f); break;
+            case 2: v = mean; break;
+            case 3: {
+                const unsigned long long mk = red[0][7] > red[1][7] ? red[0][7] : red[1][7];
+                v = log2f((float)(mk >> 32) + 1.f);
+                break;
+            }
+            case 4: {   // in double: the difference cancels on regular graphs
+                const double md = (double)sd / (double)n, var = (red2[0] + red2[1]) / (double)n - md * md;
+                v = md > 0.0 ? (float)(var / (md * md)) : 0.f;
+                break;
+            }
+            case 5: case 6: case 7: case 8: case 9:
+                v = (float)(red[0][t - 4] + red[1][t - 4]) / nn; break;
+            case 10: v = (float)(red[0][6] + red[1][6]) / mm; break;
+            case 11: v = ((float)(k_s >> 32) + 1.f) / nn; break;
+            case 12: v = (float)nonroots_s / nn; break;
+            case 13: v = (float)edges_s / mm; break;
+            case 14: v = (float)nlight_s / nn; break;
+            default: v = (float)steps_s / (nonroots_s > 1 ? (float)nonroots_s : 1.f); break;
+        }
+        xin[t] = v;
+        if (feat_out) feat_out[t] = v;
+    }
+    __syncthreads();
     int cls = 0;
     if (params) {
         mlp_forward_one(params, xin, x, h1, h2, z);
@@ -1549,7 +1619,8 @@ struct Work {
     size_t o_nz = 0;
     // the selected path: degree statistics gathered by the first k-out pass
     // and the choice made where L_max is checked (k_lmax_select)
-    FeatStats *fs = nullptr;
+    FeatStats *fs = nullptr;   // one partial per block of the first k-out pass
+    uint32_t fs_parts = 0;
     bool select = false;
     const float *sel_params = nullptr;
     int sel_force = -1;
@@ -2035,7 +2106,7 @@ cc_status sample_phase(const Graph &g, const cc_sample_opt &so, const cc_finish_
             // 26); it also clears the count array
             {
                 CC_PROF("k_compress_mid", s);
-                k_shortcut<false><<<gv, TPB, 0, s>>>(P, nullptr, g.n, nullptr, d, nullptr, nullptr, count_into);
+                k_shortcut<false><<<gv, TPB, 0, s>>>(P, nullptr, g.n, nullptr, d);
             }
             if (pick1) {
                 CC_PROF("k_kout_apply_pick", s);
@@ -2051,19 +2122,18 @@ cc_status sample_phase(const Graph &g, const cc_sample_opt &so, const cc_finish_
             Ctl *ctl = w.ctl();
             {
                 CC_PROF("k_guess_lmax", s);
-                k_guess_lmax<<<1, 256, 0, s>>>(P, nz, g.n, so.seed, ctl);
+                k_guess_lmax<<<1, 128, 0, s>>>(P, nz, g.n, so.seed, ctl);
             }
             CC_PROF("k_compress_count", s);
             k_compress_count_bin<OffT><<<grid_for(di, g.n, TPB, 6), TPB, 0, s>>>(
-                P, g.n, count_into, I, g.m, nz, ctl, w.sc.at<uint32_t>(w.o_light),
+                P, g.n, I, g.m, nz, ctl, w.sc.at<uint32_t>(w.o_light),
                                                           w.sc.at<ChunkRef>(w.o_chunks), w.chunk_cap, d);
             w.lists_built = true;
         } else if (count_into) {
             // the arg-max key is taken as the compression counts (identify
-            // then only converts it); with k > 1 the mid-round compression
-            // cleared the count array
+            // then only converts it)
             uint32_t *cnt = count_into;
-            if (so.k <= 1) CC_TRY(cudaMemsetAsync(cnt, 0, (size_t)g.n * 4, s));
+            CC_TRY(cudaMemsetAsync(cnt, 0, (size_t)g.n * 4, s));
             CC_TRY(cudaMemsetAsync(&w.ctl()->key, 0, 8, s));
             CC_PROF("k_compress_count", s);
             k_shortcut<true><<<gv, TPB, 0, s>>>(P, nullptr, g.n, cnt, d, &w.ctl()->key);
@@ -2092,7 +2162,8 @@ cc_status identify_phase(const uint32_t *L, uint32_t n, uint32_t samples, uint64
     Ctl *ctl = w.ctl();
     const unsigned gv = grid_for(di, n, TPB);
     // counted: the compression that counted also left the arg-max key
-    if (!counted) {
+    // (the fused k-out pass: counted below, from its guess)
+    if (!counted && !w.lists_built) {
         CC_TRY(cudaMemsetAsync(cnt, 0, (size_t)n * 4, s));
         {
             CC_PROF("k_count_labels", s);
@@ -2103,11 +2174,26 @@ cc_status identify_phase(const uint32_t *L, uint32_t n, uint32_t samples, uint64
         CC_PROF("k_argmax_counts", s);
         k_argmax_counts<<<gv, TPB, 0, s>>>(cnt, n, &ctl->key);
     }
+    if (w.lists_built) {
+        // exact L_max: the guess when it holds a majority of the non-roots,
+        // else a full count (guarded kernels, returning at once otherwise)
+        {
+            CC_PROF("k_lmax_majority", s);
+            k_lmax_majority<<<1, 1, 0, s>>>(ctl);
+        }
+        {
+            CC_PROF("k_count_fallback", s);
+            k_zero_if<<<gv, TPB, 0, s>>>(cnt, n, &ctl->fallback);
+            k_count_labels<true><<<gv, TPB, 0, s>>>(L, n, cnt, d, &ctl->fallback);
+            k_argmax_counts<<<gv, TPB, 0, s>>>(cnt, n, &ctl->key, &ctl->fallback);
+        }
+        CC_LAUNCH();
+    }
     if (w.lists_built && w.select) {
         // the check plus the selector's features and choice
         CC_PROF("k_lmax_select", s);
-        k_lmax_select<<<1, MLP_H, 0, s>>>(ctl, lmax_out, w.fs, n, w.sel_m, w.sel_params, w.sel_force, w.sel_feat,
-                                          w.sel_host);
+        k_lmax_select<<<1, MLP_H, 0, s>>>(ctl, lmax_out, w.fs, w.fs_parts, n, w.sel_m, w.sel_params, w.sel_force,
+                                          w.sel_feat, w.sel_host);
     } else if (w.lists_built) {
         // the fused k-out pass binned against a guess: check it
         CC_PROF("k_lmax_check", s);
@@ -2543,18 +2629,21 @@ cc_status run_select(const Graph &g, const float *params, int force, uint64_t se
     // SV / LT-PRF on the same sample need the round-start copy
     w.has_sv = true;
     w.o_prev = w.sc.reserve((size_t)g.n * 4);
+    // the first k-out pass runs grid_for(n) blocks, one partial each
+    w.fs_parts = grid_for(di, g.n, TPB);
+    const size_t o_fs = w.sc.reserve((size_t)w.fs_parts * sizeof(FeatStats));
     cc_status st = w.sc.alloc(s);
     if (st != CC_OK) return st;
     SelHost *h = nullptr;
     if (!features_only && (st = sel_host(di, &h)) != CC_OK) return st;
-    w.fs = &w.ctl()->fs;
+    w.fs = w.sc.at<FeatStats>(o_fs);
     w.select = true;
     w.sel_params = features_only ? nullptr : params;
     w.sel_force = features_only ? -1 : force;
     w.sel_feat = feat_out;
     w.sel_host = h ? h->dword : nullptr;
     w.sel_m = g.m;
-    CC_TRY(cudaMemsetAsync(w.ctl(), 0, sizeof(Ctl), s));   // the degree statistics too
+    CC_TRY(cudaMemsetAsync(w.ctl(), 0, sizeof(Ctl), s));
     int32_t info = 0;
     if ((st = sample_phase<OffT>(g, so, fo, P, w, di, d, s, &info, w.sc.at<uint32_t>(w.o_counts))) != CC_OK)
         return st;
