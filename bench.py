@@ -850,6 +850,7 @@ def bench_incremental(args, cc, synth, dev, qf):
         inc2.close()
         return w, lats, same
 
+    served(0.0)   # warm-up: the first request loop of a process pays one-time costs
     wall_srv, lat_srv, same_all = served(0.0)
     wall_pace, lat_pace, same_pace = served(wall / len(batches))
     wall_st, lat_st, same_st = served(0.0, stage=True)

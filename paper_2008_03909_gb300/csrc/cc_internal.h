@@ -110,7 +110,7 @@ struct Ctl {
     uint32_t skip;                     // selected path: 1 when the default finish must not run
     unsigned long long gcount;         // k-out fused pass: non-roots under the L_max guess
     uint32_t fallback;                 // 1 when the guess holds no majority (labels counted in full)
-    uint32_t pad[1];
+    uint32_t stats_done;               // selected path: blocks of k_degree_stats done
 };
 
 // Launch accounting: one scope per kernel launch.  Counts every launch and,

@@ -124,8 +124,8 @@ __global__ void __launch_bounds__(256, 8) k_shortcut(uint32_t *P, uint32_t *prev
 }
 
 // ---------------------------------------------------------------- degree statistics
-// The degree statistics (FeatStats) gathered by the first k-out pass,
-// which reads every vertex's offsets anyway.
+// The degree statistics (FeatStats) of the selector's features, gathered
+// by k_degree_stats on a second stream while the k-out sample runs.
 struct DegStats {
     unsigned long long sd = 0, sd2 = 0, c0 = 0, c1 = 0, c2 = 0, c3 = 0, c4 = 0, e64 = 0, mk = 0;
     __device__ __forceinline__ void add(uint64_t deg, uint32_t v) {
@@ -176,6 +176,41 @@ struct DegStats {
         }
     }
 };
+
+// One pass over the offsets: each block's partial sums go to its slot of
+// part[] (plain stores); the last block to finish (a counter in done[0])
+// adds the slots up in slot order into part[nparts] and resets the counter.
+template <typename OffT>
+__global__ void __launch_bounds__(256, 4) k_degree_stats(const OffT *I, uint32_t n, uint64_t m, FeatStats *part,
+                                                         uint32_t *done, Dev d) {
+    DegStats ds;
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n; v += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t b, e;
+        vertex_range(I, (uint32_t)v, m, b, e, d);
+        ds.add(e - b, (uint32_t)v);
+    }
+    ds.flush(part);
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x == 0) {
+        FeatStats t{};
+        const volatile FeatStats *vp = part;
+        for (uint32_t b = 0; b < gridDim.x; ++b) {
+            t.sum_deg += vp[b].sum_deg;
+            for (int j = 0; j < 5; ++j) t.cnt[j] += vp[b].cnt[j];
+            t.edges_gt64 += vp[b].edges_gt64;
+            t.maxkey = vp[b].maxkey > t.maxkey ? vp[b].maxkey : t.maxkey;
+            t.sum_deg2 += vp[b].sum_deg2;
+        }
+        part[gridDim.x] = t;
+        *done = 0;
+    }
+}
 
 // ---------------------------------------------------------------- k-out
 // Algorithm 4: each vertex of degree > 0 picks its first edge and k-1
@@ -252,15 +287,12 @@ void launch_kout(unsigned grid, cudaStream_t s, const OffT *I, const uint32_t *A
 // serialised (about 2 ns each, 0.5M of them at RMAT-26: most of the
 // kernel's time).  A block's warp steps hold at most cap_blk vertices, so
 // its region cannot overflow (checked, flagged).
-// STATS: also gather the degree statistics into *fs (the selector's
-// features; the offsets are read here anyway).
-template <typename OffT, bool STATS = false>
+template <typename OffT>
 __global__ void __launch_bounds__(256, 8) k_kout_hook_first(const OffT *I, const uint32_t *A, uint32_t n,
                                                             uint64_t m, uint32_t *P, uint2 *defer,
                                                             uint32_t *dcount, uint32_t cap_blk, uint32_t *pick1,
                                                             uint32_t k, uint32_t rule, uint64_t seed, uint32_t *nz,
-                                                            Dev d, FeatStats *fs = nullptr) {
-    DegStats ds;
+                                                            Dev d) {
     __shared__ uint32_t nblk;
     if (threadIdx.x == 0) nblk = 0;
     __syncthreads();
@@ -302,7 +334,6 @@ __global__ void __launch_bounds__(256, 8) k_kout_hook_first(const OffT *I, const
             // without reading their offsets)
             const unsigned has = __ballot_sync(0xFFFFFFFFu, e > b);
             if (nz && lane == 0 && base + 32 * j < n) nz[(base >> 5) + j] = has;
-            if (STATS && v < n) ds.add(e - b, (uint32_t)v);
             // pick 0 (the first edge, or a uniform pick under the pure rule)
             w[j] = e > b ? ld_stream(A + b + kout_offset(rule, seed, v, k, 0, e - b)) : NONE;
             // with k = 2 pick 1 is read here too and kept for the second
@@ -337,7 +368,6 @@ __global__ void __launch_bounds__(256, 8) k_kout_hook_first(const OffT *I, const
                 ++slot;
             }
     }
-    if (STATS) ds.flush(fs);   // block-wide (every thread reaches it)
     __syncthreads();
     if (threadIdx.x == 0) dcount[blockIdx.x] = nblk < cap_blk ? nblk : cap_blk;
 }
@@ -367,8 +397,21 @@ k_kout_defer(uint32_t n, uint32_t *P, const uint2 *defer, const uint32_t *dcount
 // mid-round compression instead.)
 template <class E>
 __global__ void __launch_bounds__(256, 8) k_kout_apply_pick(const uint32_t *pick1, uint32_t n, uint32_t *P, Dev d) {
-    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
-         v += (uint64_t)gridDim.x * blockDim.x) {
+    // four consecutive vertices per thread step (one 16-byte stash load),
+    // their eight parent loads in flight together
+    const uint64_t n4 = (reinterpret_cast<uintptr_t>(pick1) & 15) == 0 ? n / 4 : 0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    for (uint64_t i = tid; i < n4; i += stride) {
+        const uint4 q = __ldcs(reinterpret_cast<const uint4 *>(pick1) + i);
+        const uint32_t v0 = (uint32_t)(4 * i);
+        uint32_t u4[4] = {v0, v0 + 1, v0 + 2, v0 + 3}, w4[4] = {q.x, q.y, q.z, q.w};
+        bool ok[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ok[j] = w4[j] != NONE;
+        unite_pairs<E, 4>(P, u4, w4, ok, d);
+    }
+    for (uint64_t v = 4 * n4 + tid; v < n; v += stride) {
         const uint32_t w = pick1[v];
         uint32_t u1[1] = {(uint32_t)v}, w1[1] = {w};
         bool ok[1] = {w != NONE};
@@ -693,8 +736,8 @@ __global__ void k_lmax_check(Ctl *ctl, uint32_t *lmax) {
 // The selector's choice inside the default path (k-out + UF-Rem-CAS): the
 // L_max check of k_lmax_check, then the 16 features from what the default
 // path already computed, then the MLP's class, all in one block of 64
-// threads.  The degree statistics arrive as one partial sum per block of
-// the first k-out pass (part[0..nparts)), added up here in a fixed order.
+// threads.  The degree statistics come from k_degree_stats (a second
+// stream, joined before this kernel).
 // Features (floats): 0 log2(n+1), 1 log2(m+1), 2 m/n, 3 log2(max degree+1),
 // 4 degree variance / mean^2, 5-7 fractions of vertices of degree 0, 1, 2,
 // 8 fraction of degree 3..16, 9 fraction of degree > 64, 10 share of edges
@@ -706,35 +749,25 @@ __global__ void k_lmax_check(Ctl *ctl, uint32_t *lmax) {
 // only, class 0 (the default).  force >= 0 overrides the class.  The class
 // goes to ctl->sel_class and, with rebin in bit 8, to *host_word (mapped
 // host memory, may be null); ctl->skip = class != 0.
-__global__ void __launch_bounds__(64) k_lmax_select(Ctl *ctl, uint32_t *lmax, const FeatStats *part,
-                                                    uint32_t nparts, uint32_t n, uint64_t m, const float *params,
-                                                    int force, float *feat_out, volatile int *host_word) {
+__global__ void __launch_bounds__(64) k_lmax_select(Ctl *ctl, uint32_t *lmax, const FeatStats *fs, uint32_t n,
+                                                    uint64_t m, const float *params, int force, float *feat_out,
+                                                    volatile int *host_word) {
     __shared__ float xin[MLP_IN], x[MLP_IN], h1[MLP_H], h2[MLP_H], z[MLP_OUT];
     __shared__ unsigned long long red[2][8];
     __shared__ double red2[2];
     __shared__ unsigned long long k_s, nonroots_s, edges_s, nlight_s, steps_s;
     __shared__ uint32_t re_s;
     const int t = threadIdx.x;
-    // degree statistics: thread-strided sums, then the two warps, then smem
-    unsigned long long a[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // sum, cnt[5], e64, max key
-    double a2 = 0.0;
-    for (uint32_t b = t; b < nparts; b += blockDim.x) {
-        const FeatStats &f = part[b];
-        a[0] += f.sum_deg;
-        for (int j = 0; j < 5; ++j) a[1 + j] += f.cnt[j];
-        a[6] += f.edges_gt64;
-        a[7] = f.maxkey > a[7] ? f.maxkey : a[7];
-        a2 += f.sum_deg2;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        for (int j = 0; j < 7; ++j) a[j] += __shfl_xor_sync(0xFFFFFFFFu, a[j], o);
-        const unsigned long long y = __shfl_xor_sync(0xFFFFFFFFu, a[7], o);
-        a[7] = y > a[7] ? y : a[7];
-        a2 += __shfl_xor_sync(0xFFFFFFFFu, a2, o);
-    }
-    if ((t & 31) == 0) {
-        for (int j = 0; j < 8; ++j) red[t >> 5][j] = a[j];
-        red2[t >> 5] = a2;
+    // degree statistics, summed by k_degree_stats's last block
+    if (t == 0) {
+        const FeatStats f = *fs;
+        red[0][0] = f.sum_deg;
+        for (int j = 0; j < 5; ++j) red[0][1 + j] = f.cnt[j];
+        red[0][6] = f.edges_gt64;
+        red[0][7] = f.maxkey;
+        red2[0] = f.sum_deg2;
+        for (int j = 0; j < 8; ++j) red[1][j] = 0;
+        red2[1] = 0.0;
     }
     if (t == 0) {
         const unsigned long long k = ctl->key;
@@ -1619,8 +1652,9 @@ struct Work {
     size_t o_nz = 0;
     // the selected path: degree statistics gathered by the first k-out pass
     // and the choice made where L_max is checked (k_lmax_select)
-    FeatStats *fs = nullptr;   // one partial per block of the first k-out pass
+    FeatStats *fs = nullptr;   // one partial per block of k_degree_stats, then their sum
     uint32_t fs_parts = 0;
+    cudaEvent_t sel_join = nullptr;   // the degree statistics' stream, joined before the choice
     bool select = false;
     const float *sel_params = nullptr;
     int sel_force = -1;
@@ -2087,12 +2121,8 @@ cc_status sample_phase(const Graph &g, const cc_sample_opt &so, const cc_finish_
         uint32_t *nz = fuse ? w.sc.at<uint32_t>(w.o_nz) : nullptr;
         {
             CC_PROF("k_kout_hook_first", s);
-            if (w.fs)
-                k_kout_hook_first<OffT, true><<<gv, TPB, 0, s>>>(I, g.A, g.n, g.m, P, defer, dcount, (uint32_t)cap_blk,
-                                                                 pick1, so.k, so.kout_rule, so.seed, nz, d, w.fs);
-            else
-                k_kout_hook_first<OffT><<<gv, TPB, 0, s>>>(I, g.A, g.n, g.m, P, defer, dcount, (uint32_t)cap_blk,
-                                                           pick1, so.k, so.kout_rule, so.seed, nz, d);
+            k_kout_hook_first<OffT><<<gv, TPB, 0, s>>>(I, g.A, g.n, g.m, P, defer, dcount, (uint32_t)cap_blk, pick1,
+                                                       so.k, so.kout_rule, so.seed, nz, d);
         }
         {
             CC_PROF("k_kout_defer", s);
@@ -2191,9 +2221,10 @@ cc_status identify_phase(const uint32_t *L, uint32_t n, uint32_t samples, uint64
     }
     if (w.lists_built && w.select) {
         // the check plus the selector's features and choice
+        if (w.sel_join) CC_TRY(cudaStreamWaitEvent(s, w.sel_join, 0));
         CC_PROF("k_lmax_select", s);
-        k_lmax_select<<<1, MLP_H, 0, s>>>(ctl, lmax_out, w.fs, w.fs_parts, n, w.sel_m, w.sel_params, w.sel_force,
-                                          w.sel_feat, w.sel_host);
+        k_lmax_select<<<1, MLP_H, 0, s>>>(ctl, lmax_out, w.fs + w.fs_parts, n, w.sel_m, w.sel_params,
+                                          w.sel_force, w.sel_feat, w.sel_host);
     } else if (w.lists_built) {
         // the fused k-out pass binned against a guess: check it
         CC_PROF("k_lmax_check", s);
@@ -2595,6 +2626,8 @@ struct SelHost {
     int *word = nullptr;
     int *dword = nullptr;
     cudaEvent_t ev = nullptr;
+    cudaStream_t side = nullptr;          // the degree statistics run here
+    cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 cc_status sel_host(const DeviceInfo *di, SelHost **out) {
@@ -2604,6 +2637,9 @@ cc_status sel_host(const DeviceInfo *di, SelHost **out) {
         CC_TRY(cudaHostAlloc(reinterpret_cast<void **>(&x.word), 64, cudaHostAllocMapped | cudaHostAllocPortable));
         CC_TRY(cudaHostGetDevicePointer(reinterpret_cast<void **>(&x.dword), x.word, 0));
         CC_TRY(cudaEventCreateWithFlags(&x.ev, cudaEventDisableTiming));
+        CC_TRY(cudaStreamCreateWithFlags(&x.side, cudaStreamNonBlocking));
+        CC_TRY(cudaEventCreateWithFlags(&x.fork, cudaEventDisableTiming));
+        CC_TRY(cudaEventCreateWithFlags(&x.join, cudaEventDisableTiming));
         x.device = di->device;
         h = x;
     }
@@ -2629,21 +2665,32 @@ cc_status run_select(const Graph &g, const float *params, int force, uint64_t se
     // SV / LT-PRF on the same sample need the round-start copy
     w.has_sv = true;
     w.o_prev = w.sc.reserve((size_t)g.n * 4);
-    // the first k-out pass runs grid_for(n) blocks, one partial each
-    w.fs_parts = grid_for(di, g.n, TPB);
-    const size_t o_fs = w.sc.reserve((size_t)w.fs_parts * sizeof(FeatStats));
+    // k_degree_stats runs grid_for(n) blocks, one partial each, plus the sum
+    w.fs_parts = grid_for(di, g.n, TPB, 4);
+    const size_t o_fs = w.sc.reserve((size_t)(w.fs_parts + 1) * sizeof(FeatStats));
     cc_status st = w.sc.alloc(s);
     if (st != CC_OK) return st;
     SelHost *h = nullptr;
-    if (!features_only && (st = sel_host(di, &h)) != CC_OK) return st;
+    if ((st = sel_host(di, &h)) != CC_OK) return st;
     w.fs = w.sc.at<FeatStats>(o_fs);
     w.select = true;
     w.sel_params = features_only ? nullptr : params;
     w.sel_force = features_only ? -1 : force;
     w.sel_feat = feat_out;
-    w.sel_host = h ? h->dword : nullptr;
+    w.sel_host = features_only ? nullptr : h->dword;
     w.sel_m = g.m;
     CC_TRY(cudaMemsetAsync(w.ctl(), 0, sizeof(Ctl), s));
+    // the degree statistics on the side stream, concurrent with the sample
+    CC_TRY(cudaEventRecord(h->fork, s));
+    CC_TRY(cudaStreamWaitEvent(h->side, h->fork, 0));
+    {
+        CC_PROF("k_degree_stats", h->side);
+        k_degree_stats<OffT><<<w.fs_parts, TPB, 0, h->side>>>(static_cast<const OffT *>(g.I), g.n, g.m, w.fs,
+                                                               &w.ctl()->stats_done, d);
+    }
+    CC_LAUNCH();
+    CC_TRY(cudaEventRecord(h->join, h->side));
+    w.sel_join = h->join;
     int32_t info = 0;
     if ((st = sample_phase<OffT>(g, so, fo, P, w, di, d, s, &info, w.sc.at<uint32_t>(w.o_counts))) != CC_OK)
         return st;
