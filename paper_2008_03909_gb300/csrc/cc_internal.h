@@ -81,8 +81,7 @@ class Scratch {
 // edges at vertices of degree > 64, and the highest degree (key
 // deg << 32 | ~v: ties to the smallest vertex).
 struct FeatStats {
-    unsigned long long sum_deg, cnt[5], edges_gt64, maxkey;
-    double sum_deg2;
+    unsigned long long sum_deg, cnt[5], edges_gt64, maxkey, sum_deg2;
 };
 
 // Control block of one call, in device memory.

@@ -141,11 +141,9 @@ struct DegStats {
         mk = key > mk ? key : mk;
     }
     // every thread of the block calls this once (it synchronises): warp
-    // sums, then block sums in shared memory, written with plain stores to
-    // this block's slot of part[] (the consumer adds the slots up; global
-    // atomics from every block on the same nine words serialised at the L2
-    // and cost more than the pass itself)
-    __device__ __forceinline__ void flush(FeatStats *part) {
+    // sums, then block sums in shared memory; thread 0 writes them to *out
+    // with plain stores
+    __device__ __forceinline__ void flush(FeatStats *out) {
         __shared__ unsigned long long bs[9];
         if (threadIdx.x < 9) bs[threadIdx.x] = 0;
         __syncthreads();
@@ -167,19 +165,32 @@ struct DegStats {
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            FeatStats &f = part[blockIdx.x];
-            f.sum_deg = bs[0];
-            f.sum_deg2 = (double)bs[1];
-            f.edges_gt64 = bs[2];
-            for (int j = 0; j < 5; ++j) f.cnt[j] = bs[3 + j];
-            f.maxkey = bs[8];
+            out->sum_deg = bs[0];
+            out->sum_deg2 = bs[1];
+            out->edges_gt64 = bs[2];
+            for (int j = 0; j < 5; ++j) out->cnt[j] = bs[3 + j];
+            out->maxkey = bs[8];
         }
+    }
+    // fold in another block's sums (the last block's total of the partials)
+    __device__ __forceinline__ void merge(const FeatStats &f) {
+        sd += f.sum_deg;
+        sd2 += f.sum_deg2;
+        e64 += f.edges_gt64;
+        c0 += f.cnt[0];
+        c1 += f.cnt[1];
+        c2 += f.cnt[2];
+        c3 += f.cnt[3];
+        c4 += f.cnt[4];
+        mk = f.maxkey > mk ? f.maxkey : mk;
     }
 };
 
 // One pass over the offsets: each block's partial sums go to its slot of
 // part[] (plain stores); the last block to finish (a counter in done[0])
-// adds the slots up in slot order into part[nparts] and resets the counter.
+// adds the slots up, its threads taking slots in turn, into part[nparts],
+// and resets the counter.  All sums are integers, so the total does not
+// depend on the order.
 template <typename OffT>
 __global__ void __launch_bounds__(256, 4) k_degree_stats(const OffT *I, uint32_t n, uint64_t m, FeatStats *part,
                                                          uint32_t *done, Dev d) {
@@ -189,7 +200,7 @@ __global__ void __launch_bounds__(256, 4) k_degree_stats(const OffT *I, uint32_t
         vertex_range(I, (uint32_t)v, m, b, e, d);
         ds.add(e - b, (uint32_t)v);
     }
-    ds.flush(part);
+    ds.flush(part + blockIdx.x);
     __shared__ bool last;
     __threadfence();
     __syncthreads();
@@ -197,19 +208,16 @@ __global__ void __launch_bounds__(256, 4) k_degree_stats(const OffT *I, uint32_t
     __syncthreads();
     if (!last) return;
     __threadfence();
-    if (threadIdx.x == 0) {
-        FeatStats t{};
-        const volatile FeatStats *vp = part;
-        for (uint32_t b = 0; b < gridDim.x; ++b) {
-            t.sum_deg += vp[b].sum_deg;
-            for (int j = 0; j < 5; ++j) t.cnt[j] += vp[b].cnt[j];
-            t.edges_gt64 += vp[b].edges_gt64;
-            t.maxkey = vp[b].maxkey > t.maxkey ? vp[b].maxkey : t.maxkey;
-            t.sum_deg2 += vp[b].sum_deg2;
-        }
-        part[gridDim.x] = t;
-        *done = 0;
+    DegStats tot;
+    for (uint32_t b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+        FeatStats f;
+        const unsigned long long *src = reinterpret_cast<const unsigned long long *>(part + b);
+        unsigned long long *dst = reinterpret_cast<unsigned long long *>(&f);
+        for (int j = 0; j < (int)(sizeof(FeatStats) / 8); ++j) dst[j] = __ldcg(src + j);
+        tot.merge(f);
     }
+    tot.flush(part + gridDim.x);
+    if (threadIdx.x == 0) *done = 0;
 }
 
 // ---------------------------------------------------------------- k-out
@@ -765,7 +773,7 @@ __global__ void __launch_bounds__(64) k_lmax_select(Ctl *ctl, uint32_t *lmax, co
         for (int j = 0; j < 5; ++j) red[0][1 + j] = f.cnt[j];
         red[0][6] = f.edges_gt64;
         red[0][7] = f.maxkey;
-        red2[0] = f.sum_deg2;
+        red2[0] = (double)f.sum_deg2;
         for (int j = 0; j < 8; ++j) red[1][j] = 0;
         red2[1] = 0.0;
     }

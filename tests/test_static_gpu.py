@@ -177,6 +177,24 @@ def test_ldd_sampled_labels_bit_exact(beta):
         assert np.array_equal(lab.cpu().numpy().view(np.uint32), want)
 
 
+@pytest.mark.parametrize("sizes", [[30] * 20 + [31], [30] * 20, [2] * 500 + [40, 40]])
+def test_lmax_without_a_majority_cluster(sizes):
+    # disjoint cliques: after k-out every clique is one cluster and none holds
+    # a majority of the non-root vertices, so the sampled L_max guess cannot
+    # be confirmed by its share and the labels are counted in full; L_max
+    # (ties to the smallest label) and the finish's edges match the oracle
+    g = synth.cliques(sizes)
+    off, edg = g.numpy()
+    for fin in (("uf_rem_cas", "naive", "split_one"), ("sv", "naive", "split_one")):
+        want, ost = oracle.connectivity(off, edg, "kout", fin[0], seed=5, tries=3, beta=0.2)
+        got, st = gpu_labels(g, "kout", fin, seed=5)
+        assert np.array_equal(got, want)
+        assert st["lmax"] == ost["lmax"]
+        lab = oracle.kout_sample(off, edg, 2, 5)
+        deg = np.diff(off)
+        assert st["edges_finish"] == int(deg[lab != ost["lmax"]].sum())
+
+
 def test_ldd_tie_golden():
     # the hand-worked graph where vertex 19 is claimed by two clusters in the
     # same round: the smaller centre must win on every run (the kernel's
