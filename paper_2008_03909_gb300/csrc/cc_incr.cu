@@ -58,9 +58,13 @@ __device__ __forceinline__ void load_pairs4(const uint32_t *pairs, uint64_t g, u
 }
 
 // Insert(u, v) = Union(u, v) for every pair; four consecutive pairs per
-// thread step, their eight parent loads issued before any union.
+// thread step, their eight parent loads issued before any union.  Four
+// pairs, their parents and an inlined union loop do not fit 32 registers
+// (eight blocks per SM spilled 120 bytes per thread), so the kernel runs at
+// six blocks per SM (40 registers) on a grid of one wave at that occupancy.
+constexpr int INSERT_MINB = 6;
 template <class E>
-__global__ void __launch_bounds__(256, 8) k_incr_insert(uint32_t *P, uint32_t n, const uint32_t *pairs, uint64_t k, Dev d) {
+__global__ void __launch_bounds__(256, INSERT_MINB) k_incr_insert(uint32_t *P, uint32_t n, const uint32_t *pairs, uint64_t k, Dev d) {
     const bool vec = (reinterpret_cast<uintptr_t>(pairs) & 15) == 0;
     const uint64_t groups = (k + 3) / 4;
     for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < groups;
@@ -271,7 +275,7 @@ cc_status cc_incr_insert_batch(cc_incr *h, const uint32_t *pairs, uint64_t k, vo
             if (hc == 0) return CC_OK;
         }
     }
-    const unsigned grid = grid_for(di, (k + 3) / 4, TPB);
+    const unsigned grid = grid_for(di, (k + 3) / 4, TPB, INSERT_MINB);
     return with_uf_engine(h->fo.kind, h->fo.find, h->fo.splice, [&](auto eng) -> cc_status {
         using E = decltype(eng);
         {

@@ -292,6 +292,11 @@ __global__ void __launch_bounds__(256, 4) k_degree_stats(const OffT *I, uint32_t
 // One vertex per thread step at full occupancy (launch bounds for eight
 // 256-thread blocks per SM), with the next vertex's offsets prefetched.
 constexpr int KOUT_MINB = 8;
+// The first k-out pass keeps about 40 values live per thread (five offsets,
+// four first edges, four picks and their positions): at eight blocks per
+// SM it spilled 160-250 bytes per thread to local memory, so it runs at six
+// (40 registers).
+constexpr int HOOK_MINB = 6;
 // The first-edge queue of k_kout_hook_first: one region per block (grids of
 // at most 8 blocks per SM, so KOUT_MAX_BLOCKS covers 256 SMs).  The regions
 // hold n pairs plus, per warp of the grid, one 128-vertex step of slack.
@@ -357,7 +362,7 @@ void launch_kout(unsigned grid, cudaStream_t s, const OffT *I, const uint32_t *A
 // kernel's time).  A block's warp steps hold at most cap_blk vertices, so
 // its region cannot overflow (checked, flagged).
 template <typename OffT>
-__global__ void __launch_bounds__(256, 8) k_kout_hook_first(const OffT *I, const uint32_t *A, uint32_t n,
+__global__ void __launch_bounds__(256, HOOK_MINB) k_kout_hook_first(const OffT *I, const uint32_t *A, uint32_t n,
                                                             uint64_t m, uint32_t *P, uint2 *defer,
                                                             uint32_t *dcount, uint32_t cap_blk, uint32_t *pick1,
                                                             uint32_t k, uint32_t rule, uint64_t seed, uint32_t *nz,
@@ -907,11 +912,18 @@ __global__ void __launch_bounds__(64) k_lmax_select(Ctl *ctl, uint32_t *lmax, co
 }
 
 // ---------------------------------------------------------------- edge passes
+// The edge passes inline a union (or a frontier claim) per edge and keep a
+// warp's chunk reservation live: at eight 256-thread blocks per SM (32
+// registers) they spilled 70-280 bytes per thread to local memory, so they
+// run at six (40 registers) on grids of one wave at that occupancy.  (The
+// LDD passes stay at eight: measured, their latency hiding gains more from
+// the warps than they lose to the spills.)
+constexpr int EDGE_MINB = 6;
 // Edge pass over a vertex range (union-find finish with nothing skipped, or
 // a skip test on P[u] == L_max): light vertices run in the calling thread;
 // heavier ones are cut into chunks for k_chunks.
 template <typename OffT, class F>
-__global__ void __launch_bounds__(256, 8) k_range_bin(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, const uint32_t *P,
+__global__ void __launch_bounds__(256, EDGE_MINB) k_range_bin(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, const uint32_t *P,
                             const uint32_t *lmax_p, F f, ChunkRef *chunks, uint32_t *nchunks,
                             uint64_t cap, unsigned long long *edges, Dev d) {
     const int lane = threadIdx.x & 31;
@@ -939,7 +951,7 @@ __global__ void __launch_bounds__(256, 8) k_range_bin(const OffT *I, const uint3
 }
 
 template <typename OffT, class F>
-__global__ void __launch_bounds__(256, 8) k_chunks(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, const ChunkRef *chunks,
+__global__ void __launch_bounds__(256, EDGE_MINB) k_chunks(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, const ChunkRef *chunks,
                          const uint32_t *nchunks, uint64_t cap, F f, Dev d, const uint32_t *skip = nullptr) {
     if (skip && *skip) return;
     run_chunks(I, A, n, m, chunks, nchunks, cap, f, d);
@@ -949,7 +961,7 @@ __global__ void __launch_bounds__(256, 8) k_chunks(const OffT *I, const uint32_t
 // Vertex list (BFS / LDD frontiers): light vertices inline, heavier ones to
 // the chunk list.
 template <typename OffT, class F>
-__global__ void __launch_bounds__(256, 8) k_list_bin(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, const uint32_t *list,
+__global__ void __launch_bounds__(256, EDGE_MINB) k_list_bin(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, const uint32_t *list,
                            const uint32_t *count, F f, ChunkRef *chunks, uint32_t *nchunks, uint64_t cap,
                            Dev d) {
     const int lane = threadIdx.x & 31;
@@ -975,7 +987,7 @@ __global__ void __launch_bounds__(256, 8) k_list_bin(const OffT *I, const uint32
 // sampled label is not L_max and that have edges; light ones to a list,
 // heavy ones to the chunk list.  Built once, reused every round.
 template <typename OffT>
-__global__ void __launch_bounds__(256, 8) k_cand_bin(const OffT *I, uint32_t n, uint64_t m, const uint32_t *P, const uint32_t *lmax_p,
+__global__ void __launch_bounds__(256, EDGE_MINB) k_cand_bin(const OffT *I, uint32_t n, uint64_t m, const uint32_t *P, const uint32_t *lmax_p,
                            uint32_t *light, uint32_t *nlight, ChunkRef *chunks, uint32_t *nchunks, uint64_t cap,
                            unsigned long long *edges, Dev d, const uint32_t *only_if = nullptr,
                            const uint32_t *skip = nullptr) {
@@ -1037,7 +1049,7 @@ __global__ void __launch_bounds__(256, 8) k_cand_bin(const OffT *I, uint32_t n, 
 }
 
 template <typename OffT, class F>
-__global__ void __launch_bounds__(256, 8) k_light_list(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, const uint32_t *list,
+__global__ void __launch_bounds__(256, EDGE_MINB) k_light_list(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, const uint32_t *list,
                              const uint32_t *count, F f, Dev d, const uint32_t *skip = nullptr) {
     if (skip && *skip) return;
     const int lane = threadIdx.x & 31;
@@ -1436,6 +1448,7 @@ __global__ void __launch_bounds__(256, 8) k_ldd_wake(uint32_t s0, uint32_t s1, u
         ctl->mf[cur] = 0;
         ctl->nchunks = 0;
         ctl->ldd_done = 0;
+        ctl->ldd_minc = NONE;
     }
     // the uncovered ids of [s0, s1) join the frontier with one atomic per
     // block (block_compact; only this block touches its ids' bits, so the
@@ -1524,20 +1537,28 @@ __global__ void __launch_bounds__(256, 8) k_ldd_commit(uint32_t *P, uint32_t *vi
 // bottom-up edge costs a bit test where a top-down one costs a candidate
 // read and often a writeMin).  Beside its edge count, the frontier is
 // marked in a bitmap every round, so any round can switch.  ldd_push_nf is
-// the frontier size the top-down pass sees: 0 in a bottom-up round.
+// the frontier size the top-down pass sees: 0 in a bottom-up round.  The
+// pass also takes the smallest centre id of the frontier (ldd_minc): a
+// bottom-up scan that meets it can stop, since no neighbour offers less.
 template <typename OffT>
 __global__ void __launch_bounds__(256, 8) k_ldd_front(const OffT *I, uint32_t n, uint64_t m, const uint32_t *list,
-                                                      const uint32_t *count, uint32_t *fbm, Ctl *ctl, int cur, Dev d) {
+                                                      const uint32_t *count, const uint32_t *P, uint32_t *fbm,
+                                                      Ctl *ctl, int cur, Dev d) {
     const uint32_t total = *count;
     unsigned long long s = 0;
     const int lane = threadIdx.x & 31;
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    uint32_t minc = NONE;
     for (uint64_t base = warp * 32; base < total; base += nw * 32) {
         const bool act = base + lane < total;
         const uint32_t u = act ? list[base + lane] : 0;
         uint64_t b = 0, e = 0;
-        if (act) vertex_range(I, u, m, b, e, d);
+        if (act) {
+            vertex_range(I, u, m, b, e, d);
+            const uint32_t c = P[u];
+            minc = c < minc ? c : minc;
+        }
         s += e - b;
         // one OR per distinct bitmap word in the warp
         const uint32_t word = act ? (u >> 5) : NONE;
@@ -1547,6 +1568,8 @@ __global__ void __launch_bounds__(256, 8) k_ldd_front(const OffT *I, uint32_t n,
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
     if (lane == 0 && s) atomicAdd(&ctl->mf[cur], s);
+    minc = __reduce_min_sync(0xFFFFFFFFu, minc);
+    if (lane == 0 && minc != NONE) atomicMin(&ctl->ldd_minc, minc);
     // the last block to finish takes the round's direction
     __shared__ bool last;
     __threadfence();
@@ -1570,29 +1593,58 @@ __global__ void __launch_bounds__(256, 8) k_ldd_front(const OffT *I, uint32_t n,
 // same writeMin as a top-down claim, so w ends the round with the smallest
 // centre among its frontier neighbours either way, and the clustering does
 // not depend on the direction.  The first candidate queues w for the commit.
+// A scan keeps its smallest candidate in a register, makes one writeMin at
+// its end, and ends early at the round's smallest frontier centre (the
+// result cannot go lower, so it is exact).
 struct LDDPullEdge {
     const uint32_t *P;
     const uint32_t *fbm;
     uint32_t *cand;
     uint32_t *next;
     uint32_t *nnext;
-    __device__ __forceinline__ void offer(uint32_t w, uint32_t y) {
-        if (!((fbm[y >> 5] >> (y & 31)) & 1u)) return;
-        const uint32_t c = P[y];
-        if (ld_rel(cand + w) <= c) return;
-        if (atomicMin(cand + w, c) == NONE) next[append_one(nnext)] = w;
-    }
-    __device__ __forceinline__ void apply4(uint32_t w, const uint32_t (&y)[4], const bool (&ok)[4]) {
+    // candidates of four edges: P[y] for frontier neighbours, else NONE
+    // (the four bit loads issued together, then the parents)
+    __device__ __forceinline__ uint32_t min4(const uint32_t (&y)[4], const bool (&ok)[4]) const {
+        bool in[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if (ok[j]) offer(w, y[j]);
-    }
-    __device__ __forceinline__ void apply4u(const uint32_t (&w)[4], const uint32_t (&y)[4], const bool (&ok)[4]) {
+        for (int j = 0; j < 4; ++j) in[j] = ok[j] && ((fbm[y[j] >> 5] >> (y[j] & 31)) & 1u);
+        uint32_t c[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if (ok[j]) offer(w[j], y[j]);
+        for (int j = 0; j < 4; ++j) c[j] = in[j] ? P[y[j]] : NONE;
+        const uint32_t c01 = c[0] < c[1] ? c[0] : c[1], c23 = c[2] < c[3] ? c[2] : c[3];
+        return c01 < c23 ? c01 : c23;
+    }
+    __device__ __forceinline__ void offer(uint32_t w, uint32_t c) const {
+        if (c != NONE && ld_rel(cand + w) > c && atomicMin(cand + w, c) == NONE) next[append_one(nnext)] = w;
     }
 };
+
+// PULL_PROBE: edges a lane scans of a heavier vertex before its chunks are
+// listed (they are listed only if the probe did not meet the smallest
+// centre).
+constexpr uint32_t PULL_PROBE = 16;
+
+// The candidate of w from edges [b, b + len), scanned by its lane four at a
+// time until the smallest frontier centre turns up.
+__device__ __forceinline__ uint32_t ldd_pull_scan(const LDDPullEdge &f, const uint32_t *A, uint64_t b,
+                                                  uint32_t len, uint32_t n, uint32_t minc, const Dev &d) {
+    uint32_t best = NONE;
+    for (uint32_t x = 0; x < len && best != minc; x += 4) {
+        uint32_t y[4];
+        bool ok[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            ok[j] = x + j < len;
+            y[j] = ok[j] ? ld_stream(A + b + x + j) : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (ok[j] && y[j] >= n) { atomicOr(d.err, ERR_BAD_EDGE); ok[j] = false; }
+        const uint32_t c = f.min4(y, ok);
+        best = c < best ? c : best;
+    }
+    return best;
+}
 
 // One LDD round's edge pass, either direction (the flag is the same for
 // every thread): top-down, the frontier list's light vertices are walked
@@ -1623,6 +1675,11 @@ __global__ void __launch_bounds__(256, 8) k_ldd_bin(const OffT *I, const uint32_
         ws.close(chunks, cap);
         return;
     }
+    // bottom-up: lane L takes vertex base + L when its `vis` bit is clear
+    // and scans its edges itself (a light vertex all of them, a heavier one
+    // the first PULL_PROBE), stopping at the smallest frontier centre; a
+    // heavier vertex whose probe did not meet it goes to the chunk list
+    const uint32_t minc = ctl->ldd_minc;
     for (uint64_t base = warp * 32; base < n; base += nw * 32) {
         const uint32_t vword = vis[base >> 5];
         if (vword == 0xFFFFFFFFu) continue;   // warp-uniform
@@ -1630,9 +1687,11 @@ __global__ void __launch_bounds__(256, 8) k_ldd_bin(const OffT *I, const uint32_
         uint64_t b = 0, e = 0;
         if (w < n && !((vword >> lane) & 1u)) vertex_range(I, (uint32_t)w, m, b, e, d);
         const uint64_t deg = e - b;
-        const uint32_t nc = deg > LIGHT_MAX ? (uint32_t)((deg + CHUNK - 1) / CHUNK) : 0;
+        const bool heavy = deg > LIGHT_MAX;
+        const uint32_t best = ldd_pull_scan(fpull, A, b, heavy ? PULL_PROBE : (uint32_t)deg, n, minc, d);
+        fpull.offer((uint32_t)w, best);
+        const uint32_t nc = heavy && best != minc ? (uint32_t)((deg + CHUNK - 1) / CHUNK) : 0;
         warp_bin_chunks(ws, nchunks, chunks, cap, nc, (uint32_t)w, d);
-        warp_light_edges((uint32_t)w, b, nc ? 0u : (uint32_t)deg, A, n, fpull, d);
     }
     ws.close(chunks, cap);
 }
@@ -1641,8 +1700,45 @@ template <typename OffT>
 __global__ void __launch_bounds__(256, 8) k_ldd_chunks(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m,
                                                        const ChunkRef *chunks, const uint32_t *nchunks, uint64_t cap,
                                                        LDDEdge fpush, LDDPullEdge fpull, const Ctl *ctl, Dev d) {
-    if (ctl->ldd_pull) run_chunks(I, A, n, m, chunks, nchunks, cap, fpull, d);
-    else run_chunks(I, A, n, m, chunks, nchunks, cap, fpush, d);
+    if (!ctl->ldd_pull) {
+        run_chunks(I, A, n, m, chunks, nchunks, cap, fpush, d);
+        return;
+    }
+    // bottom-up chunks: a warp per chunk, each lane its smallest candidate;
+    // the warp stops once a lane meets the smallest frontier centre (or
+    // skips the chunk if w already holds it), then offers the warp minimum
+    const uint32_t minc = ctl->ldd_minc;
+    const int lane = threadIdx.x & 31;
+    const uint32_t total = (uint32_t)((uint64_t)*nchunks < cap ? (uint64_t)*nchunks : cap);
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t i = warp; i < total; i += nwarps) {
+        const ChunkRef c = chunks[i];
+        if (c.u == NONE || ld_rel(fpull.cand + c.u) == minc) continue;   // warp-uniform
+        uint64_t b, e;
+        vertex_range(I, c.u, m, b, e, d);
+        const uint64_t cb = b + (uint64_t)c.c * CHUNK;
+        const uint64_t ce = cb + CHUNK < e ? cb + CHUNK : e;
+        uint32_t best = NONE;
+        for (uint64_t x0 = cb; x0 < ce; x0 += 128) {
+            uint32_t y[4];
+            bool ok[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint64_t x = x0 + 32 * j + lane;
+                ok[j] = x < ce;
+                y[j] = ok[j] ? ld_stream(A + x) : 0;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (ok[j] && y[j] >= n) { atomicOr(d.err, ERR_BAD_EDGE); ok[j] = false; }
+            const uint32_t cm = fpull.min4(y, ok);
+            best = cm < best ? cm : best;
+            if (__any_sync(0xFFFFFFFFu, best == minc)) break;
+        }
+        best = __reduce_min_sync(0xFFFFFFFFu, best);
+        if (lane == 0) fpull.offer(c.u, best);
+    }
 }
 
 
@@ -1826,6 +1922,7 @@ cc_status bfs_sample(const Graph &g, const cc_sample_opt &so, uint32_t *P, Work 
     uint32_t *bm[2] = {w.sc.at<uint32_t>(w.o_bm0), w.sc.at<uint32_t>(w.o_bm1)};
     ChunkRef *chunks = w.sc.at<ChunkRef>(w.o_chunks);
     const unsigned gv = grid_for(di, n, TPB);
+    const unsigned ge = grid_for(di, n, TPB, EDGE_MINB);
     // host-visible copies of the per-level counters
     struct Lv {
         uint32_t nnext;
@@ -1953,7 +2050,7 @@ cc_status bfs_sample(const Graph &g, const cc_sample_opt &so, uint32_t *P, Work 
                         BFSEdge f{P, vis, q[qn], &loop->cnt[(L + 1) % 3], &ctl->minv, src, NONE, d.forest};
                         {
                             CC_PROF("k_chunks", s);
-                            k_chunks<OffT, BFSEdge><<<grid_for(di, (uint64_t)1 << 40, TPB), TPB, 0, s>>>(
+                            k_chunks<OffT, BFSEdge><<<grid_for(di, (uint64_t)1 << 40, TPB, EDGE_MINB), TPB, 0, s>>>(
                                 I, g.A, n, g.m, chunks, &loop->npiece[L % 3], w.chunk_cap, f, d);
                         }
                         CC_LAUNCH();
@@ -2000,12 +2097,12 @@ cc_status bfs_sample(const Graph &g, const cc_sample_opt &so, uint32_t *P, Work 
                 BFSEdge f{P, vis, q[nx], &ctl->nfront[nx], &ctl->minv, src, NONE, d.forest};
                 {
                     CC_PROF("k_list_bin", s);
-                    k_list_bin<OffT, BFSEdge><<<gv, TPB, 0, s>>>(I, g.A, n, g.m, q[cur], &ctl->nfront[cur], f, chunks,
+                    k_list_bin<OffT, BFSEdge><<<ge, TPB, 0, s>>>(I, g.A, n, g.m, q[cur], &ctl->nfront[cur], f, chunks,
                                                                  &ctl->nchunks, w.chunk_cap, d);
                 }
                 {
                     CC_PROF("k_chunks", s);
-                    k_chunks<OffT, BFSEdge><<<grid_for(di, (uint64_t)1 << 40, TPB), TPB, 0, s>>>(
+                    k_chunks<OffT, BFSEdge><<<grid_for(di, (uint64_t)1 << 40, TPB, EDGE_MINB), TPB, 0, s>>>(
                         I, g.A, n, g.m, chunks, &ctl->nchunks, w.chunk_cap, f, d);
                 }
                 {
@@ -2058,6 +2155,8 @@ cc_status ldd_sample(const Graph &g, const cc_sample_opt &so, uint32_t *P, Work 
     ChunkRef *chunks = w.sc.at<ChunkRef>(w.o_chunks);
     const unsigned gv = grid_for(di, n, TPB);
     const unsigned gc = grid_for(di, (uint64_t)1 << 40, TPB);
+    const unsigned ge = grid_for(di, n, TPB, EDGE_MINB);
+    const unsigned gce = grid_for(di, (uint64_t)1 << 40, TPB, EDGE_MINB);
     CC_TRY(cudaMemsetAsync(vis, 0, words * 4, s));
     CC_TRY(cudaMemsetAsync(fbm, 0, words * 4, s));
     CC_TRY(cudaMemsetAsync(cand, 0xFF, (size_t)n * 4, s));
@@ -2082,7 +2181,7 @@ cc_status ldd_sample(const Graph &g, const cc_sample_opt &so, uint32_t *P, Work 
         }
         {
             CC_PROF("k_ldd_front", s);
-            k_ldd_front<OffT><<<gv, TPB, 0, s>>>(I, n, g.m, q[cur], &ctl->nfront[cur], fbm, ctl, cur, d);
+            k_ldd_front<OffT><<<gv, TPB, 0, s>>>(I, n, g.m, q[cur], &ctl->nfront[cur], P, fbm, ctl, cur, d);
         }
         LDDEdge fpush{P, vis, cand, q[nx], &ctl->nfront[nx]};
         LDDPullEdge fpull{P, fbm, cand, q[nx], &ctl->nfront[nx]};
@@ -2118,12 +2217,12 @@ cc_status ldd_sample(const Graph &g, const cc_sample_opt &so, uint32_t *P, Work 
         LDDEdge f{P, vis, cand, q[nx], &ctl->nfront[nx]};
         {
             CC_PROF("k_list_bin", s);
-            k_list_bin<OffT, LDDEdge><<<gv, TPB, 0, s>>>(I, g.A, n, g.m, q[cur], &ctl->nfront[cur], f, chunks,
+            k_list_bin<OffT, LDDEdge><<<ge, TPB, 0, s>>>(I, g.A, n, g.m, q[cur], &ctl->nfront[cur], f, chunks,
                                                          &ctl->nchunks, w.chunk_cap, d);
         }
         {
             CC_PROF("k_chunks", s);
-            k_chunks<OffT, LDDEdge><<<gc, TPB, 0, s>>>(I, g.A, n, g.m, chunks, &ctl->nchunks, w.chunk_cap, f, d);
+            k_chunks<OffT, LDDEdge><<<gce, TPB, 0, s>>>(I, g.A, n, g.m, chunks, &ctl->nchunks, w.chunk_cap, f, d);
         }
         {
             CC_PROF("k_ldd_commit", s);
@@ -2179,10 +2278,12 @@ cc_status sample_phase(const Graph &g, const cc_sample_opt &so, const cc_finish_
         const OffT *I = static_cast<const OffT *>(g.I);
         uint2 *defer = w.sc.at<uint2>(w.o_defer);
         uint32_t *dcount = w.sc.at<uint32_t>(w.o_dcount);
-        // a block's warps take steps warp, warp + nw, ... of 128 vertices
-        const uint64_t steps = ((uint64_t)g.n + 127) / 128, nw = (uint64_t)gv * (TPB / 32);
+        // the first pass's grid (one wave at its occupancy); a block's warps
+        // take steps warp, warp + nw, ... of 128 vertices
+        const unsigned gh = grid_for(di, g.n, TPB, HOOK_MINB);
+        const uint64_t steps = ((uint64_t)g.n + 127) / 128, nw = (uint64_t)gh * (TPB / 32);
         const uint64_t cap_blk = (TPB / 32) * 128 * ((steps + nw - 1) / nw);
-        if (gv > KOUT_MAX_BLOCKS || (uint64_t)gv * cap_blk > kout_defer_entries(g.n) || cap_blk > 0xFFFFFFFFull)
+        if (gh > KOUT_MAX_BLOCKS || (uint64_t)gh * cap_blk > kout_defer_entries(g.n) || cap_blk > 0xFFFFFFFFull)
             return CC_ERR_INVALID;   // not reached: grids have at most 8 blocks per SM
         uint32_t *pick1 = so.k == 2 ? w.sc.at<uint32_t>(w.o_pick) : nullptr;
         // the fused binning (k = 2, exact IdentifyFrequent, a finish to follow)
@@ -2190,12 +2291,12 @@ cc_status sample_phase(const Graph &g, const cc_sample_opt &so, const cc_finish_
         uint32_t *nz = fuse ? w.sc.at<uint32_t>(w.o_nz) : nullptr;
         {
             CC_PROF("k_kout_hook_first", s);
-            k_kout_hook_first<OffT><<<gv, TPB, 0, s>>>(I, g.A, g.n, g.m, P, defer, dcount, (uint32_t)cap_blk, pick1,
+            k_kout_hook_first<OffT><<<gh, TPB, 0, s>>>(I, g.A, g.n, g.m, P, defer, dcount, (uint32_t)cap_blk, pick1,
                                                        so.k, so.kout_rule, so.seed, nz, d);
         }
         {
             CC_PROF("k_kout_defer", s);
-            k_kout_defer<E><<<gv, TPB, 0, s>>>(g.n, P, defer, dcount, gv, (uint32_t)cap_blk, d);
+            k_kout_defer<E><<<gv, TPB, 0, s>>>(g.n, P, defer, dcount, gh, (uint32_t)cap_blk, d);
         }
         if (so.k > 1) {
             // full compression between the rounds: without it the second
@@ -2319,7 +2420,8 @@ cc_status finish_phase(const Graph &g, const cc_finish_opt &fo, const uint32_t *
     Ctl *ctl = w.ctl();
     ChunkRef *chunks = w.sc.at<ChunkRef>(w.o_chunks);
     const unsigned gv = grid_for(di, n, TPB);
-    const unsigned gc = grid_for(di, (uint64_t)1 << 40, TPB);
+    const unsigned ge = grid_for(di, n, TPB, EDGE_MINB);
+    const unsigned gce = grid_for(di, (uint64_t)1 << 40, TPB, EDGE_MINB);
     if (rounds_out) *rounds_out = 0;
     // lists built by the fused k-out pass (against the exact L_max, or
     // cleared by k_lmax_check and rebuilt by the guarded k_cand_bin below)
@@ -2341,7 +2443,7 @@ cc_status finish_phase(const Graph &g, const cc_finish_opt &fo, const uint32_t *
             if (!built) CC_TRY(cudaMemsetAsync(&ctl->nlight, 0, 4, s));
             {
                 CC_PROF("k_cand_bin", s);
-                k_cand_bin<OffT><<<gv, TPB, 0, s>>>(I, n, g.m, P, lmax_p, light, &ctl->nlight, chunks, &ctl->nchunks,
+                k_cand_bin<OffT><<<ge, TPB, 0, s>>>(I, n, g.m, P, lmax_p, light, &ctl->nlight, chunks, &ctl->nchunks,
                                                     w.chunk_cap, &ctl->edges, d, only_if, skip);
             }
             CC_LAUNCH();
@@ -2352,18 +2454,18 @@ cc_status finish_phase(const Graph &g, const cc_finish_opt &fo, const uint32_t *
             if (lower_only)
                 {
                     CC_PROF("k_range_bin", s);
-                    k_range_bin<OffT, UnionEdge<E>><<<gv, TPB, 0, s>>>(I, g.A, n, g.m, P, nullptr, f, chunks,
+                    k_range_bin<OffT, UnionEdge<E>><<<ge, TPB, 0, s>>>(I, g.A, n, g.m, P, nullptr, f, chunks,
                                                                        &ctl->nchunks, w.chunk_cap, &ctl->edges, d);
                 }
             else
                 {
                     CC_PROF("k_light_list", s);
-                    k_light_list<OffT, UnionEdge<E>><<<gv, TPB, 0, s>>>(I, g.A, n, g.m, light, &ctl->nlight, f, d,
+                    k_light_list<OffT, UnionEdge<E>><<<ge, TPB, 0, s>>>(I, g.A, n, g.m, light, &ctl->nlight, f, d,
                                                                          skip);
                 }
             {
                 CC_PROF("k_chunks", s);
-                k_chunks<OffT, UnionEdge<E>><<<gc, TPB, 0, s>>>(I, g.A, n, g.m, chunks, &ctl->nchunks, w.chunk_cap, f, d,
+                k_chunks<OffT, UnionEdge<E>><<<gce, TPB, 0, s>>>(I, g.A, n, g.m, chunks, &ctl->nchunks, w.chunk_cap, f, d,
                                                                 skip);
             }
             CC_LAUNCH();
@@ -2382,7 +2484,7 @@ cc_status finish_phase(const Graph &g, const cc_finish_opt &fo, const uint32_t *
     if (!built) CC_TRY(cudaMemsetAsync(&ctl->nlight, 0, 4, s));
     {
         CC_PROF("k_cand_bin", s);
-        k_cand_bin<OffT><<<gv, TPB, 0, s>>>(I, n, g.m, P, lmax_p, light, &ctl->nlight, chunks, &ctl->nchunks,
+        k_cand_bin<OffT><<<ge, TPB, 0, s>>>(I, n, g.m, P, lmax_p, light, &ctl->nlight, chunks, &ctl->nchunks,
                                             w.chunk_cap, &ctl->edges, d, only_if);
     }
     CC_LAUNCH();
@@ -2416,21 +2518,21 @@ cc_status finish_phase(const Graph &g, const cc_finish_opt &fo, const uint32_t *
             SVEdge f{P, prev, &ctl->changed, false};
             {
                 CC_PROF("k_light_list", s);
-                k_light_list<OffT, SVEdge><<<gv, TPB, 0, s>>>(I, g.A, n, g.m, light, &ctl->nlight, f, d);
+                k_light_list<OffT, SVEdge><<<ge, TPB, 0, s>>>(I, g.A, n, g.m, light, &ctl->nlight, f, d);
             }
             {
                 CC_PROF("k_chunks", s);
-                k_chunks<OffT, SVEdge><<<gc, TPB, 0, s>>>(I, g.A, n, g.m, chunks, &ctl->nchunks, w.chunk_cap, f, d);
+                k_chunks<OffT, SVEdge><<<gce, TPB, 0, s>>>(I, g.A, n, g.m, chunks, &ctl->nchunks, w.chunk_cap, f, d);
             }
         } else {
             LTEdge f{P, prev, &ctl->changed, false};
             {
                 CC_PROF("k_light_list", s);
-                k_light_list<OffT, LTEdge><<<gv, TPB, 0, s>>>(I, g.A, n, g.m, light, &ctl->nlight, f, d);
+                k_light_list<OffT, LTEdge><<<ge, TPB, 0, s>>>(I, g.A, n, g.m, light, &ctl->nlight, f, d);
             }
             {
                 CC_PROF("k_chunks", s);
-                k_chunks<OffT, LTEdge><<<gc, TPB, 0, s>>>(I, g.A, n, g.m, chunks, &ctl->nchunks, w.chunk_cap, f, d);
+                k_chunks<OffT, LTEdge><<<gce, TPB, 0, s>>>(I, g.A, n, g.m, chunks, &ctl->nchunks, w.chunk_cap, f, d);
             }
         }
         {

@@ -177,6 +177,45 @@ def test_ldd_sampled_labels_bit_exact(beta):
         assert np.array_equal(lab.cpu().numpy().view(np.uint32), want)
 
 
+def ldd_pull_graph():
+    """A graph whose second and third LDD rounds (beta 0.05: one new centre
+    per round) run bottom-up and need every branch of the bottom-up scan.
+    Round 0 claims F = 10000..10099 (a clique) for centre 0; round 1 starts
+    centre 1, whose neighbours are the two heavy vertices h1 = 6000 and
+    h2 = 6001.  Each heavy vertex lists vertex 1 first, then 3000 fillers
+    (2000..4999), then (h1 only) all of F: h1's first edges reach only
+    centre 1, its probe misses the smallest centre 0, its chunks are listed
+    and the second one meets 0; h2 never meets 0 and keeps 1.  In round 2
+    the fillers (light, neighbours h1 < h2) stop at h1's centre 0."""
+    F = range(10000, 10100)
+    fill = range(2000, 5000)
+    e = [(0, f) for f in F] + [(a, b) for a in F for b in F if a < b] + [(1, 6000), (1, 6001)]
+    e += [(h, x) for h in (6000, 6001) for x in fill] + [(6000, f) for f in F]
+    return synth.from_edge_list(10100, e)
+
+
+def test_ldd_bottom_up_scan_paths():
+    g = ldd_pull_graph()
+    off, edg = g.numpy()
+    deg = np.diff(off)
+    m = int(off[-1])
+    # the direction rule (bottom-up when the uncovered vertices' edges are
+    # fewer than twice the frontier's) picks bottom-up in rounds 1 and 2
+    mf1 = int(deg[10000:10100].sum() + deg[1])
+    assert m - deg[0] - mf1 < 2 * mf1
+    mf2 = int(deg[6000] + deg[6001] + deg[2])
+    assert m - deg[0] - mf1 - mf2 < 2 * mf2
+    assert deg[6000] > 2048 and deg[6001] > 2048   # two chunks each
+    want, r = oracle.ldd_sample(off, edg, beta=0.05)
+    assert want[6000] == want[10000] and want[6001] == want[1] != want[0]
+    d_off, d_edg = on_gpu(g)
+    for _ in range(5):
+        lab, rounds = cc.cc_sample(d_off, d_edg, cc.sample_opt("ldd", ldd_beta=0.05))
+        assert rounds == r
+        assert np.array_equal(lab.cpu().numpy().view(np.uint32), want)
+    assert cc.device_error() == 0
+
+
 @pytest.mark.parametrize("sizes", [[30] * 20 + [31], [30] * 20, [2] * 500 + [40, 40]])
 def test_lmax_without_a_majority_cluster(sizes):
     # disjoint cliques: after k-out every clique is one cluster and none holds
