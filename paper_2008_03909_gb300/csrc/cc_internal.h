@@ -101,7 +101,7 @@ struct Ctl {
     uint32_t ldd_pull;                 // LDD: 1 while the rounds run bottom-up
     uint32_t ldd_push_nf;              // LDD: the frontier size the top-down kernels see (0 bottom-up)
     uint32_t ldd_done;                 // LDD: blocks of the frontier pass done (the last one decides)
-    uint32_t ldd_minc;                 // LDD: smallest centre id in the round's frontier
+    uint32_t ldd_minc[2];              // LDD: smallest centre id of the frontier, by parity (as nfront)
     uint32_t guess;                    // k-out: sampled guess of L_max the fused binning used
     uint32_t rebin;                    // 1 when the exact L_max differs from the guess
     unsigned long long nonroots;       // k-out fused pass: vertices whose root is not themselves

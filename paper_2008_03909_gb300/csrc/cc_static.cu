@@ -916,14 +916,16 @@ __global__ void __launch_bounds__(64) k_lmax_select(Ctl *ctl, uint32_t *lmax, co
 // warp's chunk reservation live: at eight 256-thread blocks per SM (32
 // registers) they spilled 70-280 bytes per thread to local memory, so they
 // run at six (40 registers) on grids of one wave at that occupancy.  (The
-// LDD passes stay at eight: measured, their latency hiding gains more from
-// the warps than they lose to the spills.)
+// LDD passes and the light-vertex walks k_range_bin and k_light_list stay
+// at eight: measured, on LDD and on graphs of light vertices (grids,
+// G(n, M)) their latency hiding gains more from the warps than they lose to
+// the spills.)
 constexpr int EDGE_MINB = 6;
 // Edge pass over a vertex range (union-find finish with nothing skipped, or
 // a skip test on P[u] == L_max): light vertices run in the calling thread;
 // heavier ones are cut into chunks for k_chunks.
 template <typename OffT, class F>
-__global__ void __launch_bounds__(256, EDGE_MINB) k_range_bin(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, const uint32_t *P,
+__global__ void __launch_bounds__(256, 8) k_range_bin(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, const uint32_t *P,
                             const uint32_t *lmax_p, F f, ChunkRef *chunks, uint32_t *nchunks,
                             uint64_t cap, unsigned long long *edges, Dev d) {
     const int lane = threadIdx.x & 31;
@@ -1049,7 +1051,7 @@ __global__ void __launch_bounds__(256, EDGE_MINB) k_cand_bin(const OffT *I, uint
 }
 
 template <typename OffT, class F>
-__global__ void __launch_bounds__(256, EDGE_MINB) k_light_list(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, const uint32_t *list,
+__global__ void __launch_bounds__(256, 8) k_light_list(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m, const uint32_t *list,
                              const uint32_t *count, F f, Dev d, const uint32_t *skip = nullptr) {
     if (skip && *skip) return;
     const int lane = threadIdx.x & 31;
@@ -1448,12 +1450,13 @@ __global__ void __launch_bounds__(256, 8) k_ldd_wake(uint32_t s0, uint32_t s1, u
         ctl->mf[cur] = 0;
         ctl->nchunks = 0;
         ctl->ldd_done = 0;
-        ctl->ldd_minc = NONE;
+        ctl->ldd_minc[cur ^ 1] = NONE;   // the next frontier's, filled by this round's commit
     }
     // the uncovered ids of [s0, s1) join the frontier with one atomic per
     // block (block_compact; only this block touches its ids' bits, so the
     // two passes see the same ones)
     bool any = false;
+    uint32_t vmin = NONE;
     block_compact(
         (uint64_t)(s1 - s0), nfront,
         [&](uint64_t i) {
@@ -1467,8 +1470,12 @@ __global__ void __launch_bounds__(256, 8) k_ldd_wake(uint32_t s0, uint32_t s1, u
             if (stamp) stamp[v] = step - 1;
             front[k] = v;
             any = true;
+            vmin = v < vmin ? v : vmin;
         });
     if (any) atomicMax(last_round, round + 1);
+    // the new centres' ids join the frontier's smallest centre
+    vmin = __reduce_min_sync(0xFFFFFFFFu, vmin);
+    if ((threadIdx.x & 31) == 0 && vmin != NONE) atomicMin(&ctl->ldd_minc[cur], vmin);
 }
 
 struct LDDEdge {
@@ -1510,7 +1517,7 @@ struct LDDEdge {
 __global__ void __launch_bounds__(256, 8) k_ldd_commit(uint32_t *P, uint32_t *vis, uint32_t *cand, const uint32_t *next,
                              const uint32_t *nnext, uint32_t *last_round, uint32_t round, uint32_t *stamp,
                              uint32_t step, uint32_t *fbm = nullptr, const uint32_t *front = nullptr,
-                             const uint32_t *nfront = nullptr) {
+                             const uint32_t *nfront = nullptr, uint32_t *minc_next = nullptr) {
     if (fbm) {
         const uint32_t nf = *nfront;
         for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nf;
@@ -1518,15 +1525,23 @@ __global__ void __launch_bounds__(256, 8) k_ldd_commit(uint32_t *P, uint32_t *vi
             fbm[front[i] >> 5] = 0u;
     }
     const uint32_t total = *nnext;
+    uint32_t cmin = NONE;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < total;
          i += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t w = next[i];
-        P[w] = cand[w];
+        const uint32_t c = cand[w];
+        P[w] = c;
+        cmin = c < cmin ? c : cmin;
         if (stamp) stamp[w] = step;
         cand[w] = NONE;
         atomicOr(vis + (w >> 5), 1u << (w & 31));
     }
     if (blockIdx.x == 0 && threadIdx.x == 0 && total) atomicMax(last_round, round + 1);
+    // the claimed vertices' centres: the next frontier's smallest centre
+    if (minc_next) {
+        cmin = __reduce_min_sync(0xFFFFFFFFu, cmin);
+        if ((threadIdx.x & 31) == 0 && cmin != NONE) atomicMin(minc_next, cmin);
+    }
 }
 
 // Bottom-up LDD rounds (direction optimisation, as for BFS): a top-down
@@ -1538,27 +1553,22 @@ __global__ void __launch_bounds__(256, 8) k_ldd_commit(uint32_t *P, uint32_t *vi
 // read and often a writeMin).  Beside its edge count, the frontier is
 // marked in a bitmap every round, so any round can switch.  ldd_push_nf is
 // the frontier size the top-down pass sees: 0 in a bottom-up round.  The
-// pass also takes the smallest centre id of the frontier (ldd_minc): a
-// bottom-up scan that meets it can stop, since no neighbour offers less.
+// frontier's smallest centre id (ldd_minc[cur], folded in by the commit
+// that built the frontier and by the wake that added its new centres) lets
+// a bottom-up scan stop when it meets it: no neighbour offers less.
 template <typename OffT>
 __global__ void __launch_bounds__(256, 8) k_ldd_front(const OffT *I, uint32_t n, uint64_t m, const uint32_t *list,
-                                                      const uint32_t *count, const uint32_t *P, uint32_t *fbm,
-                                                      Ctl *ctl, int cur, Dev d) {
+                                                      const uint32_t *count, uint32_t *fbm, Ctl *ctl, int cur, Dev d) {
     const uint32_t total = *count;
     unsigned long long s = 0;
     const int lane = threadIdx.x & 31;
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    uint32_t minc = NONE;
     for (uint64_t base = warp * 32; base < total; base += nw * 32) {
         const bool act = base + lane < total;
         const uint32_t u = act ? list[base + lane] : 0;
         uint64_t b = 0, e = 0;
-        if (act) {
-            vertex_range(I, u, m, b, e, d);
-            const uint32_t c = P[u];
-            minc = c < minc ? c : minc;
-        }
+        if (act) vertex_range(I, u, m, b, e, d);
         s += e - b;
         // one OR per distinct bitmap word in the warp
         const uint32_t word = act ? (u >> 5) : NONE;
@@ -1568,8 +1578,6 @@ __global__ void __launch_bounds__(256, 8) k_ldd_front(const OffT *I, uint32_t n,
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
     if (lane == 0 && s) atomicAdd(&ctl->mf[cur], s);
-    minc = __reduce_min_sync(0xFFFFFFFFu, minc);
-    if (lane == 0 && minc != NONE) atomicMin(&ctl->ldd_minc, minc);
     // the last block to finish takes the round's direction
     __shared__ bool last;
     __threadfence();
@@ -1655,7 +1663,7 @@ template <typename OffT>
 __global__ void __launch_bounds__(256, 8) k_ldd_bin(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m,
                                                     const uint32_t *front, const uint32_t *vis, LDDEdge fpush,
                                                     LDDPullEdge fpull, ChunkRef *chunks, uint32_t *nchunks,
-                                                    uint64_t cap, const Ctl *ctl, Dev d) {
+                                                    uint64_t cap, const Ctl *ctl, int cur, Dev d) {
     const int lane = threadIdx.x & 31;
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -1679,7 +1687,7 @@ __global__ void __launch_bounds__(256, 8) k_ldd_bin(const OffT *I, const uint32_
     // and scans its edges itself (a light vertex all of them, a heavier one
     // the first PULL_PROBE), stopping at the smallest frontier centre; a
     // heavier vertex whose probe did not meet it goes to the chunk list
-    const uint32_t minc = ctl->ldd_minc;
+    const uint32_t minc = ctl->ldd_minc[cur];
     for (uint64_t base = warp * 32; base < n; base += nw * 32) {
         const uint32_t vword = vis[base >> 5];
         if (vword == 0xFFFFFFFFu) continue;   // warp-uniform
@@ -1699,7 +1707,8 @@ __global__ void __launch_bounds__(256, 8) k_ldd_bin(const OffT *I, const uint32_
 template <typename OffT>
 __global__ void __launch_bounds__(256, 8) k_ldd_chunks(const OffT *I, const uint32_t *A, uint32_t n, uint64_t m,
                                                        const ChunkRef *chunks, const uint32_t *nchunks, uint64_t cap,
-                                                       LDDEdge fpush, LDDPullEdge fpull, const Ctl *ctl, Dev d) {
+                                                       LDDEdge fpush, LDDPullEdge fpull, const Ctl *ctl, int cur,
+                                                       Dev d) {
     if (!ctl->ldd_pull) {
         run_chunks(I, A, n, m, chunks, nchunks, cap, fpush, d);
         return;
@@ -1707,7 +1716,7 @@ __global__ void __launch_bounds__(256, 8) k_ldd_chunks(const OffT *I, const uint
     // bottom-up chunks: a warp per chunk, each lane its smallest candidate;
     // the warp stops once a lane meets the smallest frontier centre (or
     // skips the chunk if w already holds it), then offers the warp minimum
-    const uint32_t minc = ctl->ldd_minc;
+    const uint32_t minc = ctl->ldd_minc[cur];
     const int lane = threadIdx.x & 31;
     const uint32_t total = (uint32_t)((uint64_t)*nchunks < cap ? (uint64_t)*nchunks : cap);
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -2161,6 +2170,7 @@ cc_status ldd_sample(const Graph &g, const cc_sample_opt &so, uint32_t *P, Work 
     CC_TRY(cudaMemsetAsync(fbm, 0, words * 4, s));
     CC_TRY(cudaMemsetAsync(cand, 0xFF, (size_t)n * 4, s));
     CC_TRY(cudaMemsetAsync(ctl, 0, sizeof(Ctl), s));
+    CC_TRY(cudaMemsetAsync(ctl->ldd_minc, 0xFF, sizeof(ctl->ldd_minc), s));
     uint64_t S = 0;
     int cur = 0;
     uint32_t r = 0;
@@ -2181,24 +2191,24 @@ cc_status ldd_sample(const Graph &g, const cc_sample_opt &so, uint32_t *P, Work 
         }
         {
             CC_PROF("k_ldd_front", s);
-            k_ldd_front<OffT><<<gv, TPB, 0, s>>>(I, n, g.m, q[cur], &ctl->nfront[cur], P, fbm, ctl, cur, d);
+            k_ldd_front<OffT><<<gv, TPB, 0, s>>>(I, n, g.m, q[cur], &ctl->nfront[cur], fbm, ctl, cur, d);
         }
         LDDEdge fpush{P, vis, cand, q[nx], &ctl->nfront[nx]};
         LDDPullEdge fpull{P, fbm, cand, q[nx], &ctl->nfront[nx]};
         {
             CC_PROF("k_ldd_bin", s);
             k_ldd_bin<OffT><<<gv, TPB, 0, s>>>(I, g.A, n, g.m, q[cur], vis, fpush, fpull, chunks, &ctl->nchunks,
-                                               w.chunk_cap, ctl, d);
+                                               w.chunk_cap, ctl, cur, d);
         }
         {
             CC_PROF("k_ldd_chunks", s);
             k_ldd_chunks<OffT><<<gc, TPB, 0, s>>>(I, g.A, n, g.m, chunks, &ctl->nchunks, w.chunk_cap, fpush, fpull,
-                                                  ctl, d);
+                                                  ctl, cur, d);
         }
         {
             CC_PROF("k_ldd_commit", s);
             k_ldd_commit<<<gv, TPB, 0, s>>>(P, vis, cand, q[nx], &ctl->nfront[nx], &ctl->last_round, r, stamp,
-                                            r + 1, fbm, q[cur], &ctl->nfront[cur]);
+                                            r + 1, fbm, q[cur], &ctl->nfront[cur], &ctl->ldd_minc[nx]);
         }
         CC_TRY(cudaMemsetAsync(&ctl->nfront[cur], 0, 4, s));
         CC_LAUNCH();
@@ -2454,13 +2464,13 @@ cc_status finish_phase(const Graph &g, const cc_finish_opt &fo, const uint32_t *
             if (lower_only)
                 {
                     CC_PROF("k_range_bin", s);
-                    k_range_bin<OffT, UnionEdge<E>><<<ge, TPB, 0, s>>>(I, g.A, n, g.m, P, nullptr, f, chunks,
+                    k_range_bin<OffT, UnionEdge<E>><<<gv, TPB, 0, s>>>(I, g.A, n, g.m, P, nullptr, f, chunks,
                                                                        &ctl->nchunks, w.chunk_cap, &ctl->edges, d);
                 }
             else
                 {
                     CC_PROF("k_light_list", s);
-                    k_light_list<OffT, UnionEdge<E>><<<ge, TPB, 0, s>>>(I, g.A, n, g.m, light, &ctl->nlight, f, d,
+                    k_light_list<OffT, UnionEdge<E>><<<gv, TPB, 0, s>>>(I, g.A, n, g.m, light, &ctl->nlight, f, d,
                                                                          skip);
                 }
             {
@@ -2518,7 +2528,7 @@ cc_status finish_phase(const Graph &g, const cc_finish_opt &fo, const uint32_t *
             SVEdge f{P, prev, &ctl->changed, false};
             {
                 CC_PROF("k_light_list", s);
-                k_light_list<OffT, SVEdge><<<ge, TPB, 0, s>>>(I, g.A, n, g.m, light, &ctl->nlight, f, d);
+                k_light_list<OffT, SVEdge><<<gv, TPB, 0, s>>>(I, g.A, n, g.m, light, &ctl->nlight, f, d);
             }
             {
                 CC_PROF("k_chunks", s);
@@ -2528,7 +2538,7 @@ cc_status finish_phase(const Graph &g, const cc_finish_opt &fo, const uint32_t *
             LTEdge f{P, prev, &ctl->changed, false};
             {
                 CC_PROF("k_light_list", s);
-                k_light_list<OffT, LTEdge><<<ge, TPB, 0, s>>>(I, g.A, n, g.m, light, &ctl->nlight, f, d);
+                k_light_list<OffT, LTEdge><<<gv, TPB, 0, s>>>(I, g.A, n, g.m, light, &ctl->nlight, f, d);
             }
             {
                 CC_PROF("k_chunks", s);
