@@ -111,6 +111,7 @@ struct Ctl {
     unsigned long long gcount;         // k-out fused pass: non-roots under the L_max guess
     uint32_t fallback;                 // 1 when the guess holds no majority (labels counted in full)
     uint32_t stats_done;               // selected path: blocks of k_degree_stats done
+    uint32_t kout_span;                // k-out first pass: vertex spans taken so far
 };
 
 // Launch accounting: one scope per kernel launch.  Counts every launch and,

@@ -297,11 +297,14 @@ constexpr int KOUT_MINB = 8;
 // SM it spilled 160-250 bytes per thread to local memory, so it runs at six
 // (40 registers).
 constexpr int HOOK_MINB = 6;
-// The first-edge queue of k_kout_hook_first: one region per block (grids of
-// at most 8 blocks per SM, so KOUT_MAX_BLOCKS covers 256 SMs).  The regions
-// hold n pairs plus, per warp of the grid, one 128-vertex step of slack.
-constexpr uint32_t KOUT_MAX_BLOCKS = 2048;
-__host__ inline uint64_t kout_defer_entries(uint64_t n) { return n + 128 + (uint64_t)KOUT_MAX_BLOCKS * 8 * 128; }
+// The first k-out pass hands out its vertices in spans of KOUT_SPAN (eight
+// warp steps of 128): a warp takes the next span from a counter when it has
+// finished its last, so warps on faster SMs take more spans.  The first-edge
+// queue has one region of KOUT_SPAN pairs per span, with the span's count
+// beside it.
+constexpr uint32_t KOUT_SPAN = 1024;
+__host__ inline uint64_t kout_spans(uint64_t n) { return (n + KOUT_SPAN - 1) / KOUT_SPAN; }
+__host__ inline uint64_t kout_defer_entries(uint64_t n) { return kout_spans(n) * KOUT_SPAN; }
 
 template <typename OffT, class E, int NB>
 __global__ void __launch_bounds__(256, KOUT_MINB)
@@ -355,31 +358,26 @@ void launch_kout(unsigned grid, cudaStream_t s, const OffT *I, const uint32_t *A
 // still a root and the link keeps P[x] <= x.  Otherwise P[v] = v, and a
 // vertex with w0 > v (all its neighbours larger) is queued for a real Union
 // in part two as the pair (v, w0), so part two reads no offsets or edges.
-// The queue is cut into one region of `cap_blk` pairs per block, counted in
-// shared memory (dcount[block] at the end): one global counter for the
-// whole grid took an atomic per warp step on a single address, which
-// serialised (about 2 ns each, 0.5M of them at RMAT-26: most of the
-// kernel's time).  A block's warp steps hold at most cap_blk vertices, so
-// its region cannot overflow (checked, flagged).
+// Warps take spans of KOUT_SPAN vertices from *span_ctr (zero at launch),
+// the next span's index asked for when a span starts; a span's queued pairs
+// go to its own region of the queue (defer + span * KOUT_SPAN, at most one
+// per vertex) and their number to dcount[span], counted by the warp itself.
+// (With static steps the busiest SM ran 16% above the mean; one global
+// queue counter hit by every warp step serialised at the L2, about 2 ns per
+// atomic, 0.5M of them at RMAT-26.)
 template <typename OffT>
 __global__ void __launch_bounds__(256, HOOK_MINB) k_kout_hook_first(const OffT *I, const uint32_t *A, uint32_t n,
                                                             uint64_t m, uint32_t *P, uint2 *defer,
-                                                            uint32_t *dcount, uint32_t cap_blk, uint32_t *pick1,
+                                                            uint32_t *dcount, uint32_t *span_ctr, uint32_t *pick1,
                                                             uint32_t k, uint32_t rule, uint64_t seed, uint32_t *nz,
                                                             Dev d) {
-    __shared__ uint32_t nblk;
-    if (threadIdx.x == 0) nblk = 0;
-    __syncthreads();
-    uint2 *my_defer = defer + (uint64_t)blockIdx.x * cap_blk;
     const int lane = threadIdx.x & 31;
-    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint32_t nspan = (uint32_t)(((uint64_t)n + KOUT_SPAN - 1) / KOUT_SPAN);
     // A warp step covers 128 consecutive vertices as four groups of 32;
     // lane L owns vertex base + 32j + L, so each load instruction touches a
     // contiguous stretch of offsets, first edges and labels.
     // o[j] = I[base + 32j + L] (j < 4), o[4] = I[base + 128 + L].
     uint64_t o[5];
-    uint64_t base = warp * 128;
     auto load = [&](uint64_t bs) {
 #pragma unroll
         for (int j = 0; j < 5; ++j) {
@@ -387,75 +385,106 @@ __global__ void __launch_bounds__(256, HOOK_MINB) k_kout_hook_first(const OffT *
             o[j] = idx <= n ? (uint64_t)ld_off(I + idx) : 0;
         }
     };
-    if (base < n) load(base);
-    for (; base < n; base += nw * 128) {
-        uint64_t beg[4], end[4];
+    uint32_t span = 0;
+    if (lane == 0) span = atomicAdd(span_ctr, 1u);
+    span = __shfl_sync(0xFFFFFFFFu, span, 0);
+    if (span < nspan) load((uint64_t)span * KOUT_SPAN);
+    while (span < nspan) {
+        uint32_t next = 0;
+        if (lane == 0) next = atomicAdd(span_ctr, 1u);
+        uint2 *my_defer = defer + (uint64_t)span * KOUT_SPAN;
+        uint32_t queued = 0;   // the span's queued pairs so far (warp-uniform)
+        const uint64_t s0 = (uint64_t)span * KOUT_SPAN;
+        const uint64_t s1 = s0 + KOUT_SPAN < n ? s0 + KOUT_SPAN : n;
+        for (uint64_t base = s0; base < s1; base += 128) {
+            uint64_t beg[4], end[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const uint64_t nxt = __shfl_down_sync(0xFFFFFFFFu, o[j], 1);
-            const uint64_t first = __shfl_sync(0xFFFFFFFFu, o[j + 1], 0);
-            beg[j] = o[j];
-            end[j] = lane < 31 ? nxt : first;
-        }
-        uint32_t w[4], r[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const uint64_t v = base + 32 * j + lane;
-            uint64_t b = 0, e = 0;
-            if (v < n) clamp_range(beg[j], end[j], m, b, e, d);
-            // nz (optional): bit v set iff v has an edge, one word per 32
-            // consecutive vertices (the later binning skips isolated vertices
-            // without reading their offsets)
-            const unsigned has = __ballot_sync(0xFFFFFFFFu, e > b);
-            if (nz && lane == 0 && base + 32 * j < n) nz[(base >> 5) + j] = has;
-            // pick 0 (the first edge, or a uniform pick under the pure rule)
-            w[j] = e > b ? ld_stream(A + b + kout_offset(rule, seed, v, k, 0, e - b)) : NONE;
-            // with k = 2 pick 1 is read here too and kept for the second
-            // round, so that round reads no offsets or edges
-            r[j] = NONE;
-            if (pick1 && e > b) {
-                const uint64_t off = kout_offset(rule, seed, v, 2, 1, e - b);
-                if (off != NO_PICK) r[j] = ld_stream(A + b + off);
+            for (int j = 0; j < 4; ++j) {
+                const uint64_t nxt = __shfl_down_sync(0xFFFFFFFFu, o[j], 1);
+                const uint64_t first = __shfl_sync(0xFFFFFFFFu, o[j + 1], 0);
+                beg[j] = o[j];
+                end[j] = lane < 31 ? nxt : first;
             }
-        }
-        // the next step's offsets load while this step's first edges are read
-        if (base + nw * 128 < n) load(base + nw * 128);
-        uint32_t nd = 0;
+            uint32_t w[4], r[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const uint64_t v = base + 32 * j + lane;
-            if (w[j] != NONE && w[j] >= n) { atomicOr(d.err, ERR_BAD_EDGE); w[j] = NONE; }
-            if (v < n) P[v] = (w[j] != NONE && w[j] < v) ? w[j] : (uint32_t)v;
-            if (d.forest && v < n && w[j] != NONE && w[j] < v) d.forest[v] = make_uint2((uint32_t)v, w[j]);
-            nd += (w[j] != NONE && w[j] > v);
-            if (pick1 && v < n) {
-                if (r[j] != NONE && r[j] >= n) { atomicOr(d.err, ERR_BAD_EDGE); r[j] = NONE; }
-                pick1[v] = r[j] == (uint32_t)v ? NONE : r[j];
+            for (int j = 0; j < 4; ++j) {
+                const uint64_t v = base + 32 * j + lane;
+                uint64_t b = 0, e = 0;
+                if (v < n) clamp_range(beg[j], end[j], m, b, e, d);
+                // nz (optional): bit v set iff v has an edge, one word per
+                // 32 consecutive vertices (the later binning skips isolated
+                // vertices without reading their offsets)
+                const unsigned has = __ballot_sync(0xFFFFFFFFu, e > b);
+                if (nz && lane == 0 && base + 32 * j < n) nz[(base >> 5) + j] = has;
+                // pick 0 (the first edge, or a uniform pick under the pure rule)
+                w[j] = e > b ? ld_stream(A + b + kout_offset(rule, seed, v, k, 0, e - b)) : NONE;
+                // with k = 2 pick 1 is read here too and kept for the second
+                // round, so that round reads no offsets or edges
+                r[j] = NONE;
+                if (pick1 && e > b) {
+                    const uint64_t off = kout_offset(rule, seed, v, 2, 1, e - b);
+                    if (off != NO_PICK) r[j] = ld_stream(A + b + off);
+                }
             }
-        }
-        uint32_t slot = warp_append_full(&nblk, nd);
+            // the next step's offsets load while this step's first edges are
+            // read: the span's next step, or the first step of the next span
+            if (base + 128 < s1) {
+                load(base + 128);
+            } else {
+                const uint32_t nsp = __shfl_sync(0xFFFFFFFFu, next, 0);
+                if (nsp < nspan) load((uint64_t)nsp * KOUT_SPAN);
+            }
+            uint32_t nd = 0;
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if (w[j] != NONE && w[j] > base + 32 * j + lane) {
-                if (slot < cap_blk) my_defer[slot] = make_uint2((uint32_t)(base + 32 * j + lane), w[j]);
-                else atomicOr(d.err, ERR_NONCONVERGED);
-                ++slot;
+            for (int j = 0; j < 4; ++j) {
+                const uint64_t v = base + 32 * j + lane;
+                if (w[j] != NONE && w[j] >= n) { atomicOr(d.err, ERR_BAD_EDGE); w[j] = NONE; }
+                if (v < n) P[v] = (w[j] != NONE && w[j] < v) ? w[j] : (uint32_t)v;
+                if (d.forest && v < n && w[j] != NONE && w[j] < v) d.forest[v] = make_uint2((uint32_t)v, w[j]);
+                nd += (w[j] != NONE && w[j] > v);
+                if (pick1 && v < n) {
+                    if (r[j] != NONE && r[j] >= n) { atomicOr(d.err, ERR_BAD_EDGE); r[j] = NONE; }
+                    pick1[v] = r[j] == (uint32_t)v ? NONE : r[j];
+                }
             }
+            // the lane's slots in the span's region: an exclusive scan of the
+            // lanes' counts after the pairs queued so far
+            uint32_t incl = nd;
+#pragma unroll
+            for (int o2 = 1; o2 < 32; o2 <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, o2);
+                if (lane >= o2) incl += t;
+            }
+            uint32_t slot = queued + incl - nd;
+            queued += __shfl_sync(0xFFFFFFFFu, incl, 31);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (w[j] != NONE && w[j] > base + 32 * j + lane) {
+                    if (slot < KOUT_SPAN) my_defer[slot] = make_uint2((uint32_t)(base + 32 * j + lane), w[j]);
+                    else atomicOr(d.err, ERR_NONCONVERGED);
+                    ++slot;
+                }
+        }
+        if (lane == 0) dcount[span] = queued < KOUT_SPAN ? queued : KOUT_SPAN;
+        span = __shfl_sync(0xFFFFFFFFu, next, 0);
     }
-    __syncthreads();
-    if (threadIdx.x == 0) dcount[blockIdx.x] = nblk < cap_blk ? nblk : cap_blk;
 }
 
-// First edges, part two: Union(v, w0) for the queued (v, w0) pairs, the
-// regions of the first pass's `regions` blocks taken block by block.
+// First edges, part two: Union(v, w0) for the queued (v, w0) pairs, one
+// warp per span region (`regions` of them, `cap` pairs apart, dcount[r]
+// used).  Block 0 then clears the first pass's span counter.
 template <class E>
 __global__ void __launch_bounds__(256, KOUT_MINB)
-k_kout_defer(uint32_t n, uint32_t *P, const uint2 *defer, const uint32_t *dcount, uint32_t regions, uint32_t cap_blk,
-             Dev d) {
-    for (uint32_t r = blockIdx.x; r < regions; r += gridDim.x) {
+k_kout_defer(uint32_t n, uint32_t *P, const uint2 *defer, const uint32_t *dcount, uint32_t regions, uint32_t cap,
+             uint32_t *span_ctr, Dev d) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && span_ctr) *span_ctr = 0;
+    const int lane = threadIdx.x & 31;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t r = warp; r < regions; r += nw) {
         const uint32_t total = dcount[r];
-        const uint2 *q0 = defer + (uint64_t)r * cap_blk;
-        for (uint32_t i = threadIdx.x; i < total; i += blockDim.x) {
+        const uint2 *q0 = defer + (uint64_t)r * cap;
+        for (uint32_t i = lane; i < total; i += 32) {
             const uint2 q = q0[i];
             uint32_t u1[1] = {q.x}, w1[1] = {q.y};
             bool ok[1] = {q.y < n && q.y != q.x};
@@ -1858,10 +1887,10 @@ void plan(Work &w, const Graph &g, int sample_kind, uint32_t freq_samples, int f
     w.chunk_cap = chunk_capacity(n, g.m) + CHUNK_SLACK;
     w.o_chunks = w.sc.reserve(w.chunk_cap * sizeof(ChunkRef));
     if (sample_kind == CC_SAMPLE_KOUT) {
-        // per-block regions of the first-edge queue: n pairs plus one warp
-        // step's slack per warp of a grid of up to KOUT_MAX_BLOCKS blocks
+        // the first-edge queue: one region of KOUT_SPAN pairs per span of
+        // vertices, and the spans' counts
         w.o_defer = w.sc.reserve(kout_defer_entries(n) * 8);
-        w.o_dcount = w.sc.reserve((size_t)KOUT_MAX_BLOCKS * 4);
+        w.o_dcount = w.sc.reserve((size_t)kout_spans(n) * 4);
         w.o_pick = w.sc.reserve(n * 4);
     }
     if (sample_kind != CC_SAMPLE_NONE && freq_samples == 0) {
@@ -2288,25 +2317,25 @@ cc_status sample_phase(const Graph &g, const cc_sample_opt &so, const cc_finish_
         const OffT *I = static_cast<const OffT *>(g.I);
         uint2 *defer = w.sc.at<uint2>(w.o_defer);
         uint32_t *dcount = w.sc.at<uint32_t>(w.o_dcount);
-        // the first pass's grid (one wave at its occupancy); a block's warps
-        // take steps warp, warp + nw, ... of 128 vertices
+        // the first pass's grid (one wave at its occupancy); its warps take
+        // spans of KOUT_SPAN vertices from a counter in the control block
+        // (zero: the block is cleared before sampling, and the queue pass
+        // clears the counter again after the spans are done)
         const unsigned gh = grid_for(di, g.n, TPB, HOOK_MINB);
-        const uint64_t steps = ((uint64_t)g.n + 127) / 128, nw = (uint64_t)gh * (TPB / 32);
-        const uint64_t cap_blk = (TPB / 32) * 128 * ((steps + nw - 1) / nw);
-        if (gh > KOUT_MAX_BLOCKS || (uint64_t)gh * cap_blk > kout_defer_entries(g.n) || cap_blk > 0xFFFFFFFFull)
-            return CC_ERR_INVALID;   // not reached: grids have at most 8 blocks per SM
+        const uint32_t nspan = (uint32_t)kout_spans(g.n);
+        uint32_t *span_ctr = &w.ctl()->kout_span;
         uint32_t *pick1 = so.k == 2 ? w.sc.at<uint32_t>(w.o_pick) : nullptr;
         // the fused binning (k = 2, exact IdentifyFrequent, a finish to follow)
         const bool fuse = count_into && pick1 && w.has_nz;
         uint32_t *nz = fuse ? w.sc.at<uint32_t>(w.o_nz) : nullptr;
         {
             CC_PROF("k_kout_hook_first", s);
-            k_kout_hook_first<OffT><<<gh, TPB, 0, s>>>(I, g.A, g.n, g.m, P, defer, dcount, (uint32_t)cap_blk, pick1,
+            k_kout_hook_first<OffT><<<gh, TPB, 0, s>>>(I, g.A, g.n, g.m, P, defer, dcount, span_ctr, pick1,
                                                        so.k, so.kout_rule, so.seed, nz, d);
         }
         {
             CC_PROF("k_kout_defer", s);
-            k_kout_defer<E><<<gv, TPB, 0, s>>>(g.n, P, defer, dcount, gh, (uint32_t)cap_blk, d);
+            k_kout_defer<E><<<gv, TPB, 0, s>>>(g.n, P, defer, dcount, nspan, KOUT_SPAN, span_ctr, d);
         }
         if (so.k > 1) {
             // full compression between the rounds: without it the second
