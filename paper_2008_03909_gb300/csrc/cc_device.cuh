@@ -515,6 +515,41 @@ __device__ __forceinline__ uint32_t append_one(uint32_t *counter) {
     return g.shfl(base, 0) + g.thread_rank();
 }
 
+// ---------------------------------------------------------------- dynamic spans
+// A streaming pass over items [0, total) in spans of `span` items: a warp
+// takes the next span from ctr[0] when it finishes its last (the next one
+// asked for when a span starts), so warps on faster SMs take more spans
+// where a static grid stride leaves the slowest SM setting the kernel's
+// time.  f(i, act) is called for item i = span start + 32 t + lane with
+// every lane of the warp at each call (act false past the end), so f may
+// use warp-collective operations.  The last warp of the grid to finish
+// clears ctr[0] and ctr[1] (its done count): every other warp has had its
+// last span number by then, and the next launch on the same counters starts
+// from zero.  Every warp of the grid must call this exactly once.
+template <class F>
+__device__ __forceinline__ void warp_spans(uint32_t *ctr, uint64_t total, uint32_t span, F &&f) {
+    const unsigned FULL = 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31;
+    const uint64_t nspan = (total + span - 1) / span;
+    uint32_t s = 0;
+    if (lane == 0) s = atomicAdd(ctr, 1u);
+    s = __shfl_sync(FULL, s, 0);
+    while (s < nspan) {
+        uint32_t nx = 0;
+        if (lane == 0) nx = atomicAdd(ctr, 1u);
+        const uint64_t b = (uint64_t)s * span, e = b + span < total ? b + span : total;
+        for (uint64_t i0 = b; i0 < e; i0 += 32) f(i0 + lane, i0 + lane < e);
+        s = __shfl_sync(FULL, nx, 0);
+    }
+    if (lane == 0) {
+        const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+        if (atomicAdd(ctr + 1, 1u) == nwarps - 1) {
+            ctr[0] = 0;
+            ctr[1] = 0;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- compaction
 // Stream compaction of the index range [0, total) with one atomic per
 // block: each block takes a contiguous slice, counts the items it keeps,

@@ -112,6 +112,7 @@ struct Ctl {
     uint32_t fallback;                 // 1 when the guess holds no majority (labels counted in full)
     uint32_t stats_done;               // selected path: blocks of k_degree_stats done
     uint32_t kout_span;                // k-out first pass: vertex spans taken so far
+    uint32_t spans[2][2];              // dynamic spans of the k-out mid compression [0] and fused count [1]: taken, done
 };
 
 // Launch accounting: one scope per kernel launch.  Counts every launch and,
