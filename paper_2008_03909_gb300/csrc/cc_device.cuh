@@ -516,20 +516,25 @@ __device__ __forceinline__ uint32_t append_one(uint32_t *counter) {
 }
 
 // ---------------------------------------------------------------- dynamic spans
-// A streaming pass over items [0, total) in spans of `span` items: a warp
-// takes the next span from ctr[0] when it finishes its last (the next one
-// asked for when a span starts), so warps on faster SMs take more spans
-// where a static grid stride leaves the slowest SM setting the kernel's
-// time.  f(i, act) is called for item i = span start + 32 t + lane with
+// A streaming pass over items [0, total) in spans: a warp takes the next
+// span from ctr[0] when it finishes its last (the next one asked for when a
+// span starts), so warps on faster SMs take more spans where a static grid
+// stride leaves the slowest SM setting the kernel's time.  A span is the
+// grid's share of items over four spans per warp, in multiples of 32, at
+// least 32 and at most `max_span` (small inputs keep every warp busy).
+// f(i, act) is called for item i = span start + 32 t + lane with
 // every lane of the warp at each call (act false past the end), so f may
 // use warp-collective operations.  The last warp of the grid to finish
 // clears ctr[0] and ctr[1] (its done count): every other warp has had its
 // last span number by then, and the next launch on the same counters starts
 // from zero.  Every warp of the grid must call this exactly once.
 template <class F>
-__device__ __forceinline__ void warp_spans(uint32_t *ctr, uint64_t total, uint32_t span, F &&f) {
+__device__ __forceinline__ void warp_spans(uint32_t *ctr, uint64_t total, uint32_t max_span, F &&f) {
     const unsigned FULL = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31;
+    const uint64_t nwarps_grid = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    uint64_t span = total / (4 * nwarps_grid) / 32 * 32;
+    span = span < 32 ? 32 : (span > max_span ? max_span : span);
     const uint64_t nspan = (total + span - 1) / span;
     uint32_t s = 0;
     if (lane == 0) s = atomicAdd(ctr, 1u);

@@ -307,14 +307,20 @@ constexpr int KOUT_MINB = 8;
 // SM it spilled 160-250 bytes per thread to local memory, so it runs at six
 // (40 registers).
 constexpr int HOOK_MINB = 6;
-// The first k-out pass hands out its vertices in spans of KOUT_SPAN (eight
-// warp steps of 128): a warp takes the next span from a counter when it has
-// finished its last, so warps on faster SMs take more spans.  The first-edge
-// queue has one region of KOUT_SPAN pairs per span, with the span's count
-// beside it.
-constexpr uint32_t KOUT_SPAN = 1024;
-__host__ inline uint64_t kout_spans(uint64_t n) { return (n + KOUT_SPAN - 1) / KOUT_SPAN; }
-__host__ inline uint64_t kout_defer_entries(uint64_t n) { return kout_spans(n) * KOUT_SPAN; }
+// The first k-out pass hands out its vertices in spans of up to
+// KOUT_SPAN_MAX (eight warp steps of 128): a warp takes the next span from a
+// counter when it has finished its last, so warps on faster SMs take more
+// spans.  The span is the grid's share over four spans per warp, in whole
+// warp steps, so a small graph still gives every warp work.  The first-edge
+// queue has one region of `span` pairs per span, with the span's count
+// beside it; the scratch is sized for the smallest span.
+constexpr uint32_t KOUT_SPAN_MAX = 1024;
+__host__ inline uint32_t kout_span_for(uint64_t n, uint64_t warps) {
+    uint64_t s = n / (4 * warps) / 128 * 128;
+    return (uint32_t)(s < 128 ? 128 : (s > KOUT_SPAN_MAX ? KOUT_SPAN_MAX : s));
+}
+__host__ inline uint64_t kout_spans_max(uint64_t n) { return (n + 127) / 128; }
+__host__ inline uint64_t kout_defer_entries(uint64_t n) { return n + KOUT_SPAN_MAX; }
 
 template <typename OffT, class E, int NB>
 __global__ void __launch_bounds__(256, KOUT_MINB)
@@ -368,21 +374,22 @@ void launch_kout(unsigned grid, cudaStream_t s, const OffT *I, const uint32_t *A
 // still a root and the link keeps P[x] <= x.  Otherwise P[v] = v, and a
 // vertex with w0 > v (all its neighbours larger) is queued for a real Union
 // in part two as the pair (v, w0), so part two reads no offsets or edges.
-// Warps take spans of KOUT_SPAN vertices from *span_ctr (zero at launch),
-// the next span's index asked for when a span starts; a span's queued pairs
-// go to its own region of the queue (defer + span * KOUT_SPAN, at most one
-// per vertex) and their number to dcount[span], counted by the warp itself.
+// Warps take spans of `span` vertices (a multiple of 128) from *span_ctr
+// (zero at launch), the next span's index asked for when a span starts; a
+// span's queued pairs go to its own region of the queue (defer + its index
+// * span, at most one per vertex) and their number to dcount[index],
+// counted by the warp itself.
 // (With static steps the busiest SM ran 16% above the mean; one global
 // queue counter hit by every warp step serialised at the L2, about 2 ns per
 // atomic, 0.5M of them at RMAT-26.)
 template <typename OffT>
 __global__ void __launch_bounds__(256, HOOK_MINB) k_kout_hook_first(const OffT *I, const uint32_t *A, uint32_t n,
                                                             uint64_t m, uint32_t *P, uint2 *defer,
-                                                            uint32_t *dcount, uint32_t *span_ctr, uint32_t *pick1,
-                                                            uint32_t k, uint32_t rule, uint64_t seed, uint32_t *nz,
-                                                            Dev d) {
+                                                            uint32_t *dcount, uint32_t *span_ctr, uint32_t span_len,
+                                                            uint32_t *pick1, uint32_t k, uint32_t rule, uint64_t seed,
+                                                            uint32_t *nz, Dev d) {
     const int lane = threadIdx.x & 31;
-    const uint32_t nspan = (uint32_t)(((uint64_t)n + KOUT_SPAN - 1) / KOUT_SPAN);
+    const uint32_t nspan = (uint32_t)(((uint64_t)n + span_len - 1) / span_len);
     // A warp step covers 128 consecutive vertices as four groups of 32;
     // lane L owns vertex base + 32j + L, so each load instruction touches a
     // contiguous stretch of offsets, first edges and labels.
@@ -398,14 +405,14 @@ __global__ void __launch_bounds__(256, HOOK_MINB) k_kout_hook_first(const OffT *
     uint32_t span = 0;
     if (lane == 0) span = atomicAdd(span_ctr, 1u);
     span = __shfl_sync(0xFFFFFFFFu, span, 0);
-    if (span < nspan) load((uint64_t)span * KOUT_SPAN);
+    if (span < nspan) load((uint64_t)span * span_len);
     while (span < nspan) {
         uint32_t next = 0;
         if (lane == 0) next = atomicAdd(span_ctr, 1u);
-        uint2 *my_defer = defer + (uint64_t)span * KOUT_SPAN;
+        uint2 *my_defer = defer + (uint64_t)span * span_len;
         uint32_t queued = 0;   // the span's queued pairs so far (warp-uniform)
-        const uint64_t s0 = (uint64_t)span * KOUT_SPAN;
-        const uint64_t s1 = s0 + KOUT_SPAN < n ? s0 + KOUT_SPAN : n;
+        const uint64_t s0 = (uint64_t)span * span_len;
+        const uint64_t s1 = s0 + span_len < n ? s0 + span_len : n;
         for (uint64_t base = s0; base < s1; base += 128) {
             uint64_t beg[4], end[4];
 #pragma unroll
@@ -442,7 +449,7 @@ __global__ void __launch_bounds__(256, HOOK_MINB) k_kout_hook_first(const OffT *
                 load(base + 128);
             } else {
                 const uint32_t nsp = __shfl_sync(0xFFFFFFFFu, next, 0);
-                if (nsp < nspan) load((uint64_t)nsp * KOUT_SPAN);
+                if (nsp < nspan) load((uint64_t)nsp * span_len);
             }
             uint32_t nd = 0;
 #pragma unroll
@@ -470,12 +477,12 @@ __global__ void __launch_bounds__(256, HOOK_MINB) k_kout_hook_first(const OffT *
 #pragma unroll
             for (int j = 0; j < 4; ++j)
                 if (w[j] != NONE && w[j] > base + 32 * j + lane) {
-                    if (slot < KOUT_SPAN) my_defer[slot] = make_uint2((uint32_t)(base + 32 * j + lane), w[j]);
+                    if (slot < span_len) my_defer[slot] = make_uint2((uint32_t)(base + 32 * j + lane), w[j]);
                     else atomicOr(d.err, ERR_NONCONVERGED);
                     ++slot;
                 }
         }
-        if (lane == 0) dcount[span] = queued < KOUT_SPAN ? queued : KOUT_SPAN;
+        if (lane == 0) dcount[span] = queued < span_len ? queued : span_len;
         span = __shfl_sync(0xFFFFFFFFu, next, 0);
     }
 }
@@ -1896,10 +1903,10 @@ void plan(Work &w, const Graph &g, int sample_kind, uint32_t freq_samples, int f
     w.chunk_cap = chunk_capacity(n, g.m) + CHUNK_SLACK;
     w.o_chunks = w.sc.reserve(w.chunk_cap * sizeof(ChunkRef));
     if (sample_kind == CC_SAMPLE_KOUT) {
-        // the first-edge queue: one region of KOUT_SPAN pairs per span of
+        // the first-edge queue: one region of `span` pairs per span of
         // vertices, and the spans' counts
         w.o_defer = w.sc.reserve(kout_defer_entries(n) * 8);
-        w.o_dcount = w.sc.reserve((size_t)kout_spans(n) * 4);
+        w.o_dcount = w.sc.reserve((size_t)kout_spans_max(n) * 4);
         w.o_pick = w.sc.reserve(n * 4);
     }
     if (sample_kind != CC_SAMPLE_NONE && freq_samples == 0) {
@@ -2327,11 +2334,12 @@ cc_status sample_phase(const Graph &g, const cc_sample_opt &so, const cc_finish_
         uint2 *defer = w.sc.at<uint2>(w.o_defer);
         uint32_t *dcount = w.sc.at<uint32_t>(w.o_dcount);
         // the first pass's grid (one wave at its occupancy); its warps take
-        // spans of KOUT_SPAN vertices from a counter in the control block
-        // (zero: the block is cleared before sampling, and the queue pass
-        // clears the counter again after the spans are done)
+        // spans of vertices from a counter in the control block (zero: the
+        // block is cleared before sampling, and the queue pass clears the
+        // counter again after the spans are done)
         const unsigned gh = grid_for(di, g.n, TPB, HOOK_MINB);
-        const uint32_t nspan = (uint32_t)kout_spans(g.n);
+        const uint32_t span_len = kout_span_for(g.n, (uint64_t)gh * (TPB / 32));
+        const uint32_t nspan = (uint32_t)(((uint64_t)g.n + span_len - 1) / span_len);
         uint32_t *span_ctr = &w.ctl()->kout_span;
         uint32_t *pick1 = so.k == 2 ? w.sc.at<uint32_t>(w.o_pick) : nullptr;
         // the fused binning (k = 2, exact IdentifyFrequent, a finish to follow)
@@ -2339,12 +2347,12 @@ cc_status sample_phase(const Graph &g, const cc_sample_opt &so, const cc_finish_
         uint32_t *nz = fuse ? w.sc.at<uint32_t>(w.o_nz) : nullptr;
         {
             CC_PROF("k_kout_hook_first", s);
-            k_kout_hook_first<OffT><<<gh, TPB, 0, s>>>(I, g.A, g.n, g.m, P, defer, dcount, span_ctr, pick1,
-                                                       so.k, so.kout_rule, so.seed, nz, d);
+            k_kout_hook_first<OffT><<<gh, TPB, 0, s>>>(I, g.A, g.n, g.m, P, defer, dcount, span_ctr, span_len,
+                                                       pick1, so.k, so.kout_rule, so.seed, nz, d);
         }
         {
             CC_PROF("k_kout_defer", s);
-            k_kout_defer<E><<<gv, TPB, 0, s>>>(g.n, P, defer, dcount, nspan, KOUT_SPAN, span_ctr, d);
+            k_kout_defer<E><<<gv, TPB, 0, s>>>(g.n, P, defer, dcount, nspan, span_len, span_ctr, d);
         }
         if (so.k > 1) {
             // full compression between the rounds: without it the second
