@@ -522,6 +522,9 @@ __device__ __forceinline__ uint32_t append_one(uint32_t *counter) {
 // stride leaves the slowest SM setting the kernel's time.  A span is the
 // grid's share of items over four spans per warp, in multiples of 32, at
 // least 32 and at most `max_span` (small inputs keep every warp busy).
+// A warp's first span is its own index in the grid; the counter hands out
+// the spans after the grid's first (none when the spans do not outnumber
+// the warps, so a small input pays no atomic latency).
 // f(i, act) is called for item i = span start + 32 t + lane with
 // every lane of the warp at each call (act false past the end), so f may
 // use warp-collective operations.  The last warp of the grid to finish
@@ -536,17 +539,16 @@ __device__ __forceinline__ void warp_spans(uint32_t *ctr, uint64_t total, uint32
     uint64_t span = total / (4 * nwarps_grid) / 32 * 32;
     span = span < 32 ? 32 : (span > max_span ? max_span : span);
     const uint64_t nspan = (total + span - 1) / span;
-    uint32_t s = 0;
-    if (lane == 0) s = atomicAdd(ctr, 1u);
-    s = __shfl_sync(FULL, s, 0);
+    const bool dynamic = nspan > nwarps_grid;   // grid-uniform
+    uint64_t s = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     while (s < nspan) {
-        uint32_t nx = 0;
-        if (lane == 0) nx = atomicAdd(ctr, 1u);
-        const uint64_t b = (uint64_t)s * span, e = b + span < total ? b + span : total;
+        uint64_t nx = nspan;
+        if (dynamic && lane == 0) nx = nwarps_grid + atomicAdd(ctr, 1u);
+        const uint64_t b = s * span, e = b + span < total ? b + span : total;
         for (uint64_t i0 = b; i0 < e; i0 += 32) f(i0 + lane, i0 + lane < e);
         s = __shfl_sync(FULL, nx, 0);
     }
-    if (lane == 0) {
+    if (dynamic && lane == 0) {
         const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
         if (atomicAdd(ctr + 1, 1u) == nwarps - 1) {
             ctr[0] = 0;

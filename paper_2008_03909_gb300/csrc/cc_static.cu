@@ -374,11 +374,12 @@ void launch_kout(unsigned grid, cudaStream_t s, const OffT *I, const uint32_t *A
 // still a root and the link keeps P[x] <= x.  Otherwise P[v] = v, and a
 // vertex with w0 > v (all its neighbours larger) is queued for a real Union
 // in part two as the pair (v, w0), so part two reads no offsets or edges.
-// Warps take spans of `span` vertices (a multiple of 128) from *span_ctr
-// (zero at launch), the next span's index asked for when a span starts; a
-// span's queued pairs go to its own region of the queue (defer + its index
-// * span, at most one per vertex) and their number to dcount[index],
-// counted by the warp itself.
+// Warps take spans of `span` vertices (a multiple of 128): a warp's first
+// span is its index in the grid, the rest come from *span_ctr (zero at
+// launch; the next index asked for when a span starts, and only when the
+// spans outnumber the warps); a span's queued pairs go to its own region of
+// the queue (defer + its index * span, at most one per vertex) and their
+// number to dcount[index], counted by the warp itself.
 // (With static steps the busiest SM ran 16% above the mean; one global
 // queue counter hit by every warp step serialised at the L2, about 2 ns per
 // atomic, 0.5M of them at RMAT-26.)
@@ -402,13 +403,15 @@ __global__ void __launch_bounds__(256, HOOK_MINB) k_kout_hook_first(const OffT *
             o[j] = idx <= n ? (uint64_t)ld_off(I + idx) : 0;
         }
     };
-    uint32_t span = 0;
-    if (lane == 0) span = atomicAdd(span_ctr, 1u);
-    span = __shfl_sync(0xFFFFFFFFu, span, 0);
+    // a warp's first span is its index in the grid; the counter hands out
+    // the rest (none when the spans do not outnumber the warps)
+    const uint32_t nwg = (gridDim.x * blockDim.x) >> 5;
+    const bool dynamic = nspan > nwg;   // grid-uniform
+    uint32_t span = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (span < nspan) load((uint64_t)span * span_len);
     while (span < nspan) {
-        uint32_t next = 0;
-        if (lane == 0) next = atomicAdd(span_ctr, 1u);
+        uint32_t next = nspan;
+        if (dynamic && lane == 0) next = nwg + atomicAdd(span_ctr, 1u);
         uint2 *my_defer = defer + (uint64_t)span * span_len;
         uint32_t queued = 0;   // the span's queued pairs so far (warp-uniform)
         const uint64_t s0 = (uint64_t)span * span_len;
